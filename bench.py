@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Throughput and latency of the neural-network-potential energy+force evaluation.
+
+One step = one energy+force evaluation of the whole workload through the C ABI
+(cell list -> AEVs -> per-species networks -> analytic forces), inputs resident
+in HBM.  Default workload: 'water9000' (3000 rigid waters, 9000 atoms, periodic
+44.77 A box, 4-species 384-dim AEV, networks 384-160-128-96-1, FP32 path).
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload water9000]
+                  [--precision fp32|bf16] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank evaluates its own replica of the workload on
+its own GPU (independent replicas, no data-path collective); the time is the
+maximum over ranks.  Rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle (the slow, obviously-correct
+restatement of the paper's equations) on the host cores, on a bounded sample of
+the same workload's centres per step; under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "NN-potential energy+force atom-evals/s at 1 GB300; p50/p99 request latency"
+UNIT = "atom-evals/s"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+WORKLOAD_DESC = {
+    "water9000": "water9000: 3000 rigid waters (O-H 0.96 A, 104.5 deg) on a jittered lattice, "
+                 "9000 atoms, periodic cubic box 44.77 A (1 g/cm^3); 4-species 384-dim AEV "
+                 "(16 radial shells Rc 5.2 A, 4x8 angular terms Rc 3.5 A); per-species networks "
+                 "384-160-128-96-1 CELU; energy+forces per call",
+    "solvated100k": "solvated100k: 1000-atom branched solute in 33,000 waters, 100,000 atoms, "
+                    "periodic 99.9 A box; 7-species 1008-dim AEV; 8 networks 1008-256-192-160-1",
+    "gas24": "gas24: one 24-atom molecule (H12 C7 N3 O2), non-periodic",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water9000")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ peaks and roofline
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    """FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP per clock."""
+    return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def stage_work(stage, spec, counts, n_atoms, precision):
+    """Algorithmic work of one launch of a stage: (amount, unit, bound).
+
+    counts: mean radial neighbours n_r and angular neighbours n_a per atom.
+    Bytes are compulsory DRAM traffic; FLOPs count the arithmetic the equations
+    require ('Roofline accounting')."""
+    D = spec.widths[0]
+    E = spec.n_ensemble
+    h1, h2, h3 = spec.widths[1:4]
+    nr, na = counts
+    tri = na * (na - 1) / 2.0
+    if stage == "aev_fwd":
+        flops = n_atoms * (nr * 16 * 5 + tri * 200)
+        return flops, "FLOP", "alu"
+    if stage == "aev_bwd":
+        flops = n_atoms * (nr * 16 * 8 + tri * 330)
+        return flops, "FLOP", "alu"
+    if stage == "neighbors":
+        return n_atoms * (16 + 4 * (nr + na) + 32), "B", "hbm"
+    gemm = {"mlp_l1": (D, E * h1), "mlp_l2": (h1, h2 * E), "mlp_l3": (h2, h3 * E),
+            "mlp_b3": (h3, h2 * E), "mlp_b2": (h2, h1 * E), "mlp_b1": (E * h1, D)}
+    if stage in gemm:
+        k, n = gemm[stage]
+        return 2.0 * n_atoms * k * n, "FLOP", ("tensor" if precision == "bf16" else "alu")
+    return None
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """SM clock and clock-event reasons sampled during the timed region.
+
+    Reads NVML directly (read-only queries, ~1 ms period) so that short timed
+    regions still get samples; falls back to `nvidia-smi -lms 100`."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid, index):
+        self.samples = []       # (time, sm_mhz, max_mhz, reasons_bitmask)
+        self.stop_flag = threading.Event()
+        self.nvml = None
+        self.proc = None
+        try:
+            import ctypes
+            L = ctypes.CDLL("libnvidia-ml.so.1")
+            if L.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                ok = -1
+                if uuid:
+                    ok = L.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h))
+                if ok != 0:
+                    ok = L.nvmlDeviceGetHandleByIndex_v2(int(index), ctypes.byref(h))
+                if ok == 0:
+                    self.nvml, self.h, self.ct = L, h, ctypes
+        except OSError:
+            self.nvml = None
+
+    def _poll_nvml(self):
+        ct, L, h = self.ct, self.nvml, self.h
+        mhz, mx, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        get_r = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            L.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_flag.is_set():
+            L.nvmlDeviceGetClockInfo(h, 1, ct.byref(mhz))
+            L.nvmlDeviceGetMaxClockInfo(h, 1, ct.byref(mx))
+            get_r(h, ct.byref(rs))
+            self.samples.append((time.time(), mhz.value, mx.value, rs.value))
+            time.sleep(0.001)
+
+    def _read_smi(self):
+        for line in self.proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            try:
+                bits = 0
+                for bit, v in zip((0x8, 0x40, 0x20, 0x4), f[5:9]):
+                    if v.lower() == "active":
+                        bits |= bit
+                self.samples.append((time.time(), float(f[1]), float(f[2]), bits))
+            except (ValueError, IndexError):
+                pass
+
+    def start(self):
+        if self.nvml is not None:
+            self.t = threading.Thread(target=self._poll_nvml, daemon=True)
+            self.t.start()
+            return
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read_smi, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        self.stop_flag.set()
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if getattr(self, "t", None) is not None:
+            self.t.join(timeout=2)
+
+    def summary(self, t0, t1):
+        sel = [s for s in self.samples if t0 <= s[0] <= t1]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        reasons = set()
+        for s in sel:
+            for bit, name in self.REASONS.items():
+                if s[3] & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(s[1] for s in sel),
+                "sm_max_mhz": max(s[2] for s in sel), "reasons": sorted(reasons),
+                "samples": len(sel), "source": "nvml" if self.nvml is not None else "nvidia-smi"}
+
+
+# ------------------------------------------------------------------ reference arm (oracle)
+def oracle_sample_rate(workload, n_centres, reps, seed=0):
+    import oracle
+    systems, kind, wseed = synth.workload(workload)
+    s = systems[0]
+    spec = synth.model_spec(kind)
+    m = oracle.Model(spec, synth.make_weights(spec, wseed))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    times = []
+    for _ in range(reps):
+        c = rng.choice(s.n_ml, size=min(n_centres, s.n_ml), replace=False)
+        t0 = time.perf_counter()
+        m.energy_forces_centres(s.coords, s.species, c, s.box, s.mask)
+        times.append(time.perf_counter() - t0)
+    return len(c), times
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_c = 500
+    n, times = oracle_sample_rate(args.workload, n_c, args.warmup + args.steps)
+    t = times[args.warmup:]
+    value = n * len(t) / sum(t)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload),
+                   "sample": f"{n} random centres per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n} centres of {args.workload} per step, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    from paper_2207_14276_gb300 import Potential
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    systems, kind, wseed = synth.workload(args.workload)
+    spec = synth.model_spec(kind)
+    w = synth.make_weights(spec, wseed)
+    pot = Potential(spec, w, precision=args.precision)
+    s = systems[0]
+    x = torch.from_numpy(s.coords).to(dev)
+    sp = torch.from_numpy(s.species).to(dev)
+    mask = None if s.mask is None else torch.from_numpy(s.mask).to(dev)
+    box = None if s.box is None else [float(b) for b in s.box]
+    n_eval = s.n_ml
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    F = torch.empty((s.n_atoms, 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # first call establishes the neighbour capacity (grows and retries if needed)
+    pot.energy_forces(x, sp, box, mask)
+    for _ in range(args.warmup):
+        pot.energy_forces_into(x, sp, box, mask, E, F)
+    assert pot.sync_status() == 0
+    launches_per_step = pot.launch_count()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # neighbour statistics for the roofline accounting
+    nb_r = pot.debug_neighbors(s.n_atoms, angular=False).ne(-1).sum(1).float()
+    nb_a = pot.debug_neighbors(s.n_atoms, angular=True).ne(-1).sum(1).float()
+    sel = torch.ones(s.n_atoms, dtype=torch.bool, device=dev) if mask is None else mask.bool()
+    counts = (float(nb_r[sel].mean()), float(nb_a[sel].mean()))
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    uuid = ("GPU-" + str(uuid)) if uuid is not None else None
+    clocks = ClockSampler(uuid, local)
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    pot.profile_read(reset=True)
+    pot.profile(True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)        # evict the previous step's data from L2
+        starts[k].record(stream)
+        pot.energy_forces_into(x, sp, box, mask, E, F)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t1 = time.time()
+    pot.profile(False)
+    clocks.stop()
+    rc = pot.sync_status()
+    if rc != 0:
+        raise RuntimeError(f"device status {rc} after the timed region")
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    stages = pot.profile_read(reset=True)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n_eval * args.steps * world / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (largest stage time over the timed region)
+    peaks, peak_src = measured_peaks()
+    clk = clocks.summary(t0, t1)
+    dom = max((k for k in stages if stages[k][1] > 0), key=lambda k: stages[k][0])
+    dom_ms = stages[dom][0] / stages[dom][1]
+    work = stage_work(dom, spec, counts, n_eval, args.precision)
+    roof = None
+    if work is not None:
+        amount, unit, bound = work
+        if unit == "B":
+            achieved = amount / (dom_ms / 1e3) / 1e9
+            peak = float(peaks["hbm_gbs"])
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None}
+        elif bound == "tensor":
+            achieved = amount / (dom_ms / 1e3) / 1e12
+            peak = float(peaks["bf16_tflops"])
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None}
+        else:
+            achieved = amount / (dom_ms / 1e3) / 1e12
+            peak = fp32_alu_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None}
+        roof.update({"kernel": dom, "launch_ms": dom_ms, "peak_source": peak_src,
+                     "work_per_launch": amount, "work_unit": unit})
+
+    # end to end through the host entry point (pinned host buffers, copies inside)
+    e2e = None
+    if args.e2e_steps > 0:
+        hx = torch.from_numpy(s.coords).pin_memory().numpy()
+        hs = torch.from_numpy(s.species).pin_memory().numpy()
+        hm = None if s.mask is None else torch.from_numpy(s.mask).pin_memory().numpy()
+        hF = torch.empty((s.n_atoms, 3), dtype=torch.float32).pin_memory().numpy()
+        for _ in range(2):
+            pot.energy_forces_host_into(hx, hs, s.box, hm, out_forces=hF)
+        e2e_t = []
+        for _ in range(args.e2e_steps):
+            t_a = time.perf_counter()
+            pot.energy_forces_host_into(hx, hs, s.box, hm, out_forces=hF)
+            e2e_t.append(time.perf_counter() - t_a)
+        h2d = s.n_atoms * 12 + s.n_atoms + (s.n_atoms if s.mask is not None else 0)
+        e2e = {"value": n_eval * len(e2e_t) / sum(e2e_t), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + s.n_atoms * 12,
+               "p50_ms": 1e3 * float(np.percentile(e2e_t, 50)),
+               "p99_ms": 1e3 * float(np.percentile(e2e_t, 99))}
+        if dist is not None:
+            t = torch.tensor([e2e["value"]], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MIN)
+            e2e["value"] = float(t.item()) * world
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        n_c, times = oracle_sample_rate(args.workload, 1000, 4, seed=1)
+        cpu = {"value": n_c * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} x {n_c} random centres of {args.workload} "
+                         f"(energy + forces of their terms), FP64, single thread"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "bf16-mlp/f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload),
+                   "atoms_per_step": n_eval, "systems_per_step": 1,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (512 MB write)", "precision": args.precision},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": launches_per_step * args.steps,
+        "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1]},
+        "neighbours_per_atom": {"radial": counts[0], "angular": counts[1]},
+    }
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

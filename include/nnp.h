@@ -1,0 +1,237 @@
+/*
+ * nnp.h -- C ABI of the GB300 (sm_103a) neural-network-potential library.
+ *
+ * The library evaluates an ANI-style neural-network potential (arXiv
+ * 2207.14276, Sec. "Neural Network Potentials", Eqs. 2-5) and its analytic
+ * forces on one GPU:
+ *   cell-list neighbour search under a cutoff  ->  atomic environment vectors
+ *   (radial Gaussian shells, Eq. 4, and angular triplet terms, Eq. 5, with the
+ *   cosine cutoff of Eq. 3; one radial block per species and one angular block
+ *   per unordered species pair)  ->  one feed-forward network per species,
+ *   summed to the energy (Eq. 2)  ->  analytic backward to per-atom forces.
+ * The hybrid model of Eq. 7 is supported through a per-atom mask: only masked
+ * atoms (the solute region P) are centres or neighbours, which yields V_ML(P).
+ *
+ * As in the paper's engine interface (Sec. "A General Machine Learning
+ * Platform": positions in, energies and forces out, device pointers handed
+ * over without copies), inputs and outputs are caller-owned DEVICE pointers
+ * and every compute call is asynchronous on the caller's CUDA stream.  Only
+ * nnp_energy_forces_host takes host buffers.
+ *
+ * Units: Angstrom, kcal/mol, kcal/mol/Angstrom.
+ *
+ * Errors: every call returns an NNP_* status code and never aborts;
+ * nnp_last_error() gives a thread-local message for the last failure.
+ * Conditions that only the device can see (a species index out of range, a
+ * non-finite coordinate, a neighbour list over capacity) are recorded in a
+ * device status word of the handle and reported by nnp_sync_status().
+ *
+ * Concurrency: a handle owns one work arena.  Calls on one handle must be
+ * ordered on one stream (or otherwise serialised by the caller); to overlap
+ * work on two streams use two handles (nnp_clone shares the weights).
+ */
+#ifndef NNP_H
+#define NNP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+  NNP_OK = 0,
+  NNP_ERR_ARG = 1,            /* bad argument (null pointer, negative size, ...)      */
+  NNP_ERR_SPECIES = 2,        /* a species index >= n_species (device-detected)       */
+  NNP_ERR_BOX_TOO_SMALL = 3,  /* periodic edge < 2 * max cutoff (minimum image fails)  */
+  NNP_ERR_NONFINITE = 4,      /* NaN/Inf coordinate in the ML region (device-detected) */
+  NNP_ERR_CAPACITY = 5,       /* neighbour list over capacity; capacity has been grown,
+                                 repeat the call                                       */
+  NNP_ERR_OOM = 6,            /* device allocation failed / over the HBM budget        */
+  NNP_ERR_CUDA = 7,           /* a CUDA runtime call failed                            */
+  NNP_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up                    */
+  NNP_PENDING = 9,            /* result not ready yet                                  */
+  NNP_ERR_UNSUPPORTED = 10    /* hyper-parameters outside what the kernels implement   */
+};
+
+/* precision of the per-species networks */
+enum {
+  NNP_FP32 = 0,      /* FP32 everywhere; FP64 energy / virial reductions               */
+  NNP_BF16_MLP = 1   /* network layers on tcgen05 tensor cores, BF16 operands and
+                        FP32 accumulation; AEVs and their backward stay FP32            */
+};
+
+typedef struct nnp_handle nnp_handle;
+
+/* Species handled by the model; index order is the AEV block order (the paper's
+ * ANI models: H,C,N,O and, for ANI-2x, S,F,Cl).  n_species <= 8. */
+typedef struct {
+  int n_species;
+  int atomic_numbers[8];
+} nnp_species_t;
+
+/* AEV hyper-parameters (Eqs. 3-5).  rc_r / rc_a: radial / angular cutoff radii;
+ * eta_r, shf_r[]: radial Gaussian width and centres; eta_a, shf_a[]: Gaussian of
+ * the averaged distance in the angular term; zeta and shf_z[] (theta_s values, in
+ * radians): angular factor (1 + cos(theta - theta_s))^zeta with the 2^(1-zeta)
+ * prefactor; theta = acos(cos_scale * cos_angle) (cos_scale = 1 is the paper's
+ * form).  The kernels implement n_shf_r = 16, n_shf_a = 4, n_shf_z = 8 and an
+ * integer zeta in [1, 64]; anything else returns NNP_ERR_UNSUPPORTED. */
+typedef struct {
+  float rc_r, eta_r;
+  int n_shf_r;
+  float shf_r[32];
+  float rc_a, eta_a, zeta;
+  int n_shf_a;
+  float shf_a[16];
+  int n_shf_z;
+  float shf_z[16];
+  float cos_scale;
+} nnp_aev_params_t;
+
+/* Per-species feed-forward networks (Eq. 2; one per species and ensemble member,
+ * CELU activations between layers, linear output of width 1).
+ * widths[0] must equal the AEV length S*n_shf_r + S(S+1)/2*n_shf_a*n_shf_z and
+ * widths[n_layers] must be 1; n_layers = 4 is implemented.
+ * params: host FP32, flat, copied at nnp_create:
+ *   for e < n_ensemble, for s < n_species, for l < n_layers:
+ *       W_l row-major [widths[l+1], widths[l]], then b_l [widths[l+1]]
+ * species_shift: host [n_species] energy added per atom (NULL = zeros).
+ * The ensemble energy is the arithmetic mean of the members. */
+typedef struct {
+  int n_ensemble;
+  int n_layers;
+  const int* widths;
+  const float* params;
+  const double* species_shift;
+  float celu_alpha;
+} nnp_weights_t;
+
+/* One system of a batched call.  All pointers are device pointers owned by the
+ * caller.  coords [n_atoms,3] float32; species [n_atoms] uint8 (< n_species);
+ * mask [n_atoms] uint8, 1 = atom is in the ML region, NULL = all atoms;
+ * periodic != 0: orthorhombic box of edges box[3] with the minimum-image
+ * convention (each edge >= 2 * max(rc_r, rc_a)); otherwise box is ignored.
+ * Outputs: energy (1 double, written), forces [n_atoms,3] (written; zero for
+ * atoms outside the mask), virial [9] row-major -sum_edges u (x) dE/du (NULL =
+ * not computed), atom_energies [n_atoms] float (NULL = not written; zero
+ * outside the mask). */
+typedef struct {
+  int64_t n_atoms;
+  const float* coords;
+  const uint8_t* species;
+  const uint8_t* mask;
+  double box[3];
+  int periodic;
+  double* energy;
+  float* forces;
+  double* virial;
+  float* atom_energies;
+} nnp_system_t;
+
+/* Create a model.  Copies the parameters to the device (weights are owned by the
+ * library).  hbm_budget_bytes bounds the work arena (0 = no bound); the arena is
+ * grown on demand in proportion to the number of atoms, as in the paper's
+ * bounded upfront buffer (Sec. "Massive Parallelism within Tinker-HP").
+ * precision: NNP_FP32 or NNP_BF16_MLP.  On success *out holds the handle. */
+int nnp_create(const nnp_species_t* species, const nnp_aev_params_t* aev,
+               const nnp_weights_t* weights, int precision, size_t hbm_budget_bytes,
+               nnp_handle** out);
+
+/* A second handle on the same device weights with its own work arena, for
+ * overlapping calls on another stream.  Destroy each handle separately. */
+int nnp_clone(const nnp_handle* h, nnp_handle** out);
+
+void nnp_destroy(nnp_handle* h);
+
+/* Pre-size the work arena for up to max_atoms atoms in one call (all systems of
+ * a batch together), max_systems systems per batch and the given neighbour
+ * capacities per atom (0 keeps the current value; at most 512 radial neighbours
+ * per atom are supported, more returns NNP_ERR_UNSUPPORTED).  Synchronises the device.
+ * Calls that stay within the reservation allocate nothing. */
+int nnp_reserve(nnp_handle* h, int64_t max_atoms, int max_systems, int max_neighbors_radial,
+                int max_neighbors_angular);
+
+/* Energy and forces of one system (Eqs. 2-5; Eq. 7 with a mask), asynchronous on
+ * `stream` (a cudaStream_t, NULL = legacy default stream).
+ *   coords   device float32 [n_atoms,3]
+ *   species  device uint8 [n_atoms]
+ *   box_host host double[3] orthorhombic edges, NULL = non-periodic
+ *   mask     device uint8 [n_atoms] or NULL
+ *   energy   device double[1]; forces device float32 [n_atoms,3];
+ *   virial   device double[9] or NULL
+ * Returns NNP_OK once the work is enqueued; device-side failures are read with
+ * nnp_sync_status. */
+int nnp_energy_forces(nnp_handle* h, int64_t n_atoms, const float* coords,
+                      const uint8_t* species, const double* box_host, const uint8_t* mask,
+                      double* energy, float* forces, double* virial, void* stream);
+
+/* Batched evaluation of n_sys independent systems (molecules, replicas, lambda
+ * windows) in one pass: all systems' atoms share the neighbour, AEV and network
+ * kernels, so small systems fill the GPU together.  `systems` is a HOST array of
+ * descriptors holding device pointers.  Asynchronous like nnp_energy_forces. */
+int nnp_energy_forces_batch(nnp_handle* h, int n_sys, const nnp_system_t* systems,
+                            void* stream);
+
+/* End-to-end convenience for host callers: host buffers in and out, copies to
+ * and from the device inside, synchronous.  coords_h [n,3] float32, species_h
+ * [n] uint8, mask_h [n] or NULL, box_host double[3] or NULL; energy_h double[1],
+ * forces_h float32 [n,3], virial_h double[9] or NULL.  Retries once after a
+ * capacity overflow. */
+int nnp_energy_forces_host(nnp_handle* h, int64_t n_atoms, const float* coords_h,
+                           const uint8_t* species_h, const double* box_host,
+                           const uint8_t* mask_h, double* energy_h, float* forces_h,
+                           double* virial_h);
+
+/* Synchronise `stream`, read and clear the handle's device status word.  Returns
+ * NNP_OK or the first device-detected error since the last check
+ * (NNP_ERR_SPECIES, NNP_ERR_NONFINITE, NNP_ERR_CAPACITY, NNP_ERR_TIMEOUT).  After
+ * NNP_ERR_CAPACITY the neighbour capacity has already been grown to what the
+ * failed call needed, so repeating the call succeeds. */
+int nnp_sync_status(nnp_handle* h, void* stream);
+
+/* Length of the atomic environment vector. */
+int nnp_aev_dim(const nnp_handle* h);
+
+/* Number of kernels the last compute call enqueued (for launch accounting). */
+int nnp_last_launch_count(const nnp_handle* h);
+
+/* Per-stage timing with CUDA events recorded on the caller's stream around the
+ * kernels of each stage (prep, neighbors, aev_fwd, mlp_l1 .. mlp_b1, aev_bwd,
+ * finalize, mlp_cvt).  nnp_profile(h, 1) enables recording for later calls;
+ * nnp_profile_read synchronises the recorded events, adds their durations to
+ * per-stage totals and copies up to max_stages totals (milliseconds) and event
+ * pair counts into ms_out / calls_out (either may be NULL); *n_stages receives
+ * the number of stages; reset != 0 clears the totals afterwards.
+ * nnp_profile_stage_name(i) names stage i. */
+int nnp_profile(nnp_handle* h, int enable);
+int nnp_profile_read(nnp_handle* h, int reset, double* ms_out, long long* calls_out,
+                     int max_stages, int* n_stages);
+const char* nnp_profile_stage_name(int i);
+
+/* Thread-local description of the last error (empty string if none). */
+const char* nnp_last_error(void);
+
+/* ---------------------------------------------------------------- diagnostics
+ * Read back intermediate results of the LAST compute call on this handle (for
+ * parity tests against a reference implementation).  Asynchronous on `stream`;
+ * the handle's arena must not have been reused by a later call.
+ *
+ * nnp_debug_rows: which = 0 -> atomic environment vectors G_i (Eqs. 4-5),
+ *   which = 1 -> dE/dG_i (the network gradient fed to the force kernel).
+ *   out: device float32 [n_in_total, aev_dim], row i = input atom i of the
+ *   batch (systems concatenated in call order); rows of atoms outside the
+ *   mask are left untouched.
+ * nnp_debug_neighbors: out: device int32 [n_in_total, cap]; out[i][t] is the
+ *   batch input index of the t-th neighbour of atom i (radial cutoff list, or
+ *   the angular-cutoff sub-list if angular != 0), -1 past the end; rows of
+ *   atoms outside the mask are left untouched. */
+int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream);
+int nnp_debug_neighbors(nnp_handle* h, int angular, int cap, int* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNP_H */

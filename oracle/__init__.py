@@ -50,6 +50,8 @@ def _load():
         lib.oracle_energy_forces.argtypes = [P, i, P, P, P, P, P, P, P, P, P, P]
         lib.oracle_force_matching.restype = d
         lib.oracle_force_matching.argtypes = [P, i, P, P, P, P, P, P, P, P]
+        lib.oracle_energy_forces_centres.restype = d
+        lib.oracle_energy_forces_centres.argtypes = [P, i, P, P, P, P, i, P, P]
         lib.oracle_sample.restype = None
         lib.oracle_sample.argtypes = [P, i, P, P, P, P, i, P, P, P, P]
         _lib = lib
@@ -135,6 +137,18 @@ class Model:
                                           _ptr(_f64(box)), _ptr(_u8(mask)), _ptr(vv),
                                           _ptr(F), _ptr(gx), _ptr(gw))
         return E, F, gx, gw
+
+    def energy_forces_centres(self, coords, species, centres, box=None, mask=None):
+        """Energy of the listed centres and the forces of their terms (a bounded sample
+        of the full evaluation with the same work per centre)."""
+        x = _f64(coords)
+        n = x.shape[0]
+        c = np.ascontiguousarray(centres, dtype=np.int32)
+        F = np.zeros((n, 3))
+        E = _load().oracle_energy_forces_centres(self._h, n, _ptr(x), _ptr(_u8(species)),
+                                                 _ptr(_f64(box)), _ptr(_u8(mask)), c.shape[0],
+                                                 _ptr(c), _ptr(F))
+        return E, F
 
     def sample(self, coords, species, idx, box=None, mask=None, want_aev=False):
         """Per-atom energies, forces and (optionally) AEV rows of the atoms in idx."""

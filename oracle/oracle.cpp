@@ -329,7 +329,8 @@ void aev_backward_centre(const Model& m, int i, const std::vector<Nb<T>>& nb, co
 // E = sum_i [ mean_e net_{e,s_i}(G_i) + shift_{s_i} ] over the atoms in the mask
 template <class T>
 T energy_forces(const Model& m, int n, const T* xyz, const uint8_t* sp, const double* box,
-                const uint8_t* mask, T* forces, T* vir, T* atom_e, T* aev_out, T* dEdG_out, T* dEdW) {
+                const uint8_t* mask, T* forces, T* vir, T* atom_e, T* aev_out, T* dEdG_out, T* dEdW,
+                const int32_t* centres = nullptr, int n_centres = -1) {
   const int D = m.D();
   const double rc = std::max(m.rc_r, m.rc_a);
   std::vector<T> dEdx(3 * (size_t)n, T(0.0)), G(D), dG(D);
@@ -337,8 +338,11 @@ T energy_forces(const Model& m, int n, const T* xyz, const uint8_t* sp, const do
     for (int k = 0; k < 9; ++k) vir[k] = T(0.0);
   T E = T(0.0);
   Tape<T> tp;
-  for (int i = 0; i < n; ++i) {
-    if (atom_e) atom_e[i] = T(0.0);
+  if (atom_e)
+    for (int i = 0; i < n; ++i) atom_e[i] = T(0.0);
+  const int n_loop = centres ? n_centres : n;
+  for (int t = 0; t < n_loop; ++t) {
+    const int i = centres ? centres[t] : t;
     if (mask && !mask[i]) continue;
     auto nb = neighbours_of(i, n, xyz, box, mask, rc);
     aev_centre(m, nb, sp, G.data());
@@ -524,6 +528,16 @@ double oracle_force_matching(void* mp, int n, const double* xyz, const uint8_t* 
   }
   for (size_t k = 0; k < m.flat.size(); ++k) dLdw[k] = -dW[k].d;
   return E.v;
+}
+
+// energy of a subset of centres and the forces of their terms only (the same
+// per-centre work as the full sum; used to time the oracle on a bounded sample)
+double oracle_energy_forces_centres(void* mp, int n, const double* xyz, const uint8_t* sp,
+                                    const double* box, const uint8_t* mask, int n_centres,
+                                    const int32_t* centres, double* forces) {
+  const Model& m = *static_cast<Model*>(mp);
+  return energy_forces<double>(m, n, xyz, sp, box, mask, forces, nullptr, nullptr, nullptr,
+                               nullptr, nullptr, centres, n_centres);
 }
 
 // sampled evaluation for large systems: per-atom energies, AEV rows and forces

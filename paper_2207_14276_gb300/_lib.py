@@ -1,0 +1,115 @@
+"""ctypes view of libnnp.so (declarations mirror include/nnp.h).
+
+The shared library is built in-tree by ``paper_2207_14276_gb300.build``.  There
+is no fallback: if the library is missing or cannot be loaded, every entry
+point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnnp.so")
+
+NNP_OK = 0
+NNP_ERR_ARG = 1
+NNP_ERR_SPECIES = 2
+NNP_ERR_BOX_TOO_SMALL = 3
+NNP_ERR_NONFINITE = 4
+NNP_ERR_CAPACITY = 5
+NNP_ERR_OOM = 6
+NNP_ERR_CUDA = 7
+NNP_ERR_TIMEOUT = 8
+NNP_PENDING = 9
+NNP_ERR_UNSUPPORTED = 10
+NNP_FP32 = 0
+NNP_BF16_MLP = 1
+
+STATUS_NAMES = {
+    0: "NNP_OK", 1: "NNP_ERR_ARG", 2: "NNP_ERR_SPECIES", 3: "NNP_ERR_BOX_TOO_SMALL",
+    4: "NNP_ERR_NONFINITE", 5: "NNP_ERR_CAPACITY", 6: "NNP_ERR_OOM", 7: "NNP_ERR_CUDA",
+    8: "NNP_ERR_TIMEOUT", 9: "NNP_PENDING", 10: "NNP_ERR_UNSUPPORTED",
+}
+
+# every symbol include/nnp.h declares (checked by the CPU test-suite)
+EXPORTS = (
+    "nnp_create", "nnp_clone", "nnp_destroy", "nnp_reserve", "nnp_energy_forces",
+    "nnp_energy_forces_batch", "nnp_energy_forces_host", "nnp_sync_status", "nnp_aev_dim",
+    "nnp_last_launch_count", "nnp_last_error", "nnp_debug_rows", "nnp_debug_neighbors",
+    "nnp_profile", "nnp_profile_read", "nnp_profile_stage_name",
+)
+
+
+class NNPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SpeciesT(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int), ("atomic_numbers", ctypes.c_int * 8)]
+
+
+class AevParamsT(ctypes.Structure):
+    _fields_ = [("rc_r", ctypes.c_float), ("eta_r", ctypes.c_float), ("n_shf_r", ctypes.c_int),
+                ("shf_r", ctypes.c_float * 32), ("rc_a", ctypes.c_float),
+                ("eta_a", ctypes.c_float), ("zeta", ctypes.c_float), ("n_shf_a", ctypes.c_int),
+                ("shf_a", ctypes.c_float * 16), ("n_shf_z", ctypes.c_int),
+                ("shf_z", ctypes.c_float * 16), ("cos_scale", ctypes.c_float)]
+
+
+class WeightsT(ctypes.Structure):
+    _fields_ = [("n_ensemble", ctypes.c_int), ("n_layers", ctypes.c_int),
+                ("widths", ctypes.POINTER(ctypes.c_int)), ("params", ctypes.POINTER(ctypes.c_float)),
+                ("species_shift", ctypes.POINTER(ctypes.c_double)), ("celu_alpha", ctypes.c_float)]
+
+
+class SystemT(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("coords", ctypes.c_void_p),
+                ("species", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("box", ctypes.c_double * 3), ("periodic", ctypes.c_int),
+                ("energy", ctypes.c_void_p), ("forces", ctypes.c_void_p),
+                ("virial", ctypes.c_void_p), ("atom_energies", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libnnp.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libnnp.so not found at {LIB_PATH}: run paper_2207_14276_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    L.nnp_create.argtypes = [ctypes.POINTER(SpeciesT), ctypes.POINTER(AevParamsT),
+                             ctypes.POINTER(WeightsT), i, sz, ctypes.POINTER(P)]
+    L.nnp_clone.argtypes = [P, ctypes.POINTER(P)]
+    L.nnp_destroy.argtypes = [P]
+    L.nnp_destroy.restype = None
+    L.nnp_reserve.argtypes = [P, i64, i, i, i]
+    L.nnp_energy_forces.argtypes = [P, i64, P, P, P, P, P, P, P, P]
+    L.nnp_energy_forces_batch.argtypes = [P, i, ctypes.POINTER(SystemT), P]
+    L.nnp_energy_forces_host.argtypes = [P, i64, P, P, P, P, P, P, P]
+    L.nnp_sync_status.argtypes = [P, P]
+    L.nnp_aev_dim.argtypes = [P]
+    L.nnp_last_launch_count.argtypes = [P]
+    L.nnp_last_error.restype = ctypes.c_char_p
+    L.nnp_last_error.argtypes = []
+    L.nnp_debug_rows.argtypes = [P, i, P, P]
+    L.nnp_debug_neighbors.argtypes = [P, i, i, P, P]
+    L.nnp_profile.argtypes = [P, i]
+    L.nnp_profile_read.argtypes = [P, i, P, P, i, P]
+    L.nnp_profile_stage_name.restype = ctypes.c_char_p
+    L.nnp_profile_stage_name.argtypes = [i]
+    _lib = L
+    return L
+
+
+def check(code):
+    if code != NNP_OK:
+        raise NNPError(code, lib().nnp_last_error().decode())
+    return code

@@ -1,0 +1,709 @@
+// Host runtime and C ABI of libnnp (declared in include/nnp.h).
+//
+// A handle = shared device model (AEV constants + network weights in the
+// layouts the kernels read) + its own bounded work arena.  The arena is one
+// device allocation carved into the buffers of a batch, sized in proportion to
+// the number of atoms (the paper's upfront bounded buffer); it only grows, and
+// only between calls.  Every compute call enqueues the kernel chain on the
+// caller's stream without host synchronisation.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/nnp.h"
+#include "mlp.cuh"
+#include "nnp_internal.cuh"
+
+using namespace nnp;
+
+namespace nnp {
+void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st);
+int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
+                  float alpha, cudaStream_t st, int* n_launch, StageHook* hook);
+int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, int row_cap,
+                   const float* aev, float* dEdG, void** state);
+void mlp_tc_release(void* state);
+void launch_aev_to_bf16(const Ws& ws, int n_in, const AevConst& ac, void* out, cudaStream_t st);
+}  // namespace nnp
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CU_TRY(x)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (x);                                                           \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(NNP_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Model {
+  std::atomic<int> refs{1};
+  int device = 0;
+  int precision = NNP_FP32;
+  AevConst ac{};
+  MlpDims md{};
+  float alpha = 0.1f;
+  MlpWeights mw{};
+  double* ebias = nullptr;  // device [S]
+  std::vector<void*> allocs;
+  ~Model() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+struct nnp_handle {
+  Model* model = nullptr;
+  size_t budget = 0;
+  // arena
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  int cap_in = 0, cap_sys = 0, cap_r = 128, cap_a = 48;
+  bool dirty = true;  // capacities changed: re-carve before the next call
+  Ws ws{};
+  MlpBufs mb{};
+  int* status_host = nullptr;  // pinned [4]
+  int last_launches = 0;
+  int last_n_in = 0;
+  void* tc_state = nullptr;
+  // host-call staging
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  // optional per-stage CUDA-event timing
+  bool profile = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[32] = {0};
+  long long prof_calls[32] = {0};
+};
+
+namespace {
+
+// ---------------------------------------------------------------- model setup
+int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
+                const nnp_weights_t* w, int precision) {
+  if (!sp || !a || !w) return fail(NNP_ERR_ARG, "null argument");
+  const int S = sp->n_species;
+  if (S < 1 || S > kMaxSpecies) return fail(NNP_ERR_ARG, "n_species must be in [1, 8]");
+  if (a->n_shf_r != kNR || a->n_shf_a != kNA || a->n_shf_z != kNZ)
+    return fail(NNP_ERR_UNSUPPORTED, "kernels implement 16 radial, 4 angular-distance and 8 angle shells");
+  const double zr = std::round((double)a->zeta);
+  if (std::fabs(a->zeta - zr) > 0 || zr < 1 || zr > 64)
+    return fail(NNP_ERR_UNSUPPORTED, "zeta must be an integer in [1, 64]");
+  if (!(a->rc_r > 0) || !(a->rc_a > 0) || !(a->eta_r > 0) || !(a->eta_a > 0))
+    return fail(NNP_ERR_ARG, "cutoffs and widths must be positive");
+  if (a->rc_a > a->rc_r) return fail(NNP_ERR_UNSUPPORTED, "angular cutoff must not exceed the radial one");
+  if (!(a->cos_scale > 0) || a->cos_scale > 1) return fail(NNP_ERR_ARG, "cos_scale must be in (0, 1]");
+  if (w->n_layers != 4 || !w->widths || !w->params || w->n_ensemble < 1)
+    return fail(NNP_ERR_UNSUPPORTED, "networks must have 4 layers");
+  if (precision != NNP_FP32 && precision != NNP_BF16_MLP) return fail(NNP_ERR_ARG, "bad precision");
+  AevConst& ac = m->ac;
+  ac.S = S;
+  ac.D = S * kNR + S * (S + 1) / 2 * kNA * kNZ;
+  ac.Dp = (int)align_up(ac.D, 64);
+  ac.n_pairs = S * (S + 1) / 2;
+  ac.rc_r = a->rc_r; ac.rc_a = a->rc_a; ac.eta_r = a->eta_r; ac.eta_a = a->eta_a;
+  for (int r = 0; r < kNR; ++r) ac.shf_r[r] = a->shf_r[r];
+  for (int r = 0; r < kNA; ++r) ac.shf_a[r] = a->shf_a[r];
+  for (int z = 0; z < kNZ; ++z) {
+    ac.cos_z[z] = (float)std::cos((double)a->shf_z[z]);
+    ac.sin_z[z] = (float)std::sin((double)a->shf_z[z]);
+  }
+  ac.cos_scale = a->cos_scale;
+  ac.zeta = (int)zr;
+  ac.ang_pre = (float)std::pow(2.0, 1.0 - zr);
+  const int* wd = w->widths;
+  if (wd[0] != ac.D) return fail(NNP_ERR_ARG, "widths[0] must equal the AEV length");
+  if (wd[4] != 1) return fail(NNP_ERR_ARG, "output width must be 1");
+  for (int l = 1; l < 4; ++l)
+    if (wd[l] < 16 || wd[l] % 16 != 0 || wd[l] > 512)
+      return fail(NNP_ERR_UNSUPPORTED, "hidden widths must be multiples of 16 in [16, 512]");
+  MlpDims& md = m->md;
+  md.S = S; md.E = w->n_ensemble; md.Dp = ac.Dp; md.h1 = wd[1]; md.h2 = wd[2]; md.h3 = wd[3];
+  m->alpha = w->celu_alpha;
+  if (!(m->alpha > 0)) return fail(NNP_ERR_ARG, "celu_alpha must be positive");
+  m->precision = precision;
+  CU_TRY(cudaGetDevice(&m->device));
+
+  // unpack the flat parameter vector into the kernel layouts
+  const int E = md.E, D = ac.D, Dp = ac.Dp, h1 = md.h1, h2 = md.h2, h3 = md.h3;
+  std::vector<float> W1cat((size_t)S * E * h1 * Dp, 0.f), b1cat((size_t)S * E * h1);
+  std::vector<float> W2((size_t)E * S * h2 * h1), b2((size_t)E * S * h2);
+  std::vector<float> W3((size_t)E * S * h3 * h2), b3((size_t)E * S * h3);
+  std::vector<float> w4((size_t)E * S * h3), W3T((size_t)E * S * h2 * h3);
+  std::vector<float> W2T((size_t)E * S * h1 * h2), W1Tcat((size_t)S * Dp * E * h1, 0.f);
+  std::vector<double> ebias(S, 0.0);
+  const float* p = w->params;
+  for (int e = 0; e < E; ++e)
+    for (int s = 0; s < S; ++s) {
+      const float* L1 = p; p += (size_t)h1 * D;
+      const float* B1 = p; p += h1;
+      const float* L2 = p; p += (size_t)h2 * h1;
+      const float* B2 = p; p += h2;
+      const float* L3 = p; p += (size_t)h3 * h2;
+      const float* B3 = p; p += h3;
+      const float* L4 = p; p += h3;
+      const float* B4 = p; p += 1;
+      for (int o = 0; o < h1; ++o) {
+        for (int k = 0; k < D; ++k) {
+          W1cat[((size_t)s * E * h1 + e * h1 + o) * Dp + k] = L1[(size_t)o * D + k];
+          W1Tcat[((size_t)s * Dp + k) * E * h1 + e * h1 + o] = L1[(size_t)o * D + k] / (float)E;
+        }
+        b1cat[(size_t)s * E * h1 + e * h1 + o] = B1[o];
+      }
+      const size_t es = (size_t)e * S + s;
+      for (int o = 0; o < h2; ++o) {
+        for (int k = 0; k < h1; ++k) {
+          W2[(es * h2 + o) * h1 + k] = L2[(size_t)o * h1 + k];
+          W2T[(es * h1 + k) * h2 + o] = L2[(size_t)o * h1 + k];
+        }
+        b2[es * h2 + o] = B2[o];
+      }
+      for (int o = 0; o < h3; ++o) {
+        for (int k = 0; k < h2; ++k) {
+          W3[(es * h3 + o) * h2 + k] = L3[(size_t)o * h2 + k];
+          W3T[(es * h2 + k) * h3 + o] = L3[(size_t)o * h2 + k];
+        }
+        b3[es * h3 + o] = B3[o];
+        w4[es * h3 + o] = L4[o];
+      }
+      ebias[s] += (double)B4[0] / E;
+    }
+  for (int s = 0; s < S; ++s)
+    if (w->species_shift) ebias[s] += w->species_shift[s];
+
+  auto upload = [&](const void* src, size_t bytes, void** dst) -> int {
+    CU_TRY(cudaMalloc(dst, bytes));
+    m->allocs.push_back(*dst);
+    CU_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return NNP_OK;
+  };
+  auto upf = [&](const std::vector<float>& v, float** dst) {
+    return upload(v.data(), v.size() * sizeof(float), reinterpret_cast<void**>(dst));
+  };
+  int rc;
+  if ((rc = upf(W1cat, &m->mw.W1cat))) return rc;
+  if ((rc = upf(b1cat, &m->mw.b1cat))) return rc;
+  if ((rc = upf(W2, &m->mw.W2))) return rc;
+  if ((rc = upf(b2, &m->mw.b2))) return rc;
+  if ((rc = upf(W3, &m->mw.W3))) return rc;
+  if ((rc = upf(b3, &m->mw.b3))) return rc;
+  if ((rc = upf(w4, &m->mw.w4))) return rc;
+  if ((rc = upf(W3T, &m->mw.W3T))) return rc;
+  if ((rc = upf(W2T, &m->mw.W2T))) return rc;
+  if ((rc = upf(W1Tcat, &m->mw.W1Tcat))) return rc;
+  if ((rc = upload(ebias.data(), S * sizeof(double), reinterpret_cast<void**>(&m->ebias)))) return rc;
+  return NNP_OK;
+}
+
+// ---------------------------------------------------------------- arena
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <class T> T* take(size_t n) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+size_t carve(nnp_handle* h, char* base) {
+  const Model& m = *h->model;
+  const int S = m.ac.S, Dp = m.ac.Dp, E = m.md.E;
+  const size_t n = std::max(h->cap_in, 1);
+  const size_t nsys = std::max(h->cap_sys, 1);
+  const size_t cells = 2 * n + 27 * nsys;
+  const size_t rows = n + (size_t)S * kRowTile;
+  Carve c{base};
+  Ws& ws = h->ws;
+  ws.status = c.take<int>(4);
+  ws.sys = c.take<SysDev>(nsys);
+  ws.cell_cap = (int)cells;
+  ws.row_cap = (int)rows;
+  ws.cap_r = h->cap_r;
+  ws.cap_a = h->cap_a;
+  ws.species_count = c.take<int>(kMaxSpecies);
+  ws.species_fill = c.take<int>(kMaxSpecies);
+  ws.seg_start = c.take<int>(kMaxSpecies + 1);
+  ws.totals = c.take<int>(4);
+  ws.cell_count = c.take<int>(cells);
+  ws.cell_start = c.take<int>(cells + 1);
+  ws.in_cell = c.take<int>(n);
+  ws.in_rank = c.take<int>(n);
+  ws.in_slot = c.take<int>(n);
+  ws.in_sys = c.take<int>(n);
+  ws.xyzq = c.take<float4>(n);
+  ws.pos_src = c.take<int>(n);
+  ws.pos_slot = c.take<int>(n);
+  ws.pos_sys = c.take<int>(n);
+  ws.pos_cell = c.take<int>(n);
+  ws.slot_pos = c.take<int>(rows);
+  ws.nb_cnt = c.take<uint16_t>(n * 16);
+  ws.nb_r = c.take<int>(n * h->cap_r);
+  ws.nb_a = c.take<int>(n * h->cap_a);
+  ws.aev = c.take<float>(rows * Dp);
+  ws.dEdG = c.take<float>(rows * Dp);
+  ws.atom_e = c.take<float>(rows);
+  ws.f_pos = c.take<float4>(n);
+  const size_t esz = (m.precision == NNP_BF16_MLP) ? 2 : 4;
+  MlpBufs& mb = h->mb;
+  mb.H1 = c.take<char>(rows * E * m.md.h1 * esz);
+  mb.D1 = c.take<char>(rows * E * m.md.h1 * esz);
+  mb.H2 = c.take<char>(rows * E * m.md.h2 * esz);
+  mb.D2 = c.take<char>(rows * E * m.md.h2 * esz);
+  mb.d3 = c.take<char>(rows * E * m.md.h3 * esz);
+  mb.e_row = c.take<float>((size_t)E * rows);
+  mb.aev_h = (m.precision == NNP_BF16_MLP) ? c.take<char>(rows * Dp * 2) : nullptr;
+  return align_up(c.off, 256);
+}
+
+int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
+  if (!h->dirty && n_in <= h->cap_in && n_sys <= h->cap_sys) return NNP_OK;
+  int want_in = std::max(n_in, h->cap_in), want_sys = std::max(n_sys, h->cap_sys);
+  if (n_in > h->cap_in) want_in = std::max(n_in, (int)std::min<long long>(1LL << 30, (long long)h->cap_in * 5 / 4));
+  if (n_sys > h->cap_sys) want_sys = std::max(n_sys, h->cap_sys * 5 / 4);
+  const int old_in = h->cap_in, old_sys = h->cap_sys;
+  h->cap_in = want_in;
+  h->cap_sys = want_sys;
+  const size_t bytes = carve(h, nullptr);
+  if (h->budget && bytes > h->budget) {
+    h->cap_in = old_in;
+    h->cap_sys = old_sys;
+    carve(h, static_cast<char*>(h->arena));
+    return fail(NNP_ERR_OOM, "work arena of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
+  }
+  int* saved_status = nullptr;
+  if (h->arena) {
+    CU_TRY(cudaDeviceSynchronize());
+    saved_status = h->ws.status;
+    (void)saved_status;
+    if (h->tc_state) { mlp_tc_release(h->tc_state); h->tc_state = nullptr; }
+    cudaFree(h->arena);
+    h->arena = nullptr;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->cap_in = 0;
+    h->cap_sys = 0;
+    h->dirty = true;
+    return fail(NNP_ERR_OOM, "cudaMalloc of the work arena (" + std::to_string(bytes) + " bytes) failed");
+  }
+  CU_TRY(cudaMemset(p, 0, bytes));
+  h->arena = p;
+  h->arena_bytes = bytes;
+  carve(h, static_cast<char*>(p));
+  CU_TRY(aev_set_smem_limits(h->ws));
+  if (h->model->precision == NNP_BF16_MLP) {
+    int rc = mlp_tc_prepare(h->model->md, h->model->mw, h->mb, h->ws.row_cap, h->ws.aev,
+                            h->ws.dEdG, &h->tc_state);
+    if (rc) return rc;
+  }
+  h->dirty = false;
+  return NNP_OK;
+}
+
+// stage names (index = stage id) reported by nnp_profile_read
+const char* kStageNames[] = {"prep", "neighbors", "aev_fwd", "mlp_l1", "mlp_l2", "mlp_l3",
+                             "mlp_b3", "mlp_b2", "mlp_b1", "aev_bwd", "finalize", "mlp_cvt"};
+constexpr int kNumStages = 12;
+
+cudaEvent_t prof_event(nnp_handle* h) {
+  if (!h->prof_pool.empty()) {
+    cudaEvent_t e = h->prof_pool.back();
+    h->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// brackets the kernels of one stage with events on the launching stream
+struct StageTimer {
+  nnp_handle* h;
+  cudaStream_t st;
+  int id;
+  cudaEvent_t a = nullptr;
+  StageTimer(nnp_handle* h_, cudaStream_t st_, int id_) : h(h_), st(st_), id(id_) {
+    if (h->profile) { a = prof_event(h); cudaEventRecord(a, st); }
+  }
+  ~StageTimer() {
+    if (h->profile) {
+      cudaEvent_t b = prof_event(h);
+      cudaEventRecord(b, st);
+      h->prof_pending.push_back({id, {a, b}});
+    }
+  }
+};
+
+}  // namespace
+
+namespace nnp {
+void StageHook::begin(int id) {
+  nnp_handle* hh = static_cast<nnp_handle*>(h);
+  if (!hh->profile) return;
+  cudaEvent_t ev = prof_event(hh);
+  cudaEventRecord(ev, static_cast<cudaStream_t>(st));
+  cur = ev;
+  cur_id = id;
+}
+void StageHook::end() {
+  nnp_handle* hh = static_cast<nnp_handle*>(h);
+  if (!hh->profile || !cur) return;
+  cudaEvent_t b = prof_event(hh);
+  cudaEventRecord(b, static_cast<cudaStream_t>(st));
+  hh->prof_pending.push_back({cur_id, {static_cast<cudaEvent_t>(cur), b}});
+  cur = nullptr;
+}
+}  // namespace nnp
+
+namespace {
+
+void split_box(double L, float* hi, float* lo) {
+  *hi = (float)L;
+  *lo = (float)(L - (double)*hi);
+}
+
+// enqueue the whole chain for a batch whose descriptors are already validated
+int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st) {
+  const Model& m = *h->model;
+  long long n_in_ll = 0;
+  for (int b = 0; b < n_sys; ++b) n_in_ll += sy[b].n_atoms;
+  if (n_in_ll > (1LL << 30)) return fail(NNP_ERR_ARG, "too many atoms in one call");
+  const int n_in = (int)n_in_ll;
+  int rc = ensure_arena(h, n_in, n_sys);
+  if (rc) return rc;
+  Ws& ws = h->ws;
+  ws.n_sys = n_sys;
+  ws.n_in = n_in;
+  int launches = 0;
+  // systems without atoms: the outputs are the empty sums
+  for (int b = 0; b < n_sys; ++b)
+    if (sy[b].n_atoms == 0) {
+      CU_TRY(cudaMemsetAsync(sy[b].energy, 0, sizeof(double), st));
+      if (sy[b].virial) CU_TRY(cudaMemsetAsync(sy[b].virial, 0, 9 * sizeof(double), st));
+      launches += 1 + (sy[b].virial ? 1 : 0);
+    }
+  // per-chunk descriptors as kernel parameters
+  std::vector<BatchParams> chunks;
+  int in_base = 0;
+  for (int b0 = 0; b0 < n_sys; b0 += kMaxBatchParam) {
+    BatchParams bp{};
+    bp.sys_base = b0;
+    bp.n_sys = std::min(kMaxBatchParam, n_sys - b0);
+    for (int k = 0; k < bp.n_sys; ++k) {
+      const nnp_system_t& s = sy[b0 + k];
+      SysIn& si = bp.sys[k];
+      si.coords = s.coords;
+      si.species = s.species;
+      si.mask = s.mask;
+      si.energy = s.energy;
+      si.forces = s.forces;
+      si.virial = s.virial;
+      si.atom_e = s.atom_energies;
+      si.n_in = (int)s.n_atoms;
+      si.in_base = in_base;
+      si.periodic = s.periodic ? 1 : 0;
+      for (int c = 0; c < 3; ++c) split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c]);
+      in_base += (int)s.n_atoms;
+    }
+    chunks.push_back(bp);
+  }
+  for (const auto& bp : chunks) { launch_init_chunk(ws, bp, st); ++launches; }
+  for (const auto& bp : chunks) {
+    int n_chunk = 0;
+    for (int k = 0; k < bp.n_sys; ++k) n_chunk += bp.sys[k].n_in;
+    if (n_chunk > 0) { launch_prep_atoms(ws, bp, n_chunk, m.ac.S, st); ++launches; }
+  }
+  bool any_virial = false;
+  for (int b = 0; b < n_sys; ++b) any_virial |= (sy[b].virial != nullptr);
+  if (n_in > 0) {
+    {
+      StageTimer t(h, st, 0);
+      launch_setup(ws, m.ac, st);
+      launch_bin(ws, n_in, st);
+      launch_scan(ws, st);
+      launch_scatter(ws, n_in, st);
+    }
+    { StageTimer t(h, st, 1); launch_neighbors(ws, n_in, m.ac, st); }
+    { StageTimer t(h, st, 2); launch_aev_fwd(ws, n_in, m.ac, st); }
+    launches += 6;
+    StageHook hook{h, st};
+    if (m.precision == NNP_BF16_MLP) {
+      rc = launch_mlp_tc(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook);
+      if (rc) return rc;
+    } else {
+      launch_mlp_fp32(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook);
+    }
+    { StageTimer t(h, st, 9); launch_aev_bwd(ws, n_in, m.ac, any_virial ? 1 : 0, st); }
+    {
+      StageTimer t(h, st, 10);
+      launch_finalize_e(ws, n_in, h->mb.e_row, m.md.E, ws.row_cap, m.ebias, st);
+    }
+    launches += 2;
+  }
+  h->last_launches = launches;
+  h->last_n_in = n_in;
+  CU_TRY(cudaGetLastError());
+  return NNP_OK;
+}
+
+int validate_system(const nnp_handle* h, const nnp_system_t& s) {
+  if (s.n_atoms < 0) return fail(NNP_ERR_ARG, "negative atom count");
+  if (!s.energy) return fail(NNP_ERR_ARG, "energy output pointer is null");
+  if (s.n_atoms > 0 && (!s.coords || !s.species || !s.forces))
+    return fail(NNP_ERR_ARG, "coords, species and forces pointers are required");
+  if (s.periodic) {
+    const double rc = std::max(h->model->ac.rc_r, h->model->ac.rc_a);
+    for (int c = 0; c < 3; ++c) {
+      if (!std::isfinite(s.box[c]) || s.box[c] <= 0) return fail(NNP_ERR_ARG, "box edges must be positive");
+      if (s.box[c] < 2 * rc)
+        return fail(NNP_ERR_BOX_TOO_SMALL, "periodic box edge below twice the cutoff");
+    }
+  }
+  return NNP_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* nnp_last_error(void) { return g_err.c_str(); }
+
+int nnp_create(const nnp_species_t* species, const nnp_aev_params_t* aev,
+               const nnp_weights_t* weights, int precision, size_t hbm_budget_bytes,
+               nnp_handle** out) {
+  g_err.clear();
+  if (!out) return fail(NNP_ERR_ARG, "null output handle");
+  *out = nullptr;
+  std::unique_ptr<Model> m(new Model);
+  int rc = build_model(m.get(), species, aev, weights, precision);
+  if (rc) return rc;
+  nnp_handle* h = new nnp_handle;
+  h->model = m.release();
+  h->budget = hbm_budget_bytes;
+  if (cudaMallocHost(&h->status_host, 4 * sizeof(int)) != cudaSuccess) {
+    nnp_destroy(h);
+    return fail(NNP_ERR_CUDA, "cudaMallocHost failed");
+  }
+  *out = h;
+  return NNP_OK;
+}
+
+int nnp_clone(const nnp_handle* src, nnp_handle** out) {
+  if (!src || !out) return fail(NNP_ERR_ARG, "null argument");
+  nnp_handle* h = new nnp_handle;
+  h->model = src->model;
+  h->model->refs.fetch_add(1);
+  h->budget = src->budget;
+  h->cap_r = src->cap_r;
+  h->cap_a = src->cap_a;
+  if (cudaMallocHost(&h->status_host, 4 * sizeof(int)) != cudaSuccess) {
+    nnp_destroy(h);
+    return fail(NNP_ERR_CUDA, "cudaMallocHost failed");
+  }
+  *out = h;
+  return NNP_OK;
+}
+
+void nnp_destroy(nnp_handle* h) {
+  if (!h) return;
+  if (h->arena || h->stage) cudaDeviceSynchronize();
+  if (h->tc_state) mlp_tc_release(h->tc_state);
+  if (h->arena) cudaFree(h->arena);
+  if (h->stage) cudaFree(h->stage);
+  if (h->status_host) cudaFreeHost(h->status_host);
+  for (auto& pe : h->prof_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
+  for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+  if (h->model && h->model->refs.fetch_sub(1) == 1) delete h->model;
+  delete h;
+}
+
+int nnp_reserve(nnp_handle* h, int64_t max_atoms, int max_systems, int max_nr, int max_na) {
+  g_err.clear();
+  if (!h || max_atoms < 0 || max_systems < 0 || max_nr < 0 || max_na < 0)
+    return fail(NNP_ERR_ARG, "bad argument");
+  if (max_atoms > (1LL << 30)) return fail(NNP_ERR_ARG, "too many atoms");
+  if (max_nr > kStageCap) return fail(NNP_ERR_UNSUPPORTED, "at most 512 radial neighbours per atom");
+  if (max_nr) { h->cap_r = (int)align_up(max_nr, 32); h->dirty = true; }
+  if (max_na) { h->cap_a = (int)align_up(std::min(max_na, h->cap_r), 32); h->dirty = true; }
+  return ensure_arena(h, (int)std::max<int64_t>(max_atoms, h->cap_in), std::max(max_systems, h->cap_sys));
+}
+
+int nnp_energy_forces(nnp_handle* h, int64_t n_atoms, const float* coords, const uint8_t* species,
+                      const double* box_host, const uint8_t* mask, double* energy, float* forces,
+                      double* virial, void* stream) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  nnp_system_t s{};
+  s.n_atoms = n_atoms;
+  s.coords = coords;
+  s.species = species;
+  s.mask = mask;
+  s.periodic = box_host != nullptr;
+  if (box_host)
+    for (int c = 0; c < 3; ++c) s.box[c] = box_host[c];
+  s.energy = energy;
+  s.forces = forces;
+  s.virial = virial;
+  int rc = validate_system(h, s);
+  if (rc) return rc;
+  return run_batch(h, 1, &s, static_cast<cudaStream_t>(stream));
+}
+
+int nnp_energy_forces_batch(nnp_handle* h, int n_sys, const nnp_system_t* systems, void* stream) {
+  g_err.clear();
+  if (!h || n_sys < 0 || (n_sys > 0 && !systems)) return fail(NNP_ERR_ARG, "bad argument");
+  if (n_sys == 0) return NNP_OK;
+  for (int b = 0; b < n_sys; ++b) {
+    int rc = validate_system(h, systems[b]);
+    if (rc) return rc;
+  }
+  return run_batch(h, n_sys, systems, static_cast<cudaStream_t>(stream));
+}
+
+int nnp_sync_status(nnp_handle* h, void* stream) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU_TRY(cudaStreamSynchronize(st));
+  if (!h->arena) return NNP_OK;
+  CU_TRY(cudaMemcpy(h->status_host, h->ws.status, 4 * sizeof(int), cudaMemcpyDeviceToHost));
+  CU_TRY(cudaMemset(h->ws.status, 0, 4 * sizeof(int)));
+  const int f = h->status_host[0];
+  if (f & kStSpecies) return fail(NNP_ERR_SPECIES, "species index out of range");
+  if (f & kStNonFinite) return fail(NNP_ERR_NONFINITE, "non-finite coordinate in the ML region");
+  if (f & kStTimeout) return fail(NNP_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (f & (kStCapacity | kStCells)) {
+    const int need_r = h->status_host[1], need_a = h->status_host[2];
+    if (need_r > kStageCap)
+      return fail(NNP_ERR_UNSUPPORTED, "more than 512 neighbours inside the radial cutoff");
+    h->cap_r = std::max(h->cap_r, (int)align_up(need_r + need_r / 8 + 1, 32));
+    h->cap_r = std::min(h->cap_r, kStageCap);
+    h->cap_a = std::max(h->cap_a, (int)align_up(need_a + need_a / 8 + 1, 32));
+    h->cap_a = std::min(h->cap_a, h->cap_r);
+    h->dirty = true;
+    return fail(NNP_ERR_CAPACITY, "neighbour list over capacity (grown to " +
+                                      std::to_string(h->cap_r) + " / " + std::to_string(h->cap_a) +
+                                      "); repeat the call");
+  }
+  return NNP_OK;
+}
+
+int nnp_energy_forces_host(nnp_handle* h, int64_t n, const float* coords_h,
+                           const uint8_t* species_h, const double* box_host, const uint8_t* mask_h,
+                           double* energy_h, float* forces_h, double* virial_h) {
+  g_err.clear();
+  if (!h || n < 0 || !energy_h || (n > 0 && (!coords_h || !species_h || !forces_h)))
+    return fail(NNP_ERR_ARG, "bad argument");
+  // staging: coords, forces, species, mask, energy, virial
+  const size_t b_xyz = align_up((size_t)n * 12, 256), b_sp = align_up((size_t)n, 256);
+  const size_t need = 2 * b_xyz + 2 * b_sp + 256 + 256;
+  if (need > h->stage_bytes) {
+    if (h->stage) { CU_TRY(cudaDeviceSynchronize()); cudaFree(h->stage); h->stage = nullptr; }
+    CU_TRY(cudaMalloc(&h->stage, need));
+    h->stage_bytes = need;
+  }
+  char* base = static_cast<char*>(h->stage);
+  float* d_xyz = reinterpret_cast<float*>(base);
+  float* d_f = reinterpret_cast<float*>(base + b_xyz);
+  uint8_t* d_sp = reinterpret_cast<uint8_t*>(base + 2 * b_xyz);
+  uint8_t* d_mask = reinterpret_cast<uint8_t*>(base + 2 * b_xyz + b_sp);
+  double* d_e = reinterpret_cast<double*>(base + 2 * b_xyz + 2 * b_sp);
+  double* d_v = reinterpret_cast<double*>(base + 2 * b_xyz + 2 * b_sp + 256);
+  cudaStream_t st = nullptr;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (n > 0) {
+      CU_TRY(cudaMemcpyAsync(d_xyz, coords_h, (size_t)n * 12, cudaMemcpyHostToDevice, st));
+      CU_TRY(cudaMemcpyAsync(d_sp, species_h, (size_t)n, cudaMemcpyHostToDevice, st));
+      if (mask_h) CU_TRY(cudaMemcpyAsync(d_mask, mask_h, (size_t)n, cudaMemcpyHostToDevice, st));
+    }
+    int rc = nnp_energy_forces(h, n, d_xyz, d_sp, box_host, mask_h ? d_mask : nullptr, d_e, d_f,
+                               virial_h ? d_v : nullptr, st);
+    if (rc) return rc;
+    CU_TRY(cudaMemcpyAsync(energy_h, d_e, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (n > 0) CU_TRY(cudaMemcpyAsync(forces_h, d_f, (size_t)n * 12, cudaMemcpyDeviceToHost, st));
+    if (virial_h) CU_TRY(cudaMemcpyAsync(virial_h, d_v, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    rc = nnp_sync_status(h, st);
+    if (rc != NNP_ERR_CAPACITY) return rc;
+  }
+  return fail(NNP_ERR_CAPACITY, "neighbour list over capacity after one retry");
+}
+
+int nnp_aev_dim(const nnp_handle* h) { return h ? h->model->ac.D : -1; }
+int nnp_last_launch_count(const nnp_handle* h) { return h ? h->last_launches : -1; }
+
+int nnp_profile(nnp_handle* h, int enable) {
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  h->profile = enable != 0;
+  return NNP_OK;
+}
+
+int nnp_profile_read(nnp_handle* h, int reset, double* ms_out, long long* calls_out,
+                     int max_stages, int* n_stages) {
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  for (auto& pe : h->prof_pending) {
+    CU_TRY(cudaEventSynchronize(pe.second.second));
+    float ms = 0.f;
+    CU_TRY(cudaEventElapsedTime(&ms, pe.second.first, pe.second.second));
+    h->prof_ms[pe.first] += ms;
+    h->prof_calls[pe.first] += 1;
+    h->prof_pool.push_back(pe.second.first);
+    h->prof_pool.push_back(pe.second.second);
+  }
+  h->prof_pending.clear();
+  const int n = std::min(max_stages, kNumStages);
+  for (int i = 0; i < n; ++i) {
+    if (ms_out) ms_out[i] = h->prof_ms[i];
+    if (calls_out) calls_out[i] = h->prof_calls[i];
+  }
+  if (n_stages) *n_stages = kNumStages;
+  if (reset)
+    for (int i = 0; i < kNumStages; ++i) { h->prof_ms[i] = 0; h->prof_calls[i] = 0; }
+  return NNP_OK;
+}
+
+const char* nnp_profile_stage_name(int i) {
+  return (i >= 0 && i < kNumStages) ? kStageNames[i] : "";
+}
+
+// ---------------------------------------------------------------- diagnostics
+// Rows of the last call in batch input-atom order: which = 0 AEV, 1 dE/dG.
+// out: device float [n_in_total, D]; rows of atoms outside the mask untouched.
+int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream) {
+  if (!h || !h->arena || !out) return fail(NNP_ERR_ARG, "bad argument");
+  const float* src = which == 0 ? h->ws.aev : h->ws.dEdG;
+  launch_gather_rows(h->ws, h->last_n_in, src, h->model->ac.Dp, h->model->ac.D, out,
+                     static_cast<cudaStream_t>(stream));
+  CU_TRY(cudaGetLastError());
+  return NNP_OK;
+}
+
+// Neighbour lists of the last call in input-atom order: out[i][t] = input index
+// of the t-th neighbour of atom i (radial list, or angular if angular != 0),
+// -1 past the end.  out: device int32 [n_in_total, cap].
+int nnp_debug_neighbors(nnp_handle* h, int angular, int cap, int* out, void* stream) {
+  if (!h || !h->arena || !out || cap <= 0) return fail(NNP_ERR_ARG, "bad argument");
+  launch_gather_nbrs(h->ws, h->last_n_in, angular, cap, out, static_cast<cudaStream_t>(stream));
+  CU_TRY(cudaGetLastError());
+  return NNP_OK;
+}
+
+}  // extern "C"

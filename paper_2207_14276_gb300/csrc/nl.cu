@@ -1,0 +1,478 @@
+// Cell-list neighbour search (the linked-cell list that replaces an O(N^2)
+// pair search, paper Sec. "Massive Parallelism within Tinker-HP").
+//
+// Pipeline for a batch of systems, all on one stream, no host synchronisation:
+//   k_init     zero counters, copy the per-system descriptors to the device
+//   k_prep     per input atom: mask, validation, per-system / per-species counts,
+//              bounding boxes (non-periodic systems)
+//   k_setup    per system: cell grid, packed atom / cell offsets; 128-row padded
+//              species segments of the AEV rows
+//   k_bin      per atom: cell index, rank inside the cell, AEV row (slot)
+//   k_scan     exclusive scan of the cell counts
+//   k_scatter  packed (cell-ordered) float4 coordinates and index maps
+//   k_neighbors one warp per centre: scan the 27 neighbour cells, keep pairs
+//              with R <= rc_r, mark R <= rc_a, write species-sorted lists
+#include "nnp_internal.cuh"
+
+namespace nnp {
+
+namespace {
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ int find_sys(const BatchParams& bp, int idx) {
+  // last system whose in_base <= idx (in_base relative to the chunk start)
+  int lo = 0, hi = bp.n_sys - 1;
+  const int base0 = bp.sys[0].in_base;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (bp.sys[mid].in_base - base0 <= idx) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_init(Ws ws, BatchParams bp, int zero_all, int n_in) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  if (tid < bp.n_sys) {
+    SysDev d;
+    d.in = bp.sys[tid];
+    d.n_ml = 0;
+    d.atom_base = 0;
+    d.cell_base = 0;
+    for (int c = 0; c < 3; ++c) {
+      d.nc[c] = 1;
+      d.origin[c] = 0.f;
+      d.inv_cell[c] = 0.f;
+      d.bb_min[c] = 0xffffffffu;
+      d.bb_max[c] = 0u;
+    }
+    ws.sys[bp.sys_base + tid] = d;
+  }
+  if (!zero_all) return;
+  if (tid < kMaxSpecies) {
+    ws.species_count[tid] = 0;
+    ws.species_fill[tid] = 0;
+  }
+  if (tid < 4) ws.totals[tid] = 0;
+  for (int i = tid; i < ws.cell_cap; i += stride) ws.cell_count[i] = 0;
+  for (int i = tid; i < ws.row_cap; i += stride) ws.slot_pos[i] = -1;
+  for (int i = tid; i < n_in; i += stride) ws.f_pos[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_prep(Ws ws, BatchParams bp, int n_chunk, int S) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31;
+  const bool live = t < n_chunk;
+  int k = 0, local = 0, gi = 0, s = -1, b = -1;
+  bool ml = false;
+  float x = 0.f, y = 0.f, z = 0.f;
+  if (live) {
+    k = find_sys(bp, t);
+    const SysIn& si = bp.sys[k];
+    local = t - (si.in_base - bp.sys[0].in_base);
+    gi = si.in_base + local;
+    b = bp.sys_base + k;
+    ml = (si.mask == nullptr) || (si.mask[local] != 0);
+    // every output force starts at zero (atoms outside the mask keep it)
+    si.forces[3 * local + 0] = 0.f;
+    si.forces[3 * local + 1] = 0.f;
+    si.forces[3 * local + 2] = 0.f;
+    if (si.atom_e) si.atom_e[local] = 0.f;
+    if (local == 0) {
+      *si.energy = 0.0;
+      if (si.virial)
+        for (int c = 0; c < 9; ++c) si.virial[c] = 0.0;
+    }
+    if (ml) {
+      s = si.species[local];
+      x = si.coords[3 * local + 0];
+      y = si.coords[3 * local + 1];
+      z = si.coords[3 * local + 2];
+      int bad = 0;
+      if (s >= S) bad |= kStSpecies;
+      if (!isfinite(x) || !isfinite(y) || !isfinite(z)) bad |= kStNonFinite;
+      if (bad) {
+        atomicOr(ws.status, bad);
+        ml = false;  // excluded; the call reports the error
+      }
+    }
+    ws.in_sys[gi] = ml ? b : -1;
+  }
+  // per-system ML atom counts and bounding boxes (warp-aggregated)
+  const unsigned act = __ballot_sync(0xffffffffu, live && ml);
+  if (live && ml) {
+    const unsigned grp = __match_any_sync(act, b);
+    const int leader = __ffs(grp) - 1;
+    if ((int)lane == leader) atomicAdd(&ws.sys[b].n_ml, __popc(grp));
+    if (!bp.sys[k].periodic) {
+      const float v[3] = {x, y, z};
+      for (int c = 0; c < 3; ++c) {
+        const unsigned key = float_key(v[c]);
+        const unsigned mn = __reduce_min_sync(grp, key);
+        const unsigned mx = __reduce_max_sync(grp, key);
+        if ((int)lane == leader) {
+          atomicMin(&ws.sys[b].bb_min[c], mn);
+          atomicMax(&ws.sys[b].bb_max[c], mx);
+        }
+      }
+    }
+    const unsigned sg = __match_any_sync(act, s);
+    if ((int)lane == __ffs(sg) - 1) atomicAdd(&ws.species_count[s], __popc(sg));
+  }
+}
+
+// block-wide exclusive scan helper (blockDim.x == 256)
+__device__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int warp_sums[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) warp_sums[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int ws_ = lane < 8 ? warp_sums[lane] : 0;
+    for (int o = 1; o < 8; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, ws_, o);
+      if (lane >= o) ws_ += u;
+    }
+    if (lane < 8) warp_sums[lane] = ws_;
+  }
+  __syncthreads();
+  const int before = (w > 0 ? warp_sums[w - 1] : 0) + incl - v;
+  *total = warp_sums[7];
+  __syncthreads();
+  return before;
+}
+
+__global__ void k_setup(Ws ws, AevConst ac) {
+  const float rc = fmaxf(ac.rc_r, ac.rc_a);
+  int run_atoms = 0, run_cells = 0;
+  for (int b0 = 0; b0 < ws.n_sys; b0 += blockDim.x) {
+    const int b = b0 + threadIdx.x;
+    int n_ml = 0, ncell = 0;
+    SysDev d;
+    if (b < ws.n_sys) {
+      d = ws.sys[b];
+      n_ml = d.n_ml;
+      const int cap = 2 * d.in.n_in + 27;
+      int nc[3];
+      float len[3], org[3];
+      for (int c = 0; c < 3; ++c) {
+        if (d.in.periodic) {
+          len[c] = d.in.box_hi[c];
+          org[c] = 0.f;
+        } else if (n_ml > 0) {
+          const float lo = key_float(d.bb_min[c]), hi = key_float(d.bb_max[c]);
+          len[c] = fmaxf(hi - lo, 1e-3f);
+          org[c] = lo;
+        } else {
+          len[c] = 1.f;
+          org[c] = 0.f;
+        }
+        nc[c] = max(1, (int)floorf(len[c] / rc));
+      }
+      while ((long long)nc[0] * nc[1] * nc[2] > cap) {
+        int c = (nc[0] >= nc[1] && nc[0] >= nc[2]) ? 0 : (nc[1] >= nc[2] ? 1 : 2);
+        nc[c] = max(1, nc[c] - 1);
+      }
+      for (int c = 0; c < 3; ++c) {
+        d.nc[c] = nc[c];
+        d.origin[c] = org[c];
+        d.inv_cell[c] = nc[c] / len[c];
+      }
+      ncell = nc[0] * nc[1] * nc[2];
+    }
+    int tot_a, tot_c;
+    const int ea = block_exclusive_scan(n_ml, &tot_a);
+    const int ec = block_exclusive_scan(ncell, &tot_c);
+    if (b < ws.n_sys) {
+      d.atom_base = run_atoms + ea;
+      d.cell_base = run_cells + ec;
+      ws.sys[b] = d;
+    }
+    run_atoms += tot_a;
+    run_cells += tot_c;
+  }
+  if (threadIdx.x == 0) {
+    ws.totals[0] = run_atoms;
+    ws.totals[1] = run_cells;
+    if (run_cells > ws.cell_cap) atomicOr(ws.status, kStCells);
+    int acc = 0;
+    for (int s = 0; s < ac.S; ++s) {
+      ws.seg_start[s] = acc;
+      acc += (ws.species_count[s] + kRowTile - 1) / kRowTile * kRowTile;
+    }
+    for (int s = ac.S; s <= kMaxSpecies; ++s) ws.seg_start[s] = acc;
+  }
+}
+
+__device__ __forceinline__ int cell_coord(float x, const SysDev& d, int c) {
+  float u;
+  if (d.in.periodic) {
+    const float L = d.in.box_hi[c];
+    u = x - floorf(x / L) * L;   // exact for x already in [0, L)
+  } else {
+    u = x - d.origin[c];
+  }
+  int k = (int)floorf(u * d.inv_cell[c]);
+  return min(max(k, 0), d.nc[c] - 1);
+}
+
+__global__ void k_bin(Ws ws, int n_in) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31;
+  int b = -1;
+  if (gi < n_in) b = ws.in_sys[gi];
+  const bool ml = b >= 0;
+  const unsigned act = __ballot_sync(0xffffffffu, ml);
+  if (!ml) return;
+  const SysDev& d = ws.sys[b];
+  const int local = gi - d.in.in_base;
+  const float x = d.in.coords[3 * local + 0];
+  const float y = d.in.coords[3 * local + 1];
+  const float z = d.in.coords[3 * local + 2];
+  const int s = d.in.species[local];
+  const int cx = cell_coord(x, d, 0), cy = cell_coord(y, d, 1), cz = cell_coord(z, d, 2);
+  const int gcell = d.cell_base + (cx * d.nc[1] + cy) * d.nc[2] + cz;
+  const int rank = atomicAdd(&ws.cell_count[gcell], 1);
+  const unsigned sg = __match_any_sync(act, s);
+  const int leader = __ffs(sg) - 1;
+  int base = 0;
+  if ((int)lane == leader) base = atomicAdd(&ws.species_fill[s], __popc(sg));
+  base = __shfl_sync(sg, base, leader);
+  const int slot = ws.seg_start[s] + base + __popc(sg & lanemask_lt());
+  ws.in_cell[gi] = gcell;
+  ws.in_rank[gi] = rank;
+  ws.in_slot[gi] = slot;
+}
+
+// single-block exclusive scan of the cell counts (1024 threads)
+__global__ void k_scan(Ws ws) {
+  __shared__ int warp_sums[32];
+  const int T = ws.totals[1];
+  const int nt = blockDim.x;
+  const int per = (T + nt - 1) / nt;
+  const int beg = min(T, threadIdx.x * per), end = min(T, beg + per);
+  int sum = 0;
+  for (int i = beg; i < end; ++i) sum += ws.cell_count[i];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) warp_sums[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int v = warp_sums[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    warp_sums[lane] = v;
+  }
+  __syncthreads();
+  int run = (w > 0 ? warp_sums[w - 1] : 0) + incl - sum;
+  for (int i = beg; i < end; ++i) {
+    ws.cell_start[i] = run;
+    run += ws.cell_count[i];
+  }
+  if (threadIdx.x == nt - 1) ws.cell_start[T] = warp_sums[31];
+}
+
+__global__ void k_scatter(Ws ws, int n_in) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= n_in) return;
+  const int b = ws.in_sys[gi];
+  if (b < 0) return;
+  const SysDev& d = ws.sys[b];
+  const int local = gi - d.in.in_base;
+  const int gcell = ws.in_cell[gi];
+  const int pos = ws.cell_start[gcell] + ws.in_rank[gi];
+  const int slot = ws.in_slot[gi];
+  ws.xyzq[pos] = make_float4(d.in.coords[3 * local + 0], d.in.coords[3 * local + 1],
+                             d.in.coords[3 * local + 2], __int_as_float((int)d.in.species[local]));
+  ws.pos_src[pos] = gi;
+  ws.pos_slot[pos] = slot;
+  ws.pos_sys[pos] = b;
+  ws.pos_cell[pos] = gcell - d.cell_base;
+  ws.slot_pos[slot] = pos;
+}
+
+// one warp per centre; staged candidates in shared memory, then species-sorted
+constexpr int kNbWarps = 8;
+
+__global__ void __launch_bounds__(kNbWarps * 32) k_neighbors(Ws ws, AevConst ac) {
+  __shared__ int st_j[kNbWarps][kStageCap];
+  __shared__ uint8_t st_t[kNbWarps][kStageCap];   // species | (angular << 7)
+  const int w = threadIdx.x >> 5;
+  const unsigned lane = threadIdx.x & 31;
+  const int p = blockIdx.x * kNbWarps + w;
+  if (p >= ws.totals[0]) return;
+  const float4 xi = ws.xyzq[p];
+  const int b = ws.pos_sys[p];
+  const SysDev& d = ws.sys[b];
+  const int per = d.in.periodic;
+  const int lc = ws.pos_cell[p];
+  const int nc0 = d.nc[0], nc1 = d.nc[1], nc2 = d.nc[2];
+  const int c2 = lc % nc2, c1 = (lc / nc2) % nc1, c0 = lc / (nc1 * nc2);
+  const float rr2 = ac.rc_r * ac.rc_r, ra2 = ac.rc_a * ac.rc_a;
+  const float Lh0 = d.in.box_hi[0], Lh1 = d.in.box_hi[1], Lh2 = d.in.box_hi[2];
+  const float Ll0 = d.in.box_lo[0], Ll1 = d.in.box_lo[1], Ll2 = d.in.box_lo[2];
+  const float iL0 = per ? 1.f / Lh0 : 0.f, iL1 = per ? 1.f / Lh1 : 0.f, iL2 = per ? 1.f / Lh2 : 0.f;
+  int cnt = 0;
+  // candidate cell index lists per dimension (distinct cells only)
+  int cl0[3], cl1[3], cl2[3], n0 = 0, n1 = 0, n2 = 0;
+  {
+    const int cc[3] = {c0, c1, c2};
+    const int ncv[3] = {nc0, nc1, nc2};
+    int* out[3] = {cl0, cl1, cl2};
+    int* nout[3] = {&n0, &n1, &n2};
+    for (int c = 0; c < 3; ++c) {
+      int m = 0;
+      if (ncv[c] >= 3 || !per) {
+        for (int o = -1; o <= 1; ++o) {
+          int k = cc[c] + o;
+          if (per) k = (k + ncv[c]) % ncv[c];
+          else if (k < 0 || k >= ncv[c]) continue;
+          out[c][m++] = k;
+        }
+      } else {
+        for (int k = 0; k < ncv[c]; ++k) out[c][m++] = k;
+      }
+      *nout[c] = m;
+    }
+  }
+  for (int a0 = 0; a0 < n0; ++a0)
+    for (int a1 = 0; a1 < n1; ++a1)
+      for (int a2 = 0; a2 < n2; ++a2) {
+        const int gc = d.cell_base + (cl0[a0] * nc1 + cl1[a1]) * nc2 + cl2[a2];
+        const int beg = ws.cell_start[gc], end = ws.cell_start[gc + 1];
+        for (int j0 = beg; j0 < end; j0 += 32) {
+          const int j = j0 + lane;
+          bool keep = false, ang = false;
+          int sj = 0;
+          if (j < end && j != p) {
+            const float4 xj = ws.xyzq[j];
+            float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            if (per) {
+              float n;
+              n = rintf(dx * iL0); dx = fmaf(-n, Lh0, dx); dx = fmaf(-n, Ll0, dx);
+              n = rintf(dy * iL1); dy = fmaf(-n, Lh1, dy); dy = fmaf(-n, Ll1, dy);
+              n = rintf(dz * iL2); dz = fmaf(-n, Lh2, dz); dz = fmaf(-n, Ll2, dz);
+            }
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            keep = (r2 <= rr2) && (r2 > 1e-12f);
+            ang = keep && (r2 <= ra2);
+            sj = __float_as_int(xj.w);
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, keep);
+          if (keep) {
+            const int at = cnt + __popc(bal & lanemask_lt());
+            if (at < kStageCap) {
+              st_j[w][at] = j;
+              st_t[w][at] = (uint8_t)(sj | (ang ? 0x80 : 0));
+            }
+          }
+          cnt += __popc(bal);
+        }
+      }
+  __syncwarp();
+  const int nst = min(cnt, kStageCap);
+  // species-sorted radial and angular lists
+  int wr_r = 0, wr_a = 0;
+  uint16_t* hdr = ws.nb_cnt + (size_t)p * 16;
+  int* out_r = ws.nb_r + (size_t)p * ws.cap_r;
+  int* out_a = ws.nb_a + (size_t)p * ws.cap_a;
+  for (int s = 0; s < ac.S; ++s) {
+    int cr = 0, ca = 0;
+    for (int t0 = 0; t0 < nst; t0 += 32) {
+      const int t = t0 + lane;
+      bool mr = false, ma = false;
+      int j = 0;
+      if (t < nst) {
+        const int tt = st_t[w][t];
+        j = st_j[w][t];
+        mr = (tt & 0x7f) == s;
+        ma = mr && (tt & 0x80);
+      }
+      const unsigned br = __ballot_sync(0xffffffffu, mr);
+      const unsigned ba = __ballot_sync(0xffffffffu, ma);
+      if (mr) {
+        const int at = wr_r + cr + __popc(br & lanemask_lt());
+        if (at < ws.cap_r) out_r[at] = j;
+      }
+      if (ma) {
+        const int at = wr_a + ca + __popc(ba & lanemask_lt());
+        if (at < ws.cap_a) out_a[at] = j;
+      }
+      cr += __popc(br);
+      ca += __popc(ba);
+    }
+    // clamp the per-species counts so that the lists stay inside their capacity
+    const int keep_r = max(0, min(cr, ws.cap_r - wr_r));
+    const int keep_a = max(0, min(ca, ws.cap_a - wr_a));
+    if (lane == 0) {
+      hdr[s] = (uint16_t)keep_r;
+      hdr[8 + s] = (uint16_t)keep_a;
+    }
+    wr_r += cr;
+    wr_a += ca;
+  }
+  if (lane == 0) {
+    for (int s = ac.S; s < 8; ++s) { hdr[s] = 0; hdr[8 + s] = 0; }
+    if (cnt > ws.cap_r || wr_a > ws.cap_a || cnt > kStageCap) {
+      atomicOr(ws.status, kStCapacity);
+      atomicMax(ws.status + 1, cnt);
+      atomicMax(ws.status + 2, wr_a);
+    }
+  }
+}
+
+}  // namespace
+
+void launch_init_chunk(const Ws& ws, const BatchParams& bp, cudaStream_t st) {
+  // the first chunk of a batch also zeroes the shared counters
+  const int zero_all = (bp.sys_base == 0);
+  const int work = zero_all ? max(max(ws.cell_cap, ws.row_cap), max(ws.n_in, bp.n_sys)) : bp.n_sys;
+  int blocks = (work + 255) / 256;
+  blocks = max(1, min(blocks, 1184));
+  k_init<<<blocks, 256, 0, st>>>(ws, bp, zero_all, ws.n_in);
+}
+
+void launch_prep_atoms(const Ws& ws, const BatchParams& bp, int n_in_chunk, int S,
+                       cudaStream_t st) {
+  if (n_in_chunk <= 0) return;
+  k_prep<<<(n_in_chunk + 255) / 256, 256, 0, st>>>(ws, bp, n_in_chunk, S);
+}
+
+void launch_setup(const Ws& ws, const AevConst& ac, cudaStream_t st) {
+  k_setup<<<1, 256, 0, st>>>(ws, ac);
+}
+
+void launch_bin(const Ws& ws, int n_in, cudaStream_t st) {
+  if (n_in <= 0) return;
+  k_bin<<<(n_in + 255) / 256, 256, 0, st>>>(ws, n_in);
+}
+
+void launch_scan(const Ws& ws, cudaStream_t st) { k_scan<<<1, 1024, 0, st>>>(ws); }
+
+void launch_scatter(const Ws& ws, int n_in, cudaStream_t st) {
+  if (n_in <= 0) return;
+  k_scatter<<<(n_in + 255) / 256, 256, 0, st>>>(ws, n_in);
+}
+
+void launch_neighbors(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st) {
+  if (n_in <= 0) return;
+  k_neighbors<<<(n_in + kNbWarps - 1) / kNbWarps, kNbWarps * 32, 0, st>>>(ws, ac);
+}
+
+}  // namespace nnp

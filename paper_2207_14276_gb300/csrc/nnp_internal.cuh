@@ -1,0 +1,157 @@
+// Internal declarations shared by the CUDA translation units of libnnp.
+// Device-side layout of the work arena and the per-system descriptors.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nnp {
+
+constexpr int kMaxSpecies = 8;
+constexpr int kNR = 16;            // radial shells (Eq. 4)
+constexpr int kNA = 4;             // angular distance shells (Eq. 5)
+constexpr int kNZ = 8;             // angular sections (Eq. 5)
+constexpr int kRowTile = 128;      // species segments of AEV rows are padded to this
+constexpr int kMaxBatchParam = 64; // systems per kernel-parameter chunk
+constexpr int kStageCap = 512;     // staged radial neighbours per centre (hard cap)
+
+// status word bits (device)
+enum : int {
+  kStSpecies = 1,
+  kStNonFinite = 2,
+  kStCapacity = 4,
+  kStCells = 8,
+  kStTimeout = 16,
+};
+
+// AEV hyper-parameters in the form the kernels use
+struct AevConst {
+  int S;            // species
+  int D;            // AEV length
+  int Dp;           // padded row stride (multiple of 64)
+  int n_pairs;      // S(S+1)/2
+  float rc_r, rc_a, eta_r, eta_a;
+  float shf_r[kNR];
+  float shf_a[kNA];
+  float cos_z[kNZ], sin_z[kNZ];
+  float cos_scale;
+  int zeta;         // integer exponent
+  float ang_pre;    // 2^(1-zeta)
+};
+
+// per-system descriptor as passed in kernel parameters (host-filled part)
+struct SysIn {
+  const float* coords;
+  const uint8_t* species;
+  const uint8_t* mask;
+  double* energy;
+  float* forces;
+  double* virial;
+  float* atom_e;
+  int n_in;
+  int in_base;       // offset of this system's atoms in the batch input index space
+  int periodic;
+  float box_hi[3], box_lo[3];   // box edge as float hi + float residual
+};
+
+// per-system device state (device-filled part)
+struct SysDev {
+  SysIn in;
+  int n_ml;          // atoms inside the mask
+  int atom_base;     // first packed (cell-ordered) position of this system
+  int cell_base;     // first global cell index
+  int nc[3];         // cells per dimension
+  float origin[3];   // cell grid origin (non-periodic: bounding-box minimum)
+  float inv_cell[3]; // cells per Angstrom
+  unsigned bb_min[3], bb_max[3];  // bounding box as order-preserving uint keys
+};
+
+struct BatchParams {
+  int n_sys;         // systems in this chunk
+  int sys_base;      // index of the first system of the chunk in the batch
+  SysIn sys[kMaxBatchParam];
+};
+
+// device work arena (all pointers device)
+struct Ws {
+  int* status;       // [4]: flags, max radial count, max angular count, spare
+  SysDev* sys;       // [max_sys]
+  int n_sys;
+  int n_in;          // batch input atoms (sum of n_in)
+  int cell_cap;      // capacity of the global cell arrays
+  int row_cap;       // capacity of AEV rows (n_in + S*kRowTile)
+  int cap_r, cap_a;  // neighbour capacity per centre
+  // counters
+  int* species_count;   // [kMaxSpecies]
+  int* species_fill;    // [kMaxSpecies]
+  int* seg_start;       // [kMaxSpecies+1] 128-aligned row segments; [S] = total rows
+  int* totals;          // [4]: total ML atoms, total cells
+  int* cell_count;      // [cell_cap]
+  int* cell_start;      // [cell_cap + 1]
+  // per input atom
+  int* in_cell;         // global cell or -1
+  int* in_rank;
+  int* in_slot;
+  int* in_sys;
+  // per packed (cell-ordered) atom
+  float4* xyzq;         // x, y, z, species (int bits)
+  int* pos_src;         // batch input index
+  int* pos_slot;        // AEV row
+  int* pos_sys;
+  int* pos_cell;        // local cell index within the system grid
+  int* slot_pos;        // [row_cap] packed position of a row, -1 for padding
+  // neighbour lists
+  uint16_t* nb_cnt;     // [n_in][16]: radial count per species [0..7], angular [8..15]
+  int* nb_r;            // [n_in][cap_r] packed positions, species-sorted
+  int* nb_a;            // [n_in][cap_a]
+  // AEV / gradient
+  float* aev;           // [row_cap][Dp]
+  float* dEdG;          // [row_cap][Dp]
+  float* atom_e;        // [row_cap] per-row energy (mean over the ensemble, incl. shift)
+  float4* f_pos;        // [n_in] forces on packed atoms
+};
+
+// ---- launchers (nl.cu)
+void launch_init_chunk(const Ws& ws, const BatchParams& bp, cudaStream_t st);
+void launch_prep_atoms(const Ws& ws, const BatchParams& bp, int n_in_chunk, int S,
+                       cudaStream_t st);
+void launch_setup(const Ws& ws, const AevConst& ac, cudaStream_t st);
+void launch_bin(const Ws& ws, int n_in, cudaStream_t st);
+void launch_scan(const Ws& ws, cudaStream_t st);
+void launch_scatter(const Ws& ws, int n_in, cudaStream_t st);
+void launch_neighbors(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st);
+// ---- aev.cu
+void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st);
+void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
+                    cudaStream_t st);
+cudaError_t aev_set_smem_limits(const Ws& ws);
+size_t aev_fwd_smem(const Ws& ws);
+size_t aev_bwd_smem(const Ws& ws);
+// ---- finalize.cu
+void launch_finalize_e(const Ws& ws, int n_in, const float* e_row, int E, int e_row_net,
+                       const double* ebias, cudaStream_t st);
+void launch_gather_rows(const Ws& ws, int n_in, const float* rows, int ld, int D, float* out,
+                        cudaStream_t st);
+void launch_gather_nbrs(const Ws& ws, int n_in, int angular, int cap_out, int* out,
+                        cudaStream_t st);
+
+// order-preserving float <-> uint key (for atomicMin/atomicMax on floats)
+__host__ __device__ inline unsigned float_key(float f) {
+  unsigned u;
+#ifdef __CUDA_ARCH__
+  u = __float_as_uint(f);
+#else
+  union { float f; unsigned u; } c; c.f = f; u = c.u;
+#endif
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float key_float(unsigned k) {
+  unsigned u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  union { float f; unsigned u; } c; c.u = u; return c.f;
+#endif
+}
+
+}  // namespace nnp

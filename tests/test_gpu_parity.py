@@ -1,0 +1,271 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 path): energy within 1e-3 kcal/mol and force RMS error within
+1e-3 kcal/mol/A of the oracle (the stated FP32 bar), plus relative bounds that
+FP32 arithmetic meets with margin: force RMS error <= 1e-4 of the force RMS and
+AEV elements within 2e-5 relative (+1e-6 absolute).  Neighbour lists are
+compared as sets (index work: exact), except for pairs within 1e-4 A of the
+cutoff where FP32 and FP64 may legitimately decide differently (such pairs
+contribute exactly zero: f_c(Rc) = f_c'(Rc) = 0, Eq. 3).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._common import force_errors, model_for, to_cuda
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-3
+F_RMS_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch
+
+
+def make(kind, precision="fp32", cos_scale=1.0):
+    from paper_2207_14276_gb300 import Potential
+    spec, w = model_for(kind, cos_scale=cos_scale)
+    return Potential(spec, w, precision=precision), oracle.Model(spec, w)
+
+
+def check_system(pot, orc, s, rel_f=1e-4, aev=True):
+    d = to_cuda(s)
+    E, F = pot.energy_forces(d["coords"], d["species"], d["box"], d["mask"])
+    ref = orc.energy_forces(s.coords, s.species, s.box, s.mask, want_aev=aev)
+    E = float(E.cpu()[0])
+    F = F.cpu().numpy()
+    assert abs(E - ref["energy"]) <= E_TOL, (E, ref["energy"])
+    rms, mx = force_errors(F, ref["forces"])
+    f_rms = float(np.sqrt(np.mean(ref["forces"] ** 2)))
+    assert rms <= F_RMS_TOL
+    assert rms <= rel_f * f_rms + 1e-7, (rms, f_rms)
+    if s.mask is not None:
+        assert np.all(F[s.mask == 0] == 0.0)
+    if aev:
+        G = pot.debug_rows(0, s.n_atoms).cpu().numpy()
+        Gr = ref["aev"]
+        sel = np.ones(s.n_atoms, bool) if s.mask is None else s.mask == 1
+        np.testing.assert_allclose(G[sel], Gr[sel], rtol=2e-5, atol=1e-6)
+    return E, F, ref
+
+
+def neighbour_sets(pot, s, angular):
+    nb = pot.debug_neighbors(s.n_atoms, angular=angular).cpu().numpy()
+    pairs = set()
+    for i in range(s.n_atoms):
+        if s.mask is not None and not s.mask[i]:
+            continue
+        for j in nb[i]:
+            if j < 0:
+                break
+            pairs.add((i, int(j)))
+    return pairs
+
+
+def near_cutoff(s, pairs, rc, tol=1e-4):
+    x = s.coords.astype(np.float64)
+    out = set()
+    for i, j in pairs:
+        d = x[j] - x[i]
+        if s.box is not None:
+            d -= s.box * np.round(d / s.box)
+        if abs(np.linalg.norm(d) - rc) < tol:
+            out.add((i, j))
+    return out
+
+
+def compare_neighbours(pot, s, spec):
+    for angular, rc in ((False, spec.aev.rc_r), (True, spec.aev.rc_a)):
+        got = neighbour_sets(pot, s, angular)
+        ref = set(map(tuple, oracle.neighbours(s.coords, rc, s.box, s.mask).tolist()))
+        diff = got ^ ref
+        assert diff == near_cutoff(s, diff, rc), sorted(diff)[:10]
+
+
+def test_gas24_energy_forces_aev_neighbours(torch_cuda):
+    pot, orc = make("ani4")
+    systems, _, _ = synth.workload("gas24")
+    s = systems[0]
+    check_system(pot, orc, s)
+    compare_neighbours(pot, s, pot.spec)
+    # dE/dG (the network gradient) elementwise
+    ref = orc.energy_forces(s.coords, s.species, want_dEdG=True)["dEdG"]
+    g = pot.debug_rows(1, s.n_atoms).cpu().numpy()
+    np.testing.assert_allclose(g, ref, rtol=1e-4, atol=1e-7)
+
+
+def test_water9000_fp32(torch_cuda):
+    pot, orc = make("ani4")
+    systems, _, _ = synth.workload("water9000")
+    s = systems[0]
+    E, F, ref = check_system(pot, orc, s)
+    compare_neighbours(pot, s, pot.spec)
+    assert np.abs(F.astype(np.float64).sum(0)).max() < 1e-3
+
+
+def test_cos_scale_variant(torch_cuda):
+    pot, orc = make("ani4", cos_scale=0.95)
+    s = synth.water_box(300, 20.5, 7, seed=41)
+    check_system(pot, orc, s)
+
+
+def test_seven_species_solute(torch_cuda):
+    pot, orc = make("ani7")
+    s = synth.solvated_solute(400, 120, 24.0, seed=5)
+    check_system(pot, orc, s)
+
+
+def test_ensemble_of_eight(torch_cuda):
+    pot, orc = make("ani7x8")
+    s = synth.solvated_solute(150, 60, 18.0, seed=6)
+    check_system(pot, orc, s)
+
+
+def test_hybrid_mask(torch_cuda):
+    # Eq. 7: only the solute is in the ML region; waters get zero force
+    pot, orc = make("ani7")
+    s = synth.solvated_solute(600, 50, 27.0, seed=7, mask_solute=True)
+    E, F, ref = check_system(pot, orc, s)
+    np.testing.assert_array_equal(F[s.mask == 0], 0.0)
+    compare_neighbours(pot, s, pot.spec)
+
+
+def test_batch_of_molecules_matches_oracle_and_single_calls(torch_cuda):
+    pot, orc = make("ani4")
+    mols, _, _ = synth.workload("molecules64")
+    outs = pot.energy_forces_batch([to_cuda(m) for m in mols])
+    for m, o in zip(mols, outs):
+        ref = orc.energy_forces(m.coords, m.species)
+        assert abs(float(o["energy"].cpu()[0]) - ref["energy"]) <= E_TOL
+        rms, _ = force_errors(o["forces"].cpu().numpy(), ref["forces"])
+        assert rms <= 1e-4 * np.sqrt(np.mean(ref["forces"] ** 2)) + 1e-7
+    # the same molecule alone gives the same result as inside the batch
+    for k in (0, 17, 63):
+        d = to_cuda(mols[k])
+        E, F = pot.energy_forces(d["coords"], d["species"])
+        assert float(E.cpu()[0]) == pytest.approx(float(outs[k]["energy"].cpu()[0]), abs=1e-5)
+        np.testing.assert_allclose(F.cpu().numpy(), outs[k]["forces"].cpu().numpy(), atol=1e-5)
+
+
+def test_mixed_batch_periodic_and_gas(torch_cuda):
+    pot, orc = make("ani4")
+    a = synth.water_box(200, 18.0, 6, seed=8)
+    b = synth.workload("gas24")[0][0]
+    c = synth.water_box(100, 15.0, 5, seed=9)
+    outs = pot.energy_forces_batch([to_cuda(a), to_cuda(b), to_cuda(c)], virial=True)
+    for s, o in zip((a, b, c), outs):
+        ref = orc.energy_forces(s.coords, s.species, s.box)
+        assert abs(float(o["energy"].cpu()[0]) - ref["energy"]) <= E_TOL
+        rms, _ = force_errors(o["forces"].cpu().numpy(), ref["forces"])
+        assert rms <= 1e-4 * np.sqrt(np.mean(ref["forces"] ** 2)) + 1e-7
+        np.testing.assert_allclose(o["virial"].cpu().numpy().reshape(3, 3), ref["virial"],
+                                   atol=1e-4 * np.abs(ref["virial"]).max() + 1e-6)
+
+
+def test_unwrapped_periodic_coordinates(torch_cuda):
+    pot, orc = make("ani4")
+    s = synth.water_box(200, 18.0, 6, seed=10)
+    shifted = synth.System("shift", (s.coords + np.float32(18.0)).astype(np.float32), s.species, s.box)
+    d0, d1 = to_cuda(s), to_cuda(shifted)
+    E0, F0 = pot.energy_forces(d0["coords"], d0["species"], d0["box"])
+    E1, F1 = pot.energy_forces(d1["coords"], d1["species"], d1["box"])
+    assert float(E0.cpu()[0]) == pytest.approx(float(E1.cpu()[0]), abs=1e-4)
+    np.testing.assert_allclose(F0.cpu().numpy(), F1.cpu().numpy(), atol=1e-4)
+
+
+def test_edge_cases(torch_cuda):
+    import torch
+    pot, orc = make("ani4")
+    # empty system
+    E, F = pot.energy_forces(torch.zeros((0, 3), device="cuda"),
+                             torch.zeros(0, dtype=torch.uint8, device="cuda"))
+    assert float(E.cpu()[0]) == 0.0 and F.shape == (0, 3)
+    # a single isolated atom: E = network of a zero AEV, zero force
+    x = np.array([[1.0, 2.0, 3.0]], np.float32)
+    sp = np.array([2], np.uint8)
+    E, F = pot.energy_forces(torch.from_numpy(x).cuda(), torch.from_numpy(sp).cuda())
+    ref = orc.energy_forces(x, sp)
+    assert float(E.cpu()[0]) == pytest.approx(ref["energy"], abs=1e-5)
+    assert np.all(F.cpu().numpy() == 0.0)
+    # all atoms masked out: zero energy and forces
+    s = synth.water_box(50, 12.0, 4, seed=11)
+    d = to_cuda(s)
+    E, F = pot.energy_forces(d["coords"], d["species"], d["box"],
+                             torch.zeros(s.n_atoms, dtype=torch.uint8, device="cuda"))
+    assert float(E.cpu()[0]) == 0.0 and torch.count_nonzero(F).item() == 0
+    # two atoms just inside / outside the cutoff
+    for dist in (5.19, 5.21):
+        x = np.array([[0, 0, 0], [dist, 0, 0]], np.float32)
+        sp = np.array([0, 3], np.uint8)
+        E, F = pot.energy_forces(torch.from_numpy(x).cuda(), torch.from_numpy(sp).cuda())
+        ref = orc.energy_forces(x, sp)
+        assert float(E.cpu()[0]) == pytest.approx(ref["energy"], abs=1e-6)
+        np.testing.assert_allclose(F.cpu().numpy(), ref["forces"], atol=1e-7)
+
+
+def test_errors_are_reported(torch_cuda):
+    import torch
+    from paper_2207_14276_gb300 import NNPError
+    pot, _ = make("ani4")
+    s = synth.water_box(50, 12.0, 4, seed=12)
+    d = to_cuda(s)
+    with pytest.raises(NNPError, match="BOX_TOO_SMALL"):
+        pot.energy_forces(d["coords"], d["species"], [10.0, 12.0, 12.0])
+    bad = d["species"].clone()
+    bad[3] = 9
+    with pytest.raises(NNPError, match="SPECIES"):
+        pot.energy_forces(d["coords"], bad, d["box"])
+    x = d["coords"].clone()
+    x[5, 1] = float("nan")
+    with pytest.raises(NNPError, match="NONFINITE"):
+        pot.energy_forces(x, d["species"], d["box"])
+    # the handle stays usable after the errors
+    E, F = pot.energy_forces(d["coords"], d["species"], d["box"])
+    assert torch.isfinite(F).all()
+
+
+def test_capacity_overflow_grows_and_retries(torch_cuda):
+    pot, orc = make("ani4")
+    pot.reserve(4000, 1, 32, 32)   # too small for liquid water (~60 radial neighbours)
+    s = synth.water_box(300, 20.5, 7, seed=13)
+    check_system(pot, orc, s, aev=False)
+
+
+def test_host_entry_point(torch_cuda):
+    pot, orc = make("ani4")
+    s = synth.water_box(300, 20.5, 7, seed=14)
+    E, F = pot.energy_forces_host(s.coords, s.species, s.box)
+    ref = orc.energy_forces(s.coords, s.species, s.box)
+    assert abs(E - ref["energy"]) <= E_TOL
+    assert force_errors(F, ref["forces"])[0] <= 1e-4 * np.sqrt(np.mean(ref["forces"] ** 2))
+
+
+def test_solvated100k_sampled(torch_cuda):
+    """Full-size 100k-atom, 7-species, 8-network system: sampled atoms against the
+    oracle (per-atom energies, AEV rows and forces computed one by one), plus
+    properties that hold at any size (net force ~ 0)."""
+    import torch
+    pot, orc = make("ani7x8")
+    s = synth.workload("solvated100k")[0][0]
+    d = to_cuda(s)
+    outs = pot.energy_forces_batch([d], atom_energies=True)
+    E = float(outs[0]["energy"].cpu()[0])
+    F = outs[0]["forces"].cpu().numpy()
+    ae = outs[0]["atom_energies"].cpu().numpy()
+    assert E == pytest.approx(ae.astype(np.float64).sum(), rel=1e-6)
+    rng = np.random.Generator(np.random.PCG64(0))
+    idx = np.concatenate([np.arange(0, 1000, 97), rng.choice(s.n_atoms, 24, replace=False)])
+    ref = orc.sample(s.coords, s.species, idx, s.box, want_aev=True)
+    np.testing.assert_allclose(ae[idx], ref["atom_energies"], rtol=1e-4, atol=1e-5)
+    rms, _ = force_errors(F[idx], ref["forces"])
+    assert rms <= 1e-4 * np.sqrt(np.mean(ref["forces"] ** 2)) + 1e-6
+    G = pot.debug_rows(0, s.n_atoms)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    np.testing.assert_allclose(G, ref["aev"], rtol=2e-5, atol=1e-6)
+    assert np.abs(F.astype(np.float64).sum(0)).max() < 1e-2
