@@ -214,6 +214,43 @@ const char* nnp_profile_stage_name(int i);
 /* Thread-local description of the last error (empty string if none). */
 const char* nnp_last_error(void);
 
+/* ---------------------------------------------------------------- allocation-free call
+ * nnp_energy_forces_noalloc: the same evaluation as nnp_energy_forces, for
+ * callers that cannot let the library allocate device memory while they run --
+ * for example an MD engine that reserves the whole HBM budget for itself up
+ * front (an allocation would then fail), or a time loop in which a cudaMalloc
+ * or cudaFree would stall the whole device.  The paper has no counterpart of
+ * this entry point; it is a deployment aid.
+ *
+ * Its work buffers live in one file-scope device array of
+ * NNP_NOALLOC_SCRATCH_BYTES bytes (32 MiB) that every GPU holds from the moment
+ * the library is loaded until the process exits.  The call performs no
+ * cudaMalloc, no cudaFree and no allocating library call.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.
+ *
+ * Limits: one system, FP32 handles only (NNP_ERR_UNSUPPORTED otherwise); the
+ * atoms in the mask, their neighbour lists (at most 256 radial and 96 angular
+ * neighbours per atom) and the network activations must fit in the array --
+ * about 4000 atoms for the 4-species 384-160-128-96-1 network, fewer for wider
+ * or ensemble networks.  A larger request returns NNP_ERR_ARG with a message
+ * giving the bytes needed and the limit, before any work is enqueued.
+ *
+ * Every call reuses the same array and overwrites what the previous call left
+ * there (the call clears its counters and accumulators itself).  Calls whose
+ * GPU work overlaps -- on two streams, from two threads or through two handles
+ * -- therefore race and return wrong results; serialise them.
+ *
+ * Arguments as for nnp_energy_forces.  The call is synchronous: it waits for
+ * `stream` and returns NNP_OK or the error the device detected
+ * (NNP_ERR_SPECIES, NNP_ERR_NONFINITE, or NNP_ERR_CAPACITY if an atom has more
+ * neighbours than the fixed lists hold). */
+#define NNP_NOALLOC_SCRATCH_BYTES (32u << 20)
+int nnp_energy_forces_noalloc(nnp_handle* h, int64_t n_atoms, const float* coords,
+                              const uint8_t* species, const double* box_host,
+                              const uint8_t* mask, double* energy, float* forces,
+                              double* virial, void* stream);
+
 /* ---------------------------------------------------------------- diagnostics
  * Read back intermediate results of the LAST compute call on this handle (for
  * parity tests against a reference implementation).  Asynchronous on `stream`;

@@ -37,7 +37,7 @@ EXPORTS = (
     "nnp_create", "nnp_clone", "nnp_destroy", "nnp_reserve", "nnp_energy_forces",
     "nnp_energy_forces_batch", "nnp_energy_forces_host", "nnp_sync_status", "nnp_aev_dim",
     "nnp_last_launch_count", "nnp_last_error", "nnp_debug_rows", "nnp_debug_neighbors",
-    "nnp_profile", "nnp_profile_read", "nnp_profile_stage_name",
+    "nnp_profile", "nnp_profile_read", "nnp_profile_stage_name", "nnp_energy_forces_noalloc",
 )
 
 
@@ -101,6 +101,7 @@ def lib():
     L.nnp_last_error.argtypes = []
     L.nnp_debug_rows.argtypes = [P, i, P, P]
     L.nnp_debug_neighbors.argtypes = [P, i, i, P, P]
+    L.nnp_energy_forces_noalloc.argtypes = [P, i64, P, P, P, P, P, P, P, P]
     L.nnp_profile.argtypes = [P, i]
     L.nnp_profile_read.argtypes = [P, i, P, P, i, P]
     L.nnp_profile_stage_name.restype = ctypes.c_char_p

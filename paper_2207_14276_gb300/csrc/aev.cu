@@ -457,4 +457,25 @@ cudaError_t aev_set_smem_limits(const Ws& ws) {
   return cudaFuncSetAttribute(k_aev_bwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
+// raise (never lower) the dynamic shared-memory limit of the AEV kernels to what
+// a launch over `ws` needs
+cudaError_t aev_ensure_smem(const Ws& ws) {
+  const int need_f = (int)aev_fwd_smem(ws), need_b = (int)aev_bwd_smem(ws);
+  const void* fwd[2] = {(const void*)k_aev_fwd<32>, (const void*)k_aev_fwd<0>};
+  const void* bwd[2] = {(const void*)k_aev_bwd<32>, (const void*)k_aev_bwd<0>};
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < 2; ++i) {
+      const void* fn = pass == 0 ? fwd[i] : bwd[i];
+      const int need = pass == 0 ? need_f : need_b;
+      cudaFuncAttributes attr;
+      cudaError_t e = cudaFuncGetAttributes(&attr, fn);
+      if (e != cudaSuccess) return e;
+      if (attr.maxDynamicSharedSizeBytes < need) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        if (e != cudaSuccess) return e;
+      }
+    }
+  return cudaSuccess;
+}
+
 }  // namespace nnp

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -707,3 +708,190 @@ int nnp_debug_neighbors(nnp_handle* h, int angular, int cap, int* out, void* str
 }
 
 }  // extern "C"
+
+// ================================================================ allocation-free variant
+// nnp_energy_forces_noalloc: the nnp_energy_forces kernel chain with its work
+// buffers carved from one file-scope device array instead of the handle's
+// cudaMalloc'd arena.  For callers that may not have the library allocate
+// device memory while they run (an engine that owns the whole HBM budget, or a
+// time loop where an allocation would stall or fail).  Nothing here allocates:
+// the array is part of the loaded module, and its device address is looked up
+// once per device.
+namespace {
+
+constexpr size_t kNoAllocBytes = NNP_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoAllocCapR = 256;  // radial neighbours per atom held by the fixed lists
+constexpr int kNoAllocCapA = 96;   // angular neighbours per atom
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kNoAllocMaxDevices] = {nullptr};
+
+// device address of the scratch array on the current device (looked up on first use)
+int noalloc_base(void** out) {
+  int dev = -1;
+  CU_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(NNP_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(NNP_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") +
+                                    cudaGetErrorString(e));
+    g_noalloc_base[dev] = p;
+  }
+  *out = g_noalloc_base[dev];
+  return NNP_OK;
+}
+
+// lay out the buffers of one n-atom system over `base` (nullptr: only measure)
+size_t noalloc_carve(const Model& m, int n_atoms, char* base, Ws* ws, MlpBufs* mb) {
+  const int S = m.ac.S, Dp = m.ac.Dp, E = m.md.E;
+  const size_t n = std::max(n_atoms, 1);
+  const size_t cells = 2 * n + 27;
+  const size_t rows = n + (size_t)S * kRowTile;
+  Carve c{base};
+  ws->status = c.take<int>(4);
+  ws->sys = c.take<SysDev>(1);
+  ws->n_sys = 1;
+  ws->n_in = n_atoms;
+  ws->cell_cap = (int)cells;
+  ws->row_cap = (int)rows;
+  ws->cap_r = kNoAllocCapR;
+  ws->cap_a = kNoAllocCapA;
+  ws->species_count = c.take<int>(kMaxSpecies);
+  ws->species_fill = c.take<int>(kMaxSpecies);
+  ws->seg_start = c.take<int>(kMaxSpecies + 1);
+  ws->totals = c.take<int>(4);
+  ws->cell_count = c.take<int>(cells);
+  ws->cell_start = c.take<int>(cells + 1);
+  ws->in_cell = c.take<int>(n);
+  ws->in_rank = c.take<int>(n);
+  ws->in_slot = c.take<int>(n);
+  ws->in_sys = c.take<int>(n);
+  ws->xyzq = c.take<float4>(n);
+  ws->pos_src = c.take<int>(n);
+  ws->pos_slot = c.take<int>(n);
+  ws->pos_sys = c.take<int>(n);
+  ws->pos_cell = c.take<int>(n);
+  ws->slot_pos = c.take<int>(rows);
+  ws->nb_cnt = c.take<uint16_t>(n * 16);
+  ws->nb_r = c.take<int>(n * kNoAllocCapR);
+  ws->nb_a = c.take<int>(n * kNoAllocCapA);
+  ws->aev = c.take<float>(rows * Dp);
+  ws->dEdG = c.take<float>(rows * Dp);
+  ws->atom_e = c.take<float>(rows);
+  ws->f_pos = c.take<float4>(n);
+  mb->H1 = c.take<float>(rows * E * m.md.h1);
+  mb->D1 = c.take<float>(rows * E * m.md.h1);
+  mb->H2 = c.take<float>(rows * E * m.md.h2);
+  mb->D2 = c.take<float>(rows * E * m.md.h2);
+  mb->d3 = c.take<float>(rows * E * m.md.h3);
+  mb->e_row = c.take<float>((size_t)E * rows);
+  mb->aev_h = nullptr;
+  return align_up(c.off, 256);
+}
+
+}  // namespace
+
+extern "C" int nnp_energy_forces_noalloc(nnp_handle* h, int64_t n_atoms, const float* coords,
+                                         const uint8_t* species, const double* box_host,
+                                         const uint8_t* mask, double* energy, float* forces,
+                                         double* virial, void* stream) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  const Model& m = *h->model;
+  if (m.precision != NNP_FP32)
+    return fail(NNP_ERR_UNSUPPORTED, "the allocation-free entry point runs FP32 handles only");
+  nnp_system_t s{};
+  s.n_atoms = n_atoms;
+  s.coords = coords;
+  s.species = species;
+  s.mask = mask;
+  s.periodic = box_host != nullptr;
+  if (box_host)
+    for (int c = 0; c < 3; ++c) s.box[c] = box_host[c];
+  s.energy = energy;
+  s.forces = forces;
+  s.virial = virial;
+  int rc = validate_system(h, s);
+  if (rc) return rc;
+  if (n_atoms > (1 << 24)) return fail(NNP_ERR_ARG, "too many atoms");
+  Ws ws{};
+  MlpBufs mb{};
+  const size_t need = noalloc_carve(m, (int)n_atoms, nullptr, &ws, &mb);
+  if (need > kNoAllocBytes)
+    return fail(NNP_ERR_ARG, "system needs " + std::to_string(need) +
+                                 " bytes of work space; the allocation-free entry point has " +
+                                 std::to_string(kNoAllocBytes) + " (NNP_NOALLOC_SCRATCH_BYTES)");
+  void* base = nullptr;
+  rc = noalloc_base(&base);
+  if (rc) return rc;
+  noalloc_carve(m, (int)n_atoms, static_cast<char*>(base), &ws, &mb);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // a stale error of an earlier runtime call is not this call's
+  // the fixed neighbour lists may need more shared memory than other handles set up
+  CU_TRY(aev_ensure_smem(ws));
+  // the status word starts at zero on every call; the kernels clear the rest
+  CU_TRY(cudaMemsetAsync(ws.status, 0, 4 * sizeof(int), st));
+  if (n_atoms == 0) {
+    CU_TRY(cudaMemsetAsync(energy, 0, sizeof(double), st));
+    if (virial) CU_TRY(cudaMemsetAsync(virial, 0, 9 * sizeof(double), st));
+  } else {
+    BatchParams bp{};
+    bp.sys_base = 0;
+    bp.n_sys = 1;
+    SysIn& si = bp.sys[0];
+    si.coords = coords;
+    si.species = species;
+    si.mask = mask;
+    si.energy = energy;
+    si.forces = forces;
+    si.virial = virial;
+    si.atom_e = nullptr;
+    si.n_in = (int)n_atoms;
+    si.in_base = 0;
+    si.periodic = s.periodic;
+    for (int c = 0; c < 3; ++c)
+      split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c]);
+    const int n = (int)n_atoms;
+    // each stage's launch status is checked so that a failure names its stage
+    auto stage_ok = [&](const char* name) -> int {
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return fail(NNP_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
+      return NNP_OK;
+    };
+    launch_init_chunk(ws, bp, st);
+    if ((rc = stage_ok("init"))) return rc;
+    launch_prep_atoms(ws, bp, n, m.ac.S, st);
+    if ((rc = stage_ok("prep"))) return rc;
+    launch_setup(ws, m.ac, st);
+    launch_bin(ws, n, st);
+    launch_scan(ws, st);
+    launch_scatter(ws, n, st);
+    if ((rc = stage_ok("cells"))) return rc;
+    launch_neighbors(ws, n, m.ac, st);
+    if ((rc = stage_ok("neighbors"))) return rc;
+    launch_aev_fwd(ws, n, m.ac, st);
+    if ((rc = stage_ok("aev_fwd"))) return rc;
+    launch_mlp_fp32(ws, m.md, m.mw, mb, m.alpha, st, nullptr, nullptr);
+    if ((rc = stage_ok("mlp"))) return rc;
+    launch_aev_bwd(ws, n, m.ac, virial ? 1 : 0, st);
+    if ((rc = stage_ok("aev_bwd"))) return rc;
+    launch_finalize_e(ws, n, mb.e_row, m.md.E, ws.row_cap, m.ebias, st);
+  }
+  CU_TRY(cudaGetLastError());
+  int status[4] = {0, 0, 0, 0};
+  CU_TRY(cudaMemcpyAsync(status, ws.status, sizeof(status), cudaMemcpyDeviceToHost, st));
+  CU_TRY(cudaStreamSynchronize(st));
+  if (status[0] & kStSpecies) return fail(NNP_ERR_SPECIES, "species index out of range");
+  if (status[0] & kStNonFinite) return fail(NNP_ERR_NONFINITE, "non-finite coordinate in the ML region");
+  if (status[0] & (kStCapacity | kStCells))
+    return fail(NNP_ERR_CAPACITY, "an atom has more than " + std::to_string(kNoAllocCapR) +
+                                      " radial or " + std::to_string(kNoAllocCapA) +
+                                      " angular neighbours (fixed lists of the allocation-free entry point)");
+  return NNP_OK;
+}

@@ -125,6 +125,7 @@ void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st)
 void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
                     cudaStream_t st);
 cudaError_t aev_set_smem_limits(const Ws& ws);
+cudaError_t aev_ensure_smem(const Ws& ws);
 size_t aev_fwd_smem(const Ws& ws);
 size_t aev_bwd_smem(const Ws& ws);
 // ---- finalize.cu
