@@ -25,7 +25,7 @@ using namespace nnp;
 namespace nnp {
 void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st);
 int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
-                  float alpha, cudaStream_t st, int* n_launch, StageHook* hook);
+                  float alpha, cudaStream_t st, int* n_launch, StageHook* hook, void* state);
 int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, int row_cap,
                    const float* aev, float* dEdG, void** state);
 void mlp_tc_release(void* state);
@@ -208,6 +208,28 @@ int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
   if ((rc = upf(W2T, &m->mw.W2T))) return rc;
   if ((rc = upf(W1Tcat, &m->mw.W1Tcat))) return rc;
   if ((rc = upload(ebias.data(), S * sizeof(double), reinterpret_cast<void**>(&m->ebias)))) return rc;
+  if (precision == NNP_BF16_MLP) {
+    // BF16 copies of the GEMM operands (round to nearest even)
+    auto to_bf16 = [](const std::vector<float>& v) {
+      std::vector<uint16_t> o(v.size());
+      for (size_t i = 0; i < v.size(); ++i) {
+        uint32_t u;
+        std::memcpy(&u, &v[i], 4);
+        o[i] = (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+      }
+      return o;
+    };
+    auto upb = [&](const std::vector<float>& v, void** dst) {
+      std::vector<uint16_t> b = to_bf16(v);
+      return upload(b.data(), b.size() * sizeof(uint16_t), dst);
+    };
+    if ((rc = upb(W1cat, &m->mw.W1cat_h))) return rc;
+    if ((rc = upb(W2, &m->mw.W2_h))) return rc;
+    if ((rc = upb(W3, &m->mw.W3_h))) return rc;
+    if ((rc = upb(W3T, &m->mw.W3T_h))) return rc;
+    if ((rc = upb(W2T, &m->mw.W2T_h))) return rc;
+    if ((rc = upb(W1Tcat, &m->mw.W1Tcat_h))) return rc;
+  }
   return NNP_OK;
 }
 
@@ -447,7 +469,7 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
     launches += 6;
     StageHook hook{h, st};
     if (m.precision == NNP_BF16_MLP) {
-      rc = launch_mlp_tc(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook);
+      rc = launch_mlp_tc(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, h->tc_state);
       if (rc) return rc;
     } else {
       launch_mlp_fp32(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook);

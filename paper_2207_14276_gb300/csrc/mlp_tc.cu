@@ -1,19 +1,514 @@
-// Tensor-core (tcgen05, BF16 operands, FP32 accumulation) path of the
-// per-species networks.  Placeholder until the kernels land.
+// Tensor-core path of the per-species networks (paper Eq. 2): BF16 operands,
+// FP32 accumulation in tensor memory, on the 5th-generation tensor cores.
+//
+// Each CTA computes one 128-row x n_tile output tile of one layer GEMM
+//   C[m, n] = sum_k A[m, e*K + k] * B_{e,s}[n, k]
+// for the species s of its 128-row segment and the ensemble member e.
+//   warp 4   TMA producer: 64-wide K slices of A and B into a ring of shared
+//            memory stages (128-byte swizzle), completion on mbarriers
+//   warp 5   MMA issuer: tcgen05.mma kind::f16 (M = 128, N = n_tile, K = 16)
+//            into a TMEM accumulator; tcgen05.commit frees a stage
+//   warps 0-3 epilogue: tcgen05.ld of its 32 accumulator rows, bias, CELU and
+//            CELU', the width-1 output layer as a dot product, products with
+//            stored derivatives; BF16 (or FP32 for dE/dG) stores.
+// Every mbarrier wait is bounded; a CTA that gives up sets the status word,
+// drains the copies it issued, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <vector>
+
 #include "../../include/nnp.h"
 #include "mlp.cuh"
 
 namespace nnp {
 
-int launch_mlp_tc(const Ws&, const MlpDims&, const MlpWeights&, const MlpBufs&, float,
-                  cudaStream_t, int*, StageHook*) {
-  return NNP_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;           // bf16 elements per K slice (one 128-byte swizzle row)
+constexpr int kThreads = 192;
+constexpr int kStages = 4;
+constexpr unsigned kWaitLimit = 1u << 24;
+
+struct TcArgs {
+  int N, K, n_tile, n_k, tmem_cols;
+  int a_c1_per_e;       // A map coordinate 1 = e * a_c1_per_e (net slice)
+  int b_c2_per_e;       // B map coordinate 2 = e * b_c2_per_e + s
+  uint32_t idesc;
+  int epi;
+  const float* bias; long long bias_s, bias_e;
+  const float* w4; long long w4_s, w4_e;
+  void* out; int ldo; int out_net;          // bf16 (or fp32 for kEpiStore)
+  void* out2;                               // bf16 CELU' (kEpiCelu)
+  const void* aux; int ld_aux; int aux_net; // bf16 stored CELU' (kEpiMul)
+  float* e_row; int e_row_net;
+  float alpha;
+  const int* seg_start;
+  int S;
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-int mlp_tc_prepare(const MlpDims&, const MlpWeights&, const MlpBufs&, int, const float*, float*,
-                   void** state) {
-  *state = nullptr;
-  return NNP_ERR_UNSUPPORTED;
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-void mlp_tc_release(void*) {}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false if the limit was hit or another role gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+// bounded wait that ignores the abort flag (used to drain in-flight work)
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version
+  d |= (uint64_t)2 << 61;               // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11,"
+      " %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float celu_f(float z, float alpha, float inv_alpha) {
+  return z > 0.f ? z : alpha * (__expf(z * inv_alpha) - 1.f);
+}
+__device__ __forceinline__ float celu_d(float z, float inv_alpha) {
+  return z > 0.f ? 1.f : __expf(z * inv_alpha);
+}
+
+__device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float (&v)[16]) {
+  uint32_t w[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    w[i] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+__device__ __forceinline__ void load_bf16x16(const __nv_bfloat16* src, float (&v)[16]) {
+  const uint4* s = reinterpret_cast<const uint4*>(src);
+  uint4 q[2] = {s[0], s[1]};
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(q);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
+    float2 f = __bfloat1622float2(h);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, TcArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const int m0 = blockIdx.x * kBM;
+  const int total = g.seg_start[g.S];
+  if (m0 >= total) return;
+  int s = 0;
+  while (s + 1 < g.S && m0 >= g.seg_start[s + 1]) ++s;
+  const int e = blockIdx.z;
+  const int n0 = blockIdx.y * g.n_tile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int a_bytes = kBM * kBK * 2, b_bytes = g.n_tile * kBK * 2;
+  const int stage_bytes = a_bytes + b_bytes;   // multiple of 1024
+  volatile int* abort_flag = &abort_sh;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"((uint32_t)g.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  int issued = 0, consumed = 0;
+  if (warp == 4 && lane == 0) {
+    // ---- TMA producer
+    const int a_c1 = e * g.a_c1_per_e, b_c2 = e * g.b_c2_per_e + s;
+    for (int kb = 0; kb < g.n_k; ++kb) {
+      const int st = kb % kStages;
+      const unsigned round = kb / kStages;
+      if (kb >= kStages && !mbar_wait(&empty_bar[st], (round - 1) & 1, abort_flag)) break;
+      uint8_t* sa = smem + st * stage_bytes;
+      uint8_t* sb = sa + a_bytes;
+      mbar_expect_tx(&full_bar[st], (unsigned)stage_bytes);
+      tma_load_3d(sa, &ta, &full_bar[st], kb * kBK, a_c1, m0);
+      tma_load_3d(sb, &tb, &full_bar[st], kb * kBK, n0, b_c2);
+      ++issued;
+    }
+    // make sure every issued copy has landed before the CTA may exit
+    if (*abort_flag)
+      for (int kb = 0; kb < issued; ++kb) mbar_drain(&full_bar[kb % kStages], (kb / kStages) & 1);
+  } else if (warp == 5 && lane == 0) {
+    // ---- MMA issuer
+    for (int kb = 0; kb < g.n_k; ++kb) {
+      const int st = kb % kStages;
+      if (!mbar_wait(&full_bar[st], (kb / kStages) & 1, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t sa = smem_u32(smem + st * stage_bytes);
+      const uint32_t sb = sa + a_bytes;
+      const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sb);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk)
+        umma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), g.idesc,
+                  (kb > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(&empty_bar[st]);
+      ++consumed;
+    }
+    umma_commit(&done_bar);   // arrives when every MMA issued above has completed
+  }
+  (void)consumed;
+
+  if (warp < 4) {
+    // ---- epilogue: thread owns accumulator row m
+    const bool ok = mbar_wait(&done_bar, 0, abort_flag);
+    tc_fence_after();
+    if (ok && !*abort_flag) {
+      const int m = m0 + warp * 32 + lane;
+      const float alpha = g.alpha, inv_alpha = 1.f / g.alpha;
+      float dot = 0.f;
+      for (int c0 = 0; c0 < g.n_tile; c0 += 16) {
+        const int n = n0 + c0;
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (n >= g.N) continue;
+        if (g.epi == kEpiCelu || g.epi == kEpiCeluDot) {
+          const float* bp = g.bias + e * g.bias_e + s * g.bias_s + n;
+          float h[16], dd[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float z = v[i] + bp[i];
+            h[i] = celu_f(z, alpha, inv_alpha);
+            dd[i] = celu_d(z, inv_alpha);
+          }
+          __nv_bfloat16* o = static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)e * g.out_net + n;
+          if (g.epi == kEpiCelu) {
+            store_bf16x16(o, h);
+            __nv_bfloat16* o2 = static_cast<__nv_bfloat16*>(g.out2) + (size_t)m * g.ldo + (size_t)e * g.out_net + n;
+            store_bf16x16(o2, dd);
+          } else {
+            const float* wp = g.w4 + e * g.w4_e + s * g.w4_s + n;
+            float d3[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              dot = fmaf(h[i], wp[i], dot);
+              d3[i] = wp[i] * dd[i];
+            }
+            store_bf16x16(o, d3);
+          }
+        } else if (g.epi == kEpiMul) {
+          float a[16];
+          load_bf16x16(static_cast<const __nv_bfloat16*>(g.aux) + (size_t)m * g.ld_aux + (size_t)e * g.aux_net + n, a);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] *= a[i];
+          store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)e * g.out_net + n, v);
+        } else {
+          float4* o = reinterpret_cast<float4*>(static_cast<float*>(g.out) + (size_t)m * g.ldo + n);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+      }
+      if (g.epi == kEpiCeluDot) g.e_row[(size_t)e * g.e_row_net + m] = dot;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) {
+      atomicOr(g.status, kStTimeout);
+      mbar_drain(&done_bar, 0);   // outstanding MMAs finish before the memory is freed
+    }
+    __syncthreads();
+  }
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)g.tmem_cols)
+                 : "memory");
+}
+
+__global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                          const int* seg_start, int S, int Dp) {
+  const long long total = (long long)seg_start[S] * Dp / 4;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = reinterpret_cast<const float4*>(src)[i];
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 w = make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+    reinterpret_cast<uint2*>(dst)[i] = w;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3D bf16 map: dims (d0 innermost, d1, d2), strides in elements for d1 and d2, box (64, b1, b2)
+bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t st1,
+              uint64_t st2, uint32_t b1, uint32_t b2) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {st1 * 2, st2 * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kBK, b1, b2};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+struct TcGemmPlan {
+  CUtensorMap ta, tb;
+  TcArgs a;
+  dim3 grid;
+  size_t smem;
+  int stage_id;
+};
+
+struct TcState {
+  std::vector<TcGemmPlan> plans;
+  void* aev_h = nullptr;
+  const float* aev = nullptr;
+  float* e_row = nullptr;
+  int row_cap = 0, Dp = 0, E = 1;
+};
+
+int pick_n_tile(int N, int row_tiles, bool single) {
+  int nt = N <= 256 ? N : 256;
+  if (!single) {
+    // more CTAs for small problems: split N while there is less than one wave
+    while (row_tiles * ((N + nt - 1) / nt) < 148 && nt % 32 == 0 && nt > 64) nt /= 2;
+  }
+  return nt;
+}
+
+int tmem_cols_for(int n_tile) {
+  int c = 32;
+  while (c < n_tile) c <<= 1;
+  return c;
+}
+
+}  // namespace
+
+int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, int row_cap,
+                   const float* aev, float* dEdG, void** state_out) {
+  *state_out = nullptr;
+  if (!encode_fn()) return NNP_ERR_CUDA;
+  if (!mw.W1cat_h || !mb.aev_h) return NNP_ERR_ARG;
+  TcState* st = new TcState;
+  st->aev_h = mb.aev_h;
+  st->aev = aev;
+  st->e_row = mb.e_row;
+  st->row_cap = row_cap;
+  st->Dp = md.Dp;
+  st->E = md.E;
+  const int S = md.S, E = md.E, Dp = md.Dp, h1 = md.h1, h2 = md.h2, h3 = md.h3;
+  const uint64_t R = (uint64_t)row_cap;
+  const int row_tiles = (row_cap + kBM - 1) / kBM;
+  struct L {
+    int stage, epi, N, K, nets;
+    const void* A; uint64_t a_d0, a_d1, a_st1, a_st2;
+    const void* B; uint64_t b_d0, b_d1, b_d2;
+    int b_c2_per_e;
+    const float* bias; long long bias_s, bias_e;
+    const float* w4; long long w4_s, w4_e;
+    void* out; int ldo, out_net; void* out2; const void* aux; int ld_aux, aux_net;
+  };
+  std::vector<L> layers = {
+      // L1: AEV x [W1 of all members]^T
+      {3, kEpiCelu, E * h1, Dp, 1, mb.aev_h, (uint64_t)Dp, 1, (uint64_t)Dp, (uint64_t)Dp,
+       mw.W1cat_h, (uint64_t)Dp, (uint64_t)E * h1, (uint64_t)S, 0, mw.b1cat, (long long)E * h1, 0,
+       nullptr, 0, 0, mb.H1, E * h1, 0, mb.D1, nullptr, 0, 0},
+      // L2 per member
+      {4, kEpiCelu, h2, h1, E, mb.H1, (uint64_t)h1, (uint64_t)E, (uint64_t)h1, (uint64_t)E * h1,
+       mw.W2_h, (uint64_t)h1, (uint64_t)h2, (uint64_t)E * S, S, mw.b2, h2, (long long)S * h2,
+       nullptr, 0, 0, mb.H2, E * h2, h2, mb.D2, nullptr, 0, 0},
+      // L3 + output dot
+      {5, kEpiCeluDot, h3, h2, E, mb.H2, (uint64_t)h2, (uint64_t)E, (uint64_t)h2, (uint64_t)E * h2,
+       mw.W3_h, (uint64_t)h2, (uint64_t)h3, (uint64_t)E * S, S, mw.b3, h3, (long long)S * h3,
+       mw.w4, h3, (long long)S * h3, mb.d3, E * h3, h3, nullptr, nullptr, 0, 0},
+      // B3: delta2 = (delta3 W3) * D2, written over H2
+      {6, kEpiMul, h2, h3, E, mb.d3, (uint64_t)h3, (uint64_t)E, (uint64_t)h3, (uint64_t)E * h3,
+       mw.W3T_h, (uint64_t)h3, (uint64_t)h2, (uint64_t)E * S, S, nullptr, 0, 0, nullptr, 0, 0,
+       mb.H2, E * h2, h2, nullptr, mb.D2, E * h2, h2},
+      // B2: delta1 = (delta2 W2) * D1, written over H1
+      {7, kEpiMul, h1, h2, E, mb.H2, (uint64_t)h2, (uint64_t)E, (uint64_t)h2, (uint64_t)E * h2,
+       mw.W2T_h, (uint64_t)h2, (uint64_t)h1, (uint64_t)E * S, S, nullptr, 0, 0, nullptr, 0, 0,
+       mb.H1, E * h1, h1, nullptr, mb.D1, E * h1, h1},
+      // B1: dE/dG = [delta1_e] [W1_e / E]   (K = E*h1), FP32 output
+      {8, kEpiStore, Dp, E * h1, 1, mb.H1, (uint64_t)E * h1, 1, (uint64_t)E * h1, (uint64_t)E * h1,
+       mw.W1Tcat_h, (uint64_t)E * h1, (uint64_t)Dp, (uint64_t)S, 0, nullptr, 0, 0, nullptr, 0, 0,
+       dEdG, Dp, 0, nullptr, nullptr, 0, 0},
+  };
+  for (const L& l : layers) {
+    TcGemmPlan p{};
+    const bool single = (l.epi == kEpiCeluDot);
+    const int nt = pick_n_tile(l.N, row_tiles * l.nets, single);
+    if (nt % 16 != 0 || nt > 256 || (single && nt < l.N)) { delete st; return NNP_ERR_UNSUPPORTED; }
+    if (!make_map(&p.ta, l.A, l.a_d0, l.a_d1, R, l.a_st1, l.a_st2, 1, kBM) ||
+        !make_map(&p.tb, l.B, l.b_d0, l.b_d1, l.b_d2, l.b_d0, l.b_d0 * l.b_d1, (uint32_t)nt, 1)) {
+      delete st;
+      return NNP_ERR_CUDA;
+    }
+    TcArgs& a = p.a;
+    a.N = l.N; a.K = l.K; a.n_tile = nt; a.n_k = (l.K + kBK - 1) / kBK;
+    a.tmem_cols = tmem_cols_for(nt);
+    a.a_c1_per_e = (l.nets > 1) ? 1 : 0;
+    a.b_c2_per_e = l.b_c2_per_e;
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+    a.epi = l.epi;
+    a.bias = l.bias; a.bias_s = l.bias_s; a.bias_e = l.bias_e;
+    a.w4 = l.w4; a.w4_s = l.w4_s; a.w4_e = l.w4_e;
+    a.out = l.out; a.ldo = l.ldo; a.out_net = l.out_net; a.out2 = l.out2;
+    a.aux = l.aux; a.ld_aux = l.ld_aux; a.aux_net = l.aux_net;
+    a.e_row = mb.e_row; a.e_row_net = row_cap;
+    p.grid = dim3(row_tiles, (l.N + nt - 1) / nt, l.nets);
+    // shared memory: stages plus 1 KB for alignment; never so little that more CTAs
+    // would share an SM than its 512 tensor-memory columns can hold
+    size_t sm = (size_t)kStages * (kBM * kBK * 2 + nt * kBK * 2) + 1024;
+    const int max_ctas = 512 / a.tmem_cols;
+    const size_t floor_sm = 232448 / (size_t)(max_ctas + 1) + 1;
+    p.smem = sm > floor_sm ? sm : floor_sm;
+    if (p.smem > 232448 - 2048) { delete st; return NNP_ERR_UNSUPPORTED; }
+    p.stage_id = l.stage;
+    st->plans.push_back(p);
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 2048);
+  if (e != cudaSuccess) { delete st; return NNP_ERR_CUDA; }
+  *state_out = st;
+  return NNP_OK;
+}
+
+void mlp_tc_release(void* state) { delete static_cast<TcState*>(state); }
+
+int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, float alpha,
+                  cudaStream_t st, int* n_launch, StageHook* hook, void* state) {
+  (void)mw; (void)mb;
+  TcState* s = static_cast<TcState*>(state);
+  if (!s) return NNP_ERR_ARG;
+  if (hook) hook->begin(11);
+  k_to_bf16<<<4 * 152, 256, 0, st>>>(ws.aev, static_cast<__nv_bfloat16*>(s->aev_h), ws.seg_start, md.S, md.Dp);
+  if (hook) hook->end();
+  for (auto& p : s->plans) {
+    TcArgs a = p.a;
+    a.alpha = alpha;
+    a.seg_start = ws.seg_start;
+    a.S = md.S;
+    a.status = ws.status;
+    if (hook) hook->begin(p.stage_id);
+    k_gemm_tc<<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a);
+    if (hook) hook->end();
+  }
+  if (n_launch) *n_launch += 1 + (int)s->plans.size();
+  return NNP_OK;
+}
 
 }  // namespace nnp
