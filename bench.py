@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--serving-rates", default="1000,10000,50000",
+                    help="Poisson request rates (req/s) of the serving stream; '' to skip")
+    ap.add_argument("--serving-requests", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -246,6 +249,72 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ serving
+def drive_stream(srv, reqs, rids):
+    """Submit requests at their scheduled Poisson arrival times from this thread,
+    poll completions from a second one.  Latency = completion - scheduled arrival
+    (the lag of the submitting thread plus the server's submit-to-done time)."""
+    n = len(reqs)
+    tickets = [0] * n
+    lag = [0.0] * n
+    done = [None] * n
+
+    def poller():
+        for k in range(n):
+            while tickets[k] == 0:
+                time.sleep(0)
+            done[k] = srv.poll(tickets[k])
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter() + 0.02
+    for k, r in enumerate(reqs):
+        target = t0 + r.arrival_s
+        while True:
+            now = time.perf_counter()
+            if now >= target:
+                break
+            if target - now > 2e-3:
+                time.sleep(target - now - 1e-3)
+        if r.system is not None:
+            tk = srv.submit(r.system.coords, r.system.species)
+        else:
+            tk = srv.submit(r.solute_xyz, resident_id=rids[r.box_id])
+        lag[k] = time.perf_counter() - target
+        tickets[k] = tk
+    th.join()
+    lat = np.array([lag[k] + done[k][3] for k in range(n)])
+    bad = sum(1 for d in done if d[0] != 0)
+    makespan = max(reqs[k].arrival_s + lat[k] for k in range(n))
+    atoms = sum(r.n_ml for r in reqs)
+    return {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "atom_evals_per_s": atoms / makespan, "requests": n, "failed": bad}
+
+
+def run_serving(rates, n_requests, precision="bf16", lanes=2, max_systems=256,
+                max_atoms=262144, seed=3):
+    from paper_2207_14276_gb300 import Potential
+    from paper_2207_14276_gb300.serving import Server
+    spec = synth.model_spec("ani7")
+    pot = Potential(spec, synth.make_weights(spec, 1), precision=precision)
+    boxes = synth.resident_boxes()
+    srv = Server(pot, n_lanes=lanes, max_batch_atoms=max_atoms, max_batch_systems=max_systems)
+    rids = [srv.register(b.coords, b.species, b.box, b.mask) for b in boxes]
+    # warm-up: every lane sees a full-size batch once
+    drive_stream(srv, synth.request_stream(1e6, 64, seed=999, boxes=boxes), rids)
+    out = {}
+    for i, rate in enumerate(rates):
+        reqs = synth.request_stream(rate, n_requests, seed=seed + i, boxes=boxes)
+        b0, r0 = srv.stats()
+        res = drive_stream(srv, reqs, rids)
+        b1, r1 = srv.stats()
+        res["mean_batch"] = (r1 - r0) / max(b1 - b0, 1)
+        out[str(int(rate))] = res
+    srv.close()
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -376,6 +445,18 @@ def run_ours(args):
             dist.all_reduce(t, op=dist.ReduceOp.MIN)
             e2e["value"] = float(t.item()) * world
 
+    serving = None
+    if args.serving_rates and rank == 0:
+        rates = [float(r) for r in args.serving_rates.split(",") if r]
+        serving = {
+            "workload": "request stream: 70% gas-phase molecules of 10-120 atoms, 30% new "
+                        "solute coordinates (30-80 atoms) for one of 8 resident ~20k-atom "
+                        "solvated boxes (mask = solute); 7-species 1008-dim AEV, networks "
+                        "1008-256-192-160-1; Poisson arrivals; latency from scheduled arrival",
+            "batched_bf16": run_serving(rates, args.serving_requests, "bf16", lanes=2),
+            "one_system_per_launch_fp32": run_serving(rates[:2], args.serving_requests // 4,
+                                                      "fp32", lanes=1, max_systems=1),
+        }
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -405,6 +486,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1]},
         "neighbours_per_atom": {"radial": counts[0], "angular": counts[1]},
+        "serving": serving,
     }
     print(json.dumps(out))
     if dist is not None:

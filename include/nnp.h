@@ -185,6 +185,62 @@ int nnp_energy_forces_host(nnp_handle* h, int64_t n_atoms, const float* coords_h
                            const uint8_t* mask_h, double* energy_h, float* forces_h,
                            double* virial_h);
 
+/* ---------------------------------------------------------------- serving
+ * A continuous-batching server for streams of independent energy+force
+ * requests (many small molecules, or new solute coordinates for solvated boxes
+ * kept resident on the device -- the shape of the free-energy windows and
+ * replicas of the paper's hybrid simulations).  The server owns n_lanes lanes;
+ * each lane is a clone of `model` (shared weights, own work arena reserved for
+ * max_batch_atoms atoms and max_batch_systems systems), its own CUDA stream and
+ * a worker thread.  Requests join one FIFO queue; a free lane takes every queued
+ * request that fits its reservation (admission by device-memory footprint),
+ * stages the inputs with one host-to-device copy, evaluates them in one batched
+ * pass and copies the results back.  Lanes run concurrently, so batches overlap
+ * on the device, and requests arriving while lanes are busy are admitted as soon
+ * as a lane frees.
+ *
+ * nnp_request_t: HOST buffers owned by the caller, which must stay valid until
+ * the request is polled complete.
+ *   resident_id < 0: a standalone system of n_atoms atoms (coords [n,3],
+ *     species [n], mask [n] or NULL, box/periodic as in nnp_system_t);
+ *   resident_id >= 0: the first n_atoms atoms of the registered resident system
+ *     get the new coordinates `coords`; species, mask and box are the resident's.
+ *   energy: double[1] out; forces: float [n_atoms,3] out (NULL = not returned). */
+typedef struct {
+  int64_t n_atoms;
+  const float* coords;
+  const uint8_t* species;
+  const uint8_t* mask;
+  double box[3];
+  int periodic;
+  int resident_id;
+  double* energy;
+  float* forces;
+} nnp_request_t;
+
+typedef struct nnp_server nnp_server;
+
+/* Create a server on the current device.  `model` must outlive the server. */
+int nnp_server_create(const nnp_handle* model, int n_lanes, int64_t max_batch_atoms,
+                      int max_batch_systems, nnp_server** out);
+/* Stop the lanes (queued requests are finished first) and free everything. */
+void nnp_server_destroy(nnp_server* s);
+/* Keep a system resident on the device (host inputs copied once); *resident_id
+ * names it in later requests.  Synchronous. */
+int nnp_server_register(nnp_server* s, int64_t n_atoms, const float* coords_h,
+                        const uint8_t* species_h, const uint8_t* mask_h,
+                        const double* box_host, int* resident_id);
+/* Queue a request; *ticket identifies it.  Thread-safe.  NNP_ERR_OOM if the
+ * request does not fit a lane's reservation. */
+int nnp_server_submit(nnp_server* s, const nnp_request_t* request, uint64_t* ticket);
+/* NNP_PENDING while the request runs (wait = 0); with wait != 0 blocks until it
+ * completes.  On completion returns the request's status, writes the time from
+ * submission to completion (seconds) to *latency_s (may be NULL) and forgets
+ * the ticket. */
+int nnp_server_poll(nnp_server* s, uint64_t ticket, int wait, double* latency_s);
+/* Batches and requests completed so far (either pointer may be NULL). */
+int nnp_server_stats(nnp_server* s, long long* batches, long long* requests);
+
 /* Synchronise `stream`, read and clear the handle's device status word.  Returns
  * NNP_OK or the first device-detected error since the last check
  * (NNP_ERR_SPECIES, NNP_ERR_NONFINITE, NNP_ERR_CAPACITY, NNP_ERR_TIMEOUT).  After

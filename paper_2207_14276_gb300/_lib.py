@@ -38,6 +38,8 @@ EXPORTS = (
     "nnp_energy_forces_batch", "nnp_energy_forces_host", "nnp_sync_status", "nnp_aev_dim",
     "nnp_last_launch_count", "nnp_last_error", "nnp_debug_rows", "nnp_debug_neighbors",
     "nnp_profile", "nnp_profile_read", "nnp_profile_stage_name", "nnp_energy_forces_noalloc",
+    "nnp_server_create", "nnp_server_destroy", "nnp_server_register", "nnp_server_submit",
+    "nnp_server_poll", "nnp_server_stats",
 )
 
 
@@ -73,6 +75,14 @@ class SystemT(ctypes.Structure):
                 ("virial", ctypes.c_void_p), ("atom_energies", ctypes.c_void_p)]
 
 
+class RequestT(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("coords", ctypes.c_void_p),
+                ("species", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("box", ctypes.c_double * 3), ("periodic", ctypes.c_int),
+                ("resident_id", ctypes.c_int), ("energy", ctypes.c_void_p),
+                ("forces", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -102,6 +112,13 @@ def lib():
     L.nnp_debug_rows.argtypes = [P, i, P, P]
     L.nnp_debug_neighbors.argtypes = [P, i, i, P, P]
     L.nnp_energy_forces_noalloc.argtypes = [P, i64, P, P, P, P, P, P, P, P]
+    L.nnp_server_create.argtypes = [P, i, i64, i, ctypes.POINTER(P)]
+    L.nnp_server_destroy.argtypes = [P]
+    L.nnp_server_destroy.restype = None
+    L.nnp_server_register.argtypes = [P, i64, P, P, P, P, ctypes.POINTER(ctypes.c_int)]
+    L.nnp_server_submit.argtypes = [P, ctypes.POINTER(RequestT), ctypes.POINTER(ctypes.c_uint64)]
+    L.nnp_server_poll.argtypes = [P, ctypes.c_uint64, i, ctypes.POINTER(ctypes.c_double)]
+    L.nnp_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.nnp_profile.argtypes = [P, i]
     L.nnp_profile_read.argtypes = [P, i, P, P, i, P]
     L.nnp_profile_stage_name.restype = ctypes.c_char_p

@@ -1,0 +1,97 @@
+"""Continuous-batching server: every result is the same alone and in the mix.
+
+Requests of uneven sizes (gas-phase molecules of 10-120 atoms, and new solute
+coordinates for solvated boxes kept resident on the device, where only the
+solute is in the ML region) are submitted faster than one lane can serve them,
+so lanes form multi-request batches and two lanes overlap on the device.  Each
+result is compared with the same system evaluated alone through
+nnp_energy_forces.  FP32: the per-atom arithmetic is identical, only the order
+of FP32 additions differs, so energies agree to 1e-5 relative and forces to
+1e-4 of the force scale.  BF16: a last-bit FP32 difference in an AEV element can
+flip its BF16 rounding, so the two results may differ by up to twice the BF16
+error bound of tests/test_gpu_bf16.py (energy 2e-3 sum_i |E_i|, force RMS 2e-2
+of the force RMS).
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests._common import model_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_server_results_equal_alone(torch_cuda, precision):
+    torch = torch_cuda
+    from paper_2207_14276_gb300 import Potential
+    from paper_2207_14276_gb300.serving import Server
+    spec, w = model_for("ani7")
+    pot = Potential(spec, w, precision=precision)
+    srv = Server(pot, n_lanes=2, max_batch_atoms=40000, max_batch_systems=64)
+    boxes = [synth.solvated_solute(600, 40 + 10 * b, 27.0, seed=90 + b, mask_solute=True)
+             for b in range(2)]
+    rids = [srv.register(b.coords, b.species, b.box, b.mask) for b in boxes]
+    reqs = synth.request_stream(1e6, 60, seed=11, boxes=boxes)
+    tickets = []
+    for r in reqs:
+        if r.system is not None:
+            tickets.append(srv.submit(r.system.coords, r.system.species))
+        else:
+            tickets.append(srv.submit(r.solute_xyz, resident_id=rids[r.box_id]))
+    results = [srv.poll(t) for t in tickets]
+    batches, served = srv.stats()
+    assert served == len(reqs)
+    assert batches < served          # requests were batched together
+    for r, (rc, E, F, lat) in zip(reqs, results):
+        assert rc == 0
+        if r.system is not None:
+            s = r.system
+            x = torch.from_numpy(s.coords).cuda()
+            sp = torch.from_numpy(s.species).cuda()
+            o = pot.energy_forces_batch([{"coords": x, "species": sp}], atom_energies=True)[0]
+            E0, F0, ae = o["energy"], o["forces"].cpu().numpy(), o["atom_energies"].cpu().numpy()
+        else:
+            b = boxes[r.box_id]
+            xyz = b.coords.copy()
+            xyz[:r.solute_xyz.shape[0]] = r.solute_xyz
+            o = pot.energy_forces_batch([{"coords": torch.from_numpy(xyz).cuda(),
+                                          "species": torch.from_numpy(b.species).cuda(),
+                                          "box": list(b.box),
+                                          "mask": torch.from_numpy(b.mask).cuda()}],
+                                        atom_energies=True)[0]
+            E0, F0, ae = o["energy"], o["forces"].cpu().numpy(), o["atom_energies"].cpu().numpy()
+            F0 = F0[:r.solute_xyz.shape[0]]
+        E0 = float(E0.cpu()[0])
+        if precision == "fp32":
+            assert E == pytest.approx(E0, rel=1e-5, abs=1e-5)
+            scale = float(np.abs(F0).max()) + 1e-6
+            np.testing.assert_allclose(F, F0, atol=1e-4 * scale)
+        else:
+            assert abs(E - E0) <= 4e-3 * float(np.abs(ae).sum()) + 1e-5
+            d = (F - F0).astype(np.float64)
+            assert np.sqrt(np.mean(d * d)) <= 4e-2 * np.sqrt(np.mean(F0.astype(np.float64) ** 2)) + 1e-6
+    srv.close()
+
+
+def test_server_rejects_oversized_request(torch_cuda):
+    from paper_2207_14276_gb300 import NNPError, Potential
+    from paper_2207_14276_gb300.serving import Server
+    spec, w = model_for("ani4")
+    pot = Potential(spec, w)
+    srv = Server(pot, n_lanes=1, max_batch_atoms=1000, max_batch_systems=8)
+    big = synth.water_box(400, 23.0, 8, seed=3)
+    with pytest.raises(NNPError, match="OOM"):
+        srv.submit(big.coords, big.species, big.box)
+    small = synth.workload("gas24")[0][0]
+    rc, E, F, lat = srv.poll(srv.submit(small.coords, small.species))
+    assert rc == 0 and np.isfinite(E)
+    srv.close()
