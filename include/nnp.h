@@ -185,6 +185,36 @@ int nnp_energy_forces_host(nnp_handle* h, int64_t n_atoms, const float* coords_h
                            const uint8_t* mask_h, double* energy_h, float* forces_h,
                            double* virial_h);
 
+/* ---------------------------------------------------------------- differentiation
+ * Vector-Jacobian product of (E, F) for training by force matching: given
+ * gE = dL/dE and v = dL/dF of a loss L(E, F) (e.g. sum (F - F_target)^2, where
+ * v = 2 (F - F_target)), returns
+ *   dL/dcoords  = -gE F + (d/de) F(r + e v)      (a Hessian-vector product), and
+ *   dL/dweights = gE dE/dweights - d/dweights [ sum_i dE/dG_i . J_i v ],
+ * the second derivatives of Eqs. 2-5 taken analytically: the AEV Jacobian along
+ * v, a forward-over-reverse pass through the networks, and the AEV backward
+ * in dual-number arithmetic.  FP32 handles only.  The call recomputes the
+ * forward pass and also writes E and F.
+ * dL_dweights: device float [nnp_n_weights(h)], flat in the nnp_weights_t layout,
+ * written (summed over the systems of a batch).  Per system: dL_dF device float
+ * [n,3] (input), dL_dcoords device float [n,3] (output; zero outside the mask).
+ * Asynchronous on `stream`. */
+typedef struct {
+  nnp_system_t sys;      /* inputs and the energy/forces outputs (virial ignored) */
+  double dL_dE;
+  const float* dL_dF;
+  float* dL_dcoords;
+} nnp_vjp_system_t;
+
+int nnp_force_vjp_batch(nnp_handle* h, int n_sys, const nnp_vjp_system_t* systems,
+                        float* dL_dweights, void* stream);
+int nnp_force_vjp(nnp_handle* h, int64_t n_atoms, const float* coords, const uint8_t* species,
+                  const double* box_host, const uint8_t* mask, double dL_dE,
+                  const float* dL_dF, double* energy, float* forces, float* dL_dcoords,
+                  float* dL_dweights, void* stream);
+/* Number of network parameters (length of the flat weight vector). */
+int64_t nnp_n_weights(const nnp_handle* h);
+
 /* ---------------------------------------------------------------- serving
  * A continuous-batching server for streams of independent energy+force
  * requests (many small molecules, or new solute coordinates for solvated boxes

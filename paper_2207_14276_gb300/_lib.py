@@ -39,7 +39,8 @@ EXPORTS = (
     "nnp_last_launch_count", "nnp_last_error", "nnp_debug_rows", "nnp_debug_neighbors",
     "nnp_profile", "nnp_profile_read", "nnp_profile_stage_name", "nnp_energy_forces_noalloc",
     "nnp_server_create", "nnp_server_destroy", "nnp_server_register", "nnp_server_submit",
-    "nnp_server_poll", "nnp_server_stats",
+    "nnp_server_poll", "nnp_server_stats", "nnp_force_vjp_batch", "nnp_force_vjp",
+    "nnp_n_weights",
 )
 
 
@@ -73,6 +74,11 @@ class SystemT(ctypes.Structure):
                 ("box", ctypes.c_double * 3), ("periodic", ctypes.c_int),
                 ("energy", ctypes.c_void_p), ("forces", ctypes.c_void_p),
                 ("virial", ctypes.c_void_p), ("atom_energies", ctypes.c_void_p)]
+
+
+class VjpSystemT(ctypes.Structure):
+    _fields_ = [("sys", SystemT), ("dL_dE", ctypes.c_double), ("dL_dF", ctypes.c_void_p),
+                ("dL_dcoords", ctypes.c_void_p)]
 
 
 class RequestT(ctypes.Structure):
@@ -119,6 +125,10 @@ def lib():
     L.nnp_server_submit.argtypes = [P, ctypes.POINTER(RequestT), ctypes.POINTER(ctypes.c_uint64)]
     L.nnp_server_poll.argtypes = [P, ctypes.c_uint64, i, ctypes.POINTER(ctypes.c_double)]
     L.nnp_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.nnp_force_vjp_batch.argtypes = [P, i, ctypes.POINTER(VjpSystemT), P, P]
+    L.nnp_force_vjp.argtypes = [P, i64, P, P, P, P, ctypes.c_double, P, P, P, P, P, P]
+    L.nnp_n_weights.argtypes = [P]
+    L.nnp_n_weights.restype = i64
     L.nnp_profile.argtypes = [P, i]
     L.nnp_profile_read.argtypes = [P, i, P, P, i, P]
     L.nnp_profile_stage_name.restype = ctypes.c_char_p

@@ -19,6 +19,7 @@
 #include "../../include/nnp.h"
 #include "mlp.cuh"
 #include "nnp_internal.cuh"
+#include "vjp.cuh"
 
 using namespace nnp;
 
@@ -84,6 +85,11 @@ struct nnp_handle {
   // host-call staging
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // force vector-Jacobian product buffers (grown on demand)
+  void* vjp_arena = nullptr;
+  size_t vjp_bytes = 0;
+  int vjp_rows = 0;
+  VjpBufs vb{};
   // optional per-stage CUDA-event timing
   bool profile = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
@@ -548,10 +554,11 @@ int nnp_clone(const nnp_handle* src, nnp_handle** out) {
 
 void nnp_destroy(nnp_handle* h) {
   if (!h) return;
-  if (h->arena || h->stage) cudaDeviceSynchronize();
+  if (h->arena || h->stage || h->vjp_arena) cudaDeviceSynchronize();
   if (h->tc_state) mlp_tc_release(h->tc_state);
   if (h->arena) cudaFree(h->arena);
   if (h->stage) cudaFree(h->stage);
+  if (h->vjp_arena) cudaFree(h->vjp_arena);
   if (h->status_host) cudaFreeHost(h->status_host);
   for (auto& pe : h->prof_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
   for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
@@ -668,6 +675,250 @@ int nnp_energy_forces_host(nnp_handle* h, int64_t n, const float* coords_h,
     if (rc != NNP_ERR_CAPACITY) return rc;
   }
   return fail(NNP_ERR_CAPACITY, "neighbour list over capacity after one retry");
+}
+
+// ---------------------------------------------------------------- force VJP
+namespace {
+
+size_t carve_vjp(nnp_handle* h, char* base, int rows, int n) {
+  const Model& m = *h->model;
+  const int E = m.md.E, Dp = m.ac.Dp;
+  const size_t w1 = (size_t)rows * E * m.md.h1, w2 = (size_t)rows * E * m.md.h2, w3 = (size_t)rows * E * m.md.h3;
+  Carve c{base};
+  VjpBufs& v = h->vb;
+  v.v_pos = c.take<float4>(n);
+  v.df_pos = c.take<float4>(n);
+  v.gE_row = c.take<float>(rows);
+  v.U = c.take<float>((size_t)rows * Dp);
+  v.Q = c.take<float>((size_t)rows * Dp);
+  float** l1[] = {&v.H1, &v.D1, &v.Z1d, &v.H1d, &v.A1h, &v.A1z, &v.dl1, &v.dl1d};
+  for (float** q : l1) *q = c.take<float>(w1);
+  float** l2[] = {&v.H2, &v.D2, &v.Z2d, &v.H2d, &v.A2h, &v.A2z, &v.dl2, &v.dl2d};
+  for (float** q : l2) *q = c.take<float>(w2);
+  float** l3[] = {&v.H3, &v.D3, &v.Z3d, &v.H3d, &v.dl3, &v.dl3d};
+  for (float** q : l3) *q = c.take<float>(w3);
+  v.e_row = c.take<float>((size_t)E * rows);
+  return align_up(c.off, 256);
+}
+
+int ensure_vjp(nnp_handle* h) {
+  const int rows = h->ws.row_cap, n = std::max(h->cap_in, 1);
+  if (h->vjp_arena && rows <= h->vjp_rows) {
+    // neighbour capacities may have grown since the buffers were made
+    CU_TRY(vjp_set_smem(h->ws));
+    return NNP_OK;
+  }
+  const size_t bytes = carve_vjp(h, nullptr, rows, n);
+  if (h->vjp_arena) {
+    CU_TRY(cudaDeviceSynchronize());
+    cudaFree(h->vjp_arena);
+    h->vjp_arena = nullptr;
+  }
+  if (cudaMalloc(&h->vjp_arena, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->vjp_arena = nullptr;
+    h->vjp_rows = 0;
+    return fail(NNP_ERR_OOM, "cudaMalloc of the force-VJP buffers failed");
+  }
+  CU_TRY(cudaMemset(h->vjp_arena, 0, bytes));
+  h->vjp_bytes = bytes;
+  h->vjp_rows = rows;
+  carve_vjp(h, static_cast<char*>(h->vjp_arena), rows, n);
+  CU_TRY(vjp_set_smem(h->ws));
+  return NNP_OK;
+}
+
+GemmArgs gemm_base(const Ws& ws, const Model& m) {
+  GemmArgs g{};
+  g.alpha = m.alpha;
+  g.seg_start = ws.seg_start;
+  g.S = m.md.S;
+  return g;
+}
+
+// forward, tangent forward and forward-over-reverse of the networks (FP32)
+void vjp_networks(nnp_handle* h, cudaStream_t st) {
+  const Model& m = *h->model;
+  const Ws& ws = h->ws;
+  const VjpBufs& v = h->vb;
+  const MlpWeights& w = m.mw;
+  const int E = m.md.E, S = m.md.S, Dp = m.ac.Dp, h1 = m.md.h1, h2 = m.md.h2, h3 = m.md.h3;
+  const int R = ws.row_cap;
+  auto L1 = [&](const float* A, int epi, float* out, float* out2, const float* aux) {
+    GemmArgs g = gemm_base(ws, m);
+    g.A = A; g.lda = Dp; g.a_net = 0;
+    g.B = w.W1cat; g.b_s = (long long)E * h1 * Dp; g.b_e = 0; g.ldb = Dp;
+    g.bias = w.b1cat; g.bias_s = (long long)E * h1; g.bias_e = 0;
+    g.N = E * h1; g.K = Dp;
+    g.out = out; g.out2 = out2; g.ldo = E * h1; g.out_net = 0;
+    g.aux = aux; g.ld_aux = E * h1; g.aux_net = 0;
+    g.epi = epi;
+    launch_gemm_fp32(g, R, st, 1);
+  };
+  // per-member layer: out[:, e*n_out] = A[:, e*k] B_{e,s}^T
+  auto Lm = [&](const float* A, int k, const float* B, int n_out, const float* bias, int epi, float* out,
+                float* out2, const float* aux) {
+    GemmArgs g = gemm_base(ws, m);
+    g.A = A; g.lda = E * k; g.a_net = k;
+    g.B = B; g.b_s = (long long)n_out * k; g.b_e = (long long)S * n_out * k; g.ldb = k;
+    g.bias = bias; g.bias_s = n_out; g.bias_e = (long long)S * n_out;
+    g.N = n_out; g.K = k;
+    g.out = out; g.out2 = out2; g.ldo = E * n_out; g.out_net = n_out;
+    g.aux = aux; g.ld_aux = E * n_out; g.aux_net = n_out;
+    g.epi = epi;
+    launch_gemm_fp32(g, R, st, E);
+  };
+  L1(ws.aev, kEpiCelu, v.H1, v.D1, nullptr);
+  Lm(v.H1, h1, w.W2, h2, w.b2, kEpiCelu, v.H2, v.D2, nullptr);
+  Lm(v.H2, h2, w.W3, h3, w.b3, kEpiCelu, v.H3, v.D3, nullptr);
+  L1(v.U, kEpiStoreMul, v.Z1d, v.H1d, v.D1);
+  Lm(v.H1d, h1, w.W2, h2, nullptr, kEpiStoreMul, v.Z2d, v.H2d, v.D2);
+  Lm(v.H2d, h2, w.W3, h3, nullptr, kEpiStoreMul, v.Z3d, v.H3d, v.D3);
+  launch_vjp_out3(ws, v, w.w4, S, E, h3, m.alpha, st);
+  Lm(v.dl3, h3, w.W3T, h2, nullptr, kEpiStore, v.A2h, nullptr, nullptr);
+  Lm(v.dl3d, h3, w.W3T, h2, nullptr, kEpiStore, v.A2z, nullptr, nullptr);
+  launch_vjp_delta(ws, S, E * h2, v.A2h, v.A2z, v.D2, v.Z2d, v.dl2, v.dl2d, m.alpha, st);
+  Lm(v.dl2, h2, w.W2T, h1, nullptr, kEpiStore, v.A1h, nullptr, nullptr);
+  Lm(v.dl2d, h2, w.W2T, h1, nullptr, kEpiStore, v.A1z, nullptr, nullptr);
+  launch_vjp_delta(ws, S, E * h1, v.A1h, v.A1z, v.D1, v.Z1d, v.dl1, v.dl1d, m.alpha, st);
+  auto B1 = [&](const float* A, float* out) {
+    GemmArgs g = gemm_base(ws, m);
+    g.A = A; g.lda = E * h1; g.a_net = 0;
+    g.B = w.W1Tcat; g.b_s = (long long)Dp * E * h1; g.b_e = 0; g.ldb = E * h1;
+    g.N = Dp; g.K = E * h1;
+    g.out = out; g.ldo = Dp; g.out_net = 0;
+    g.epi = kEpiStore;
+    launch_gemm_fp32(g, R, st, 1);
+  };
+  B1(v.dl1, ws.dEdG);
+  B1(v.dl1d, v.Q);
+}
+
+void vjp_weight_grads(nnp_handle* h, float* out, cudaStream_t st) {
+  const Model& m = *h->model;
+  const Ws& ws = h->ws;
+  const VjpBufs& v = h->vb;
+  const int E = m.md.E, S = m.md.S, D = m.ac.D, Dp = m.ac.Dp, h1 = m.md.h1, h2 = m.md.h2, h3 = m.md.h3;
+  const long long off2 = (long long)h1 * D + h1, off3 = off2 + (long long)h2 * h1 + h2;
+  const long long off4 = off3 + (long long)h3 * h2 + h3;
+  const long long per_net = off4 + h3 + 1;
+  WgradArgs a{};
+  a.S = S; a.scale = 1.f / E; a.out = out; a.per_net = per_net;
+  a.X1 = v.dl1; a.X2 = v.dl1d; a.ldx = E * h1; a.x_net = h1;
+  a.Y1 = ws.aev; a.Y2 = v.U; a.ldy = Dp; a.y_net = 0;
+  a.n_out = h1; a.n_in = Dp; a.n_in_real = D; a.layer_off = 0;
+  launch_wgrad(a, ws, v, E, st);
+  a.X1 = v.dl2; a.X2 = v.dl2d; a.ldx = E * h2; a.x_net = h2;
+  a.Y1 = v.H1; a.Y2 = v.H1d; a.ldy = E * h1; a.y_net = h1;
+  a.n_out = h2; a.n_in = h1; a.n_in_real = h1; a.layer_off = off2;
+  launch_wgrad(a, ws, v, E, st);
+  a.X1 = v.dl3; a.X2 = v.dl3d; a.ldx = E * h3; a.x_net = h3;
+  a.Y1 = v.H2; a.Y2 = v.H2d; a.ldy = E * h2; a.y_net = h2;
+  a.n_out = h3; a.n_in = h2; a.n_in_real = h2; a.layer_off = off3;
+  launch_wgrad(a, ws, v, E, st);
+  launch_wgrad_out(ws, v, S, E, h3, out, per_net, off4, st);
+}
+
+}  // namespace
+
+extern "C" int nnp_force_vjp_batch(nnp_handle* h, int n_sys, const nnp_vjp_system_t* vs,
+                                   float* dL_dweights, void* stream) {
+  g_err.clear();
+  if (!h || n_sys < 1 || !vs || !dL_dweights) return fail(NNP_ERR_ARG, "bad argument");
+  const Model& m = *h->model;
+  if (m.precision != NNP_FP32) return fail(NNP_ERR_UNSUPPORTED, "the force VJP runs FP32 handles");
+  std::vector<nnp_system_t> sy(n_sys);
+  long long n_in_ll = 0;
+  for (int b = 0; b < n_sys; ++b) {
+    sy[b] = vs[b].sys;
+    int rc = validate_system(h, sy[b]);
+    if (rc) return rc;
+    if (sy[b].n_atoms > 0 && (!vs[b].dL_dF || !vs[b].dL_dcoords))
+      return fail(NNP_ERR_ARG, "dL_dF and dL_dcoords are required");
+    if (sy[b].n_atoms == 0) return fail(NNP_ERR_ARG, "empty system in a force VJP batch");
+    n_in_ll += sy[b].n_atoms;
+  }
+  if (n_in_ll > (1LL << 30)) return fail(NNP_ERR_ARG, "too many atoms in one call");
+  const int n_in = (int)n_in_ll;
+  int rc = ensure_arena(h, n_in, n_sys);
+  if (rc) return rc;
+  if ((rc = ensure_vjp(h))) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws& ws = h->ws;
+  ws.n_sys = n_sys;
+  ws.n_in = n_in;
+  int in_base = 0;
+  std::vector<BatchParams> chunks;
+  for (int b0 = 0; b0 < n_sys; b0 += kMaxBatchParam) {
+    BatchParams bp{};
+    bp.sys_base = b0;
+    bp.n_sys = std::min(kMaxBatchParam, n_sys - b0);
+    for (int k = 0; k < bp.n_sys; ++k) {
+      const nnp_system_t& s = sy[b0 + k];
+      SysIn& si = bp.sys[k];
+      si.coords = s.coords; si.species = s.species; si.mask = s.mask;
+      si.energy = s.energy; si.forces = s.forces; si.virial = nullptr; si.atom_e = s.atom_energies;
+      si.n_in = (int)s.n_atoms; si.in_base = in_base; si.periodic = s.periodic ? 1 : 0;
+      for (int c = 0; c < 3; ++c) split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c]);
+      si.dLdF = vs[b0 + k].dL_dF;
+      si.dLdR = vs[b0 + k].dL_dcoords;
+      si.gE = vs[b0 + k].dL_dE;
+      in_base += (int)s.n_atoms;
+    }
+    chunks.push_back(bp);
+  }
+  for (const auto& bp : chunks) launch_init_chunk(ws, bp, st);
+  for (const auto& bp : chunks) {
+    int n_chunk = 0;
+    for (int k = 0; k < bp.n_sys; ++k) n_chunk += bp.sys[k].n_in;
+    launch_prep_atoms(ws, bp, n_chunk, m.ac.S, st);
+  }
+  launch_setup(ws, m.ac, st);
+  launch_bin(ws, n_in, st);
+  launch_scan(ws, st);
+  launch_scatter(ws, n_in, st);
+  launch_neighbors(ws, n_in, m.ac, st);
+  launch_aev_fwd(ws, n_in, m.ac, st);
+  launch_vjp_zero(ws, h->vb, n_in, st);
+  launch_gather_v(ws, h->vb, n_in, st);
+  launch_aev_jvp(ws, m.ac, h->vb, n_in, st);
+  vjp_networks(h, st);
+  launch_aev_bwd(ws, n_in, m.ac, 0, st);
+  launch_aev_bwd_dual(ws, m.ac, h->vb, n_in, st);
+  launch_finalize_e(ws, n_in, h->vb.e_row, m.md.E, ws.row_cap, m.ebias, st);
+  launch_vjp_scatter(ws, h->vb, n_in, st);
+  vjp_weight_grads(h, dL_dweights, st);
+  h->last_n_in = n_in;
+  CU_TRY(cudaGetLastError());
+  return NNP_OK;
+}
+
+extern "C" int nnp_force_vjp(nnp_handle* h, int64_t n_atoms, const float* coords, const uint8_t* species,
+                             const double* box_host, const uint8_t* mask, double dL_dE, const float* dL_dF,
+                             double* energy, float* forces, float* dL_dcoords, float* dL_dweights,
+                             void* stream) {
+  nnp_vjp_system_t v{};
+  v.sys.n_atoms = n_atoms;
+  v.sys.coords = coords;
+  v.sys.species = species;
+  v.sys.mask = mask;
+  v.sys.periodic = box_host != nullptr;
+  if (box_host)
+    for (int c = 0; c < 3; ++c) v.sys.box[c] = box_host[c];
+  v.sys.energy = energy;
+  v.sys.forces = forces;
+  v.dL_dE = dL_dE;
+  v.dL_dF = dL_dF;
+  v.dL_dcoords = dL_dcoords;
+  return nnp_force_vjp_batch(h, 1, &v, dL_dweights, stream);
+}
+
+extern "C" int64_t nnp_n_weights(const nnp_handle* h) {
+  if (!h) return -1;
+  const Model& m = *h->model;
+  const long long D = m.ac.D, h1 = m.md.h1, h2 = m.md.h2, h3 = m.md.h3;
+  const long long per = h1 * D + h1 + h2 * h1 + h2 + h3 * h2 + h3 + h3 + 1;
+  return per * m.md.S * m.md.E;
 }
 
 int nnp_aev_dim(const nnp_handle* h) { return h ? h->model->ac.D : -1; }

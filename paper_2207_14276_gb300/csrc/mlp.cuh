@@ -12,6 +12,7 @@ enum Epi : int {
   kEpiCeluDot = 1,  // e_row += CELU(acc + b) . w4 ; out = w4 * CELU'(acc + b)
   kEpiMul = 2,      // out = acc * aux
   kEpiStore = 3,    // out = acc
+  kEpiStoreMul = 4, // out = acc, out2 = acc * aux
 };
 
 // One grouped GEMM: for every 128-row tile of species s and net e = blockIdx.z,
@@ -72,6 +73,7 @@ struct StageHook {
 };
 
 void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st);
+void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st, int n_nets);
 void launch_mlp_fp32(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
                      float alpha, cudaStream_t st, int* n_launch, StageHook* hook);
 

@@ -118,12 +118,16 @@ __global__ void __launch_bounds__(256) k_gemm_fp32(GemmArgs g) {
     for (int i = 0; i < 4; ++i) {
       const int m = m0 + ty * 4 + i;
       float v[4] = {acc[i][0], acc[i][1], acc[i][2], acc[i][3]};
-      if (EPI == kEpiMul) {
+      float* o = static_cast<float*>(g.out) + (size_t)m * g.ldo + (size_t)e * g.out_net + nb;
+      if (EPI == kEpiMul || EPI == kEpiStoreMul) {
         const float4 a = *reinterpret_cast<const float4*>(
             static_cast<const float*>(g.aux) + (size_t)m * g.ld_aux + (size_t)e * g.aux_net + nb);
+        if (EPI == kEpiStoreMul) {
+          *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
+          o = static_cast<float*>(g.out2) + (size_t)m * g.ldo + (size_t)e * g.out_net + nb;
+        }
         v[0] *= a.x; v[1] *= a.y; v[2] *= a.z; v[3] *= a.w;
       }
-      float* o = static_cast<float*>(g.out) + (size_t)m * g.ldo + (size_t)e * g.out_net + nb;
       *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
     }
   }
@@ -137,6 +141,7 @@ void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st, int n_net
     case kEpiCelu: k_gemm_fp32<kEpiCelu><<<grid, 256, 0, st>>>(g); break;
     case kEpiCeluDot: k_gemm_fp32<kEpiCeluDot><<<grid, 256, 0, st>>>(g); break;
     case kEpiMul: k_gemm_fp32<kEpiMul><<<grid, 256, 0, st>>>(g); break;
+    case kEpiStoreMul: k_gemm_fp32<kEpiStoreMul><<<grid, 256, 0, st>>>(g); break;
     default: k_gemm_fp32<kEpiStore><<<grid, 256, 0, st>>>(g); break;
   }
 }

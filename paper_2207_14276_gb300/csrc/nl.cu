@@ -83,6 +83,11 @@ __global__ void k_prep(Ws ws, BatchParams bp, int n_chunk, int S) {
     si.forces[3 * local + 1] = 0.f;
     si.forces[3 * local + 2] = 0.f;
     if (si.atom_e) si.atom_e[local] = 0.f;
+    if (si.dLdR) {
+      si.dLdR[3 * local + 0] = 0.f;
+      si.dLdR[3 * local + 1] = 0.f;
+      si.dLdR[3 * local + 2] = 0.f;
+    }
     if (local == 0) {
       *si.energy = 0.0;
       if (si.virial)

@@ -52,6 +52,10 @@ struct SysIn {
   int in_base;       // offset of this system's atoms in the batch input index space
   int periodic;
   float box_hi[3], box_lo[3];   // box edge as float hi + float residual
+  // force vector-Jacobian product only (null otherwise)
+  const float* dLdF;
+  float* dLdR;
+  double gE;
 };
 
 // per-system device state (device-filled part)

@@ -194,6 +194,53 @@ class Potential:
                                            vp(F), vp(V)))
         return (E[0], F, V.reshape(3, 3)) if virial else (E[0], F)
 
+    @property
+    def n_weights(self):
+        return lib().nnp_n_weights(self._h)
+
+    def force_vjp_batch(self, systems, dL_dE, dL_dF, stream=None):
+        """Vector-Jacobian product of (E, F) for a batch (FP32 handles).
+        systems: list of dicts (coords, species, box, mask) of cuda tensors; dL_dE: per-system
+        floats; dL_dF: list of cuda float32 [n,3].  Returns (energies [n_sys] float64,
+        forces list, dL/dcoords list, dL/dweights flat float32)."""
+        n_sys = len(systems)
+        arr = (_lib.VjpSystemT * n_sys)()
+        dev = systems[0]["coords"].device
+        E = torch.empty(n_sys, dtype=torch.float64, device=dev)
+        Fs, Gs, keep = [], [], []
+        for k, s in enumerate(systems):
+            n = s["coords"].shape[0]
+            F = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            G = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            v = dL_dF[k].contiguous().float()
+            keep.append(v)
+            d = arr[k]
+            d.sys.n_atoms = n
+            d.sys.coords = s["coords"].data_ptr()
+            d.sys.species = s["species"].data_ptr()
+            d.sys.mask = s["mask"].data_ptr() if s.get("mask") is not None else None
+            box = s.get("box")
+            d.sys.periodic = 1 if box is not None else 0
+            if box is not None:
+                for c in range(3):
+                    d.sys.box[c] = float(box[c])
+            d.sys.energy = E.data_ptr() + 8 * k
+            d.sys.forces = F.data_ptr()
+            d.dL_dE = float(dL_dE[k])
+            d.dL_dF = v.data_ptr()
+            d.dL_dcoords = G.data_ptr()
+            Fs.append(F)
+            Gs.append(G)
+        W = torch.empty(self.n_weights, dtype=torch.float32, device=dev)
+        for attempt in range(2):
+            check(lib().nnp_force_vjp_batch(self._h, n_sys, arr, _ptr(W), _stream_ptr(stream)))
+            rc = self.sync_status(stream)
+            if rc == _lib.NNP_ERR_CAPACITY and attempt == 0:
+                continue
+            check(rc)
+            break
+        return E, Fs, Gs, W
+
     def profile(self, enable=True):
         check(lib().nnp_profile(self._h, 1 if enable else 0))
 
