@@ -257,7 +257,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
 }
 
 template <int ZETA>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 3)
 k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
   extern __shared__ float4 sm4[];
   __shared__ ListHdr hdrs[kWarps];
@@ -265,10 +265,11 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
   const unsigned lane = threadIdx.x & 31;
   const int p = blockIdx.x * kWarps + w;
   if (p >= ws.totals[0]) return;
-  float4* angv = sm4 + (size_t)w * (3 * ws.cap_a + 32);
+  float4* angv = sm4 + (size_t)w * (3 * ws.cap_a + 40);
   float4* angf = angv + ws.cap_a;          // fc, dfc
   float4* acc3 = angf + ws.cap_a;          // dE/du per angular neighbour
   float* grad = reinterpret_cast<float*>(acc3 + ws.cap_a);  // S*16 radial dE/dG
+  float4* gblk = acc3 + ws.cap_a + 32;     // current angular block's dE/dG, [z][a]
   ListHdr& H = hdrs[w];
 
   const float4 xi = ws.xyzq[p];
@@ -330,13 +331,11 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
       if (n_tri == 0) continue;
       const float inv_cu = 1.f / (float)max(cu, 1);
       // the block's 32 dE/dG values (index 8a + z), same for every lane
-      float Gv[32];
-      const float4* gb4 = reinterpret_cast<const float4*>(g_row + ac.S * kNR + pidx * 32);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 v = gb4[q];
-        Gv[4 * q + 0] = v.x; Gv[4 * q + 1] = v.y; Gv[4 * q + 2] = v.z; Gv[4 * q + 3] = v.w;
-      }
+      // the block's 32 dE/dG values (index 8a + z), transposed to [z][a] so that
+      // each angle section is one broadcast 16-byte load
+      __syncwarp();
+      reinterpret_cast<float*>(gblk)[(lane & 7) * 4 + (lane >> 3)] = g_row[ac.S * kNR + pidx * 32 + lane];
+      __syncwarp();
       for (int t0 = 0; t0 < n_tri; t0 += 32) {
         const int t = t0 + lane;
         if (t >= n_tri) continue;
@@ -364,12 +363,9 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
           const float B1 = ipow<(ZETA > 0 ? ZETA - 1 : 0)>(base, ac.zeta - 1);
           const float B = B1 * base;
           const float dB = B1 * fmaf(-ac.sin_z[z], c_over_s, ac.cos_z[z]);
-          float P = 0.f, Q = 0.f;
-#pragma unroll
-          for (int a = 0; a < kNA; ++a) {
-            P = fmaf(Gv[a * kNZ + z], A[a], P);
-            Q = fmaf(Gv[a * kNZ + z], dA[a], Q);
-          }
+          const float4 gz = gblk[z];
+          const float P = fmaf(gz.x, A[0], fmaf(gz.y, A[1], fmaf(gz.z, A[2], gz.w * A[3])));
+          const float Q = fmaf(gz.x, dA[0], fmaf(gz.y, dA[1], fmaf(gz.z, dA[2], gz.w * dA[3])));
           tc = fmaf(dB, P, tc);
           tR = fmaf(B, Q, tR);
           tf = fmaf(B, P, tf);
@@ -428,7 +424,7 @@ size_t aev_fwd_smem(const Ws& ws) {
   return (size_t)kWarps * (ws.cap_a + ws.cap_a / 4 + ws.cap_r / 2 + 2) * sizeof(float4);
 }
 size_t aev_bwd_smem(const Ws& ws) {
-  return (size_t)kWarps * (3 * ws.cap_a + 32) * sizeof(float4);
+  return (size_t)kWarps * (3 * ws.cap_a + 40) * sizeof(float4);
 }
 
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st) {

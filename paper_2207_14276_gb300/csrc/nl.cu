@@ -356,11 +356,28 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_neighbors(Ws ws, AevConst ac)
       *nout[c] = m;
     }
   }
+  // z-neighbour cells that are consecutive in the cell order form one range of
+  // the cell-sorted atoms: sort the (at most 3) z indices and merge runs
+  int zs[3];
+  for (int a2 = 0; a2 < n2; ++a2) zs[a2] = cl2[a2];
+  for (int a = 0; a < n2; ++a)
+    for (int b = a + 1; b < n2; ++b)
+      if (zs[b] < zs[a]) { const int t = zs[a]; zs[a] = zs[b]; zs[b] = t; }
+  int zr_beg[3], zr_end[3], nzr = 0;
+  for (int a2 = 0; a2 < n2; ++a2) {
+    if (nzr > 0 && zs[a2] == zr_end[nzr - 1]) {
+      zr_end[nzr - 1] = zs[a2] + 1;
+    } else {
+      zr_beg[nzr] = zs[a2];
+      zr_end[nzr] = zs[a2] + 1;
+      ++nzr;
+    }
+  }
   for (int a0 = 0; a0 < n0; ++a0)
     for (int a1 = 0; a1 < n1; ++a1)
-      for (int a2 = 0; a2 < n2; ++a2) {
-        const int gc = d.cell_base + (cl0[a0] * nc1 + cl1[a1]) * nc2 + cl2[a2];
-        const int beg = ws.cell_start[gc], end = ws.cell_start[gc + 1];
+      for (int zr = 0; zr < nzr; ++zr) {
+        const int row = d.cell_base + (cl0[a0] * nc1 + cl1[a1]) * nc2;
+        const int beg = ws.cell_start[row + zr_beg[zr]], end = ws.cell_start[row + zr_end[zr]];
         for (int j0 = beg; j0 < end; j0 += 32) {
           const int j = j0 + lane;
           bool keep = false, ang = false;
