@@ -249,6 +249,25 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+def max_over_ranks(x, dist=None, device=None):
+    """Maximum of a float over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, local_ms, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank processes
+    units_per_rank_step per step; the job takes as long as its slowest rank."""
+    world = dist.get_world_size() if (dist is not None and dist.is_initialized()) else 1
+    total_ms = max_over_ranks(local_ms, dist, device)
+    return units_per_rank_step * steps * world / (total_ms / 1e3), total_ms
+
+
 # ------------------------------------------------------------------ serving
 def drive_stream(srv, reqs, rids):
     """Submit requests at their scheduled Poisson arrival times from this thread,
@@ -388,11 +407,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = sum(step_ms)
     stages = pot.profile_read(reset=True)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n_eval * args.steps * world / (total_ms / 1e3)
+    value, total_ms = whole_job_rate(n_eval, args.steps, total_ms, dist, dev)
 
     # roofline of the dominant kernel (largest stage time over the timed region)
     peaks, peak_src = measured_peaks()
@@ -441,9 +456,8 @@ def run_ours(args):
                "p50_ms": 1e3 * float(np.percentile(e2e_t, 50)),
                "p99_ms": 1e3 * float(np.percentile(e2e_t, 99))}
         if dist is not None:
-            t = torch.tensor([e2e["value"]], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MIN)
-            e2e["value"] = float(t.item()) * world
+            # whole-job e2e rate: every rank's replica, limited by the slowest rank
+            e2e["value"] = world * n_eval / max_over_ranks(n_eval / e2e["value"], dist, dev)
 
     serving = None
     if args.serving_rates and rank == 0:

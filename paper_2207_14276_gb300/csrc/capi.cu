@@ -341,7 +341,7 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
   if (h->model->precision == NNP_BF16_MLP) {
     int rc = mlp_tc_prepare(h->model->md, h->model->mw, h->mb, h->ws.row_cap, h->ws.aev,
                             h->ws.dEdG, &h->tc_state);
-    if (rc) return rc;
+    if (rc) return fail(rc, "tensor-core GEMM set-up (tensor maps, launch limits) failed");
   }
   h->dirty = false;
   return NNP_OK;

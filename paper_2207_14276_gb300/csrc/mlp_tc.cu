@@ -8,9 +8,13 @@
 //            memory stages (128-byte swizzle), completion on mbarriers
 //   warp 5   MMA issuer: tcgen05.mma kind::f16 (M = 128, N = n_tile, K = 16)
 //            into a TMEM accumulator; tcgen05.commit frees a stage
-//   warps 0-3 epilogue: tcgen05.ld of its 32 accumulator rows, bias, CELU and
-//            CELU', the width-1 output layer as a dot product, products with
-//            stored derivatives; BF16 (or FP32 for dE/dG) stores.
+//   warps 0-3 epilogue: tcgen05.ld of its 32 accumulator rows, bias, CELU,
+//            the width-1 output layer as a dot product, and in the backward the
+//            product with CELU'(z) rebuilt from the stored activation
+//            (1 for h > 0, 1 + h/alpha otherwise); BF16 (FP32 for dE/dG) stores.
+// The N tiles of a row tile are adjacent in launch order (they share A in L2);
+// tiles are at most 128 columns with 3 stages so that two CTAs share an SM and
+// one CTA's epilogue overlaps the other's MMAs.
 // Every mbarrier wait is bounded; a CTA that gives up sets the status word,
 // drains the copies it issued, frees its tensor memory and returns.
 #include <cuda.h>
@@ -30,11 +34,14 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBK = 64;           // bf16 elements per K slice (one 128-byte swizzle row)
 constexpr int kThreads = 192;
-constexpr int kStages = 4;
+constexpr int kMaxStages = 4;
 constexpr unsigned kWaitLimit = 1u << 24;
+// dynamic shared memory limit: the 227 KB per block minus the kernel's static
+// shared memory (barriers, bias and w4 staging) and some headroom
+constexpr int kMaxDynSmem = 232448 - 8192;
 
 struct TcArgs {
-  int N, K, n_tile, n_k, tmem_cols;
+  int N, K, n_tile, n_k, tmem_cols, stages;
   int a_c1_per_e;       // A map coordinate 1 = e * a_c1_per_e (net slice)
   int b_c2_per_e;       // B map coordinate 2 = e * b_c2_per_e + s
   uint32_t idesc;
@@ -42,8 +49,8 @@ struct TcArgs {
   const float* bias; long long bias_s, bias_e;
   const float* w4; long long w4_s, w4_e;
   void* out; int ldo; int out_net;          // bf16 (or fp32 for kEpiStore)
-  void* out2;                               // bf16 CELU' (kEpiCelu)
-  const void* aux; int ld_aux; int aux_net; // bf16 stored CELU' (kEpiMul)
+  void* out2;                               // unused on this path
+  const void* aux; int ld_aux; int aux_net; // bf16 stored activation (kEpiMul)
   float* e_row; int e_row_net;
   float alpha;
   const int* seg_start;
@@ -182,16 +189,20 @@ __device__ __forceinline__ void load_bf16x16(const __nv_bfloat16* src, float (&v
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, TcArgs g) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
+  __shared__ float bias_sh[256], w4_sh[256];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
-  const int m0 = blockIdx.x * kBM;
+  // the N tiles of one row tile are adjacent in launch order, so they run
+  // together and share the row tile of A in L2
+  const int m0 = blockIdx.y * kBM;
   const int total = g.seg_start[g.S];
   if (m0 >= total) return;
   int s = 0;
   while (s + 1 < g.S && m0 >= g.seg_start[s + 1]) ++s;
   const int e = blockIdx.z;
-  const int n0 = blockIdx.y * g.n_tile;
+  const int n0 = blockIdx.x * g.n_tile;
+  const int kStages = g.stages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int a_bytes = kBM * kBK * 2, b_bytes = g.n_tile * kBK * 2;
@@ -199,7 +210,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   volatile int* abort_flag = &abort_sh;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; i < kMaxStages; ++i) {
       mbar_init(&full_bar[i], 1);
       mbar_init(&empty_bar[i], 1);
     }
@@ -213,6 +224,12 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
                  "r"((uint32_t)g.tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  for (int c = threadIdx.x; c < g.n_tile; c += blockDim.x) {
+    const int n = n0 + c;
+    const bool ok = n < g.N;
+    bias_sh[c] = (ok && g.bias) ? g.bias[e * g.bias_e + s * g.bias_s + n] : 0.f;
+    w4_sh[c] = (ok && g.w4) ? g.w4[e * g.w4_e + s * g.w4_s + n] : 0.f;
   }
   tc_fence_before();
   __syncthreads();
@@ -271,34 +288,32 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
         if (n >= g.N) continue;
         if (g.epi == kEpiCelu || g.epi == kEpiCeluDot) {
-          const float* bp = g.bias + e * g.bias_e + s * g.bias_s + n;
           float h[16], dd[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const float z = v[i] + bp[i];
+            const float z = v[i] + bias_sh[c0 + i];
             h[i] = celu_f(z, alpha, inv_alpha);
             dd[i] = celu_d(z, inv_alpha);
           }
           __nv_bfloat16* o = static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)e * g.out_net + n;
           if (g.epi == kEpiCelu) {
-            store_bf16x16(o, h);
-            __nv_bfloat16* o2 = static_cast<__nv_bfloat16*>(g.out2) + (size_t)m * g.ldo + (size_t)e * g.out_net + n;
-            store_bf16x16(o2, dd);
+            store_bf16x16(o, h);   // CELU' is rebuilt from h where it is needed
           } else {
-            const float* wp = g.w4 + e * g.w4_e + s * g.w4_s + n;
             float d3[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              dot = fmaf(h[i], wp[i], dot);
-              d3[i] = wp[i] * dd[i];
+              dot = fmaf(h[i], w4_sh[c0 + i], dot);
+              d3[i] = w4_sh[c0 + i] * dd[i];
             }
             store_bf16x16(o, d3);
           }
         } else if (g.epi == kEpiMul) {
+          // aux holds the layer's stored activation h = CELU(z): CELU'(z) = 1 for h > 0,
+          // 1 + h / alpha otherwise (exp(z/alpha) = 1 + h/alpha on that branch)
           float a[16];
           load_bf16x16(static_cast<const __nv_bfloat16*>(g.aux) + (size_t)m * g.ld_aux + (size_t)e * g.aux_net + n, a);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] *= a[i];
+          for (int i = 0; i < 16; ++i) v[i] *= (a[i] > 0.f) ? 1.f : fmaf(a[i], inv_alpha, 1.f);
           store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)e * g.out_net + n, v);
         } else {
           float4* o = reinterpret_cast<float4*>(static_cast<float*>(g.out) + (size_t)m * g.ldo + n);
@@ -382,7 +397,12 @@ struct TcState {
 };
 
 int pick_n_tile(int N, int row_tiles, bool single) {
-  int nt = N <= 256 ? N : 256;
+  // at most 128 columns (two CTAs share an SM's tensor memory) unless the
+  // output-layer dot product needs the whole row in one tile
+  if (single) return N <= 256 ? N : 256;
+  int nt = 16;
+  for (int c = 128; c >= 16; c -= 16)
+    if (N % c == 0) { nt = c; break; }
   if (!single) {
     // more CTAs for small problems: split N while there is less than one wave
     while (row_tiles * ((N + nt - 1) / nt) < 148 && nt % 32 == 0 && nt > 64) nt /= 2;
@@ -435,14 +455,14 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
       {5, kEpiCeluDot, h3, h2, E, mb.H2, (uint64_t)h2, (uint64_t)E, (uint64_t)h2, (uint64_t)E * h2,
        mw.W3_h, (uint64_t)h2, (uint64_t)h3, (uint64_t)E * S, S, mw.b3, h3, (long long)S * h3,
        mw.w4, h3, (long long)S * h3, mb.d3, E * h3, h3, nullptr, nullptr, 0, 0},
-      // B3: delta2 = (delta3 W3) * D2, written over H2
+      // B3: delta2 = (delta3 W3) * CELU'(z2) from H2, written over H2
       {6, kEpiMul, h2, h3, E, mb.d3, (uint64_t)h3, (uint64_t)E, (uint64_t)h3, (uint64_t)E * h3,
        mw.W3T_h, (uint64_t)h3, (uint64_t)h2, (uint64_t)E * S, S, nullptr, 0, 0, nullptr, 0, 0,
-       mb.H2, E * h2, h2, nullptr, mb.D2, E * h2, h2},
-      // B2: delta1 = (delta2 W2) * D1, written over H1
+       mb.H2, E * h2, h2, nullptr, mb.H2, E * h2, h2},
+      // B2: delta1 = (delta2 W2) * CELU'(z1) from H1, written over H1
       {7, kEpiMul, h1, h2, E, mb.H2, (uint64_t)h2, (uint64_t)E, (uint64_t)h2, (uint64_t)E * h2,
        mw.W2T_h, (uint64_t)h2, (uint64_t)h1, (uint64_t)E * S, S, nullptr, 0, 0, nullptr, 0, 0,
-       mb.H1, E * h1, h1, nullptr, mb.D1, E * h1, h1},
+       mb.H1, E * h1, h1, nullptr, mb.H1, E * h1, h1},
       // B1: dE/dG = [delta1_e] [W1_e / E]   (K = E*h1), FP32 output
       {8, kEpiStore, Dp, E * h1, 1, mb.H1, (uint64_t)E * h1, 1, (uint64_t)E * h1, (uint64_t)E * h1,
        mw.W1Tcat_h, (uint64_t)E * h1, (uint64_t)Dp, (uint64_t)S, 0, nullptr, 0, 0, nullptr, 0, 0,
@@ -470,18 +490,19 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     a.out = l.out; a.ldo = l.ldo; a.out_net = l.out_net; a.out2 = l.out2;
     a.aux = l.aux; a.ld_aux = l.ld_aux; a.aux_net = l.aux_net;
     a.e_row = mb.e_row; a.e_row_net = row_cap;
-    p.grid = dim3(row_tiles, (l.N + nt - 1) / nt, l.nets);
+    p.grid = dim3((l.N + nt - 1) / nt, row_tiles, l.nets);
     // shared memory: stages plus 1 KB for alignment; never so little that more CTAs
     // would share an SM than its 512 tensor-memory columns can hold
-    size_t sm = (size_t)kStages * (kBM * kBK * 2 + nt * kBK * 2) + 1024;
+    a.stages = a.n_k < 3 ? (a.n_k < 1 ? 1 : a.n_k) : 3;
+    size_t sm = (size_t)a.stages * (kBM * kBK * 2 + nt * kBK * 2) + 1024;
     const int max_ctas = 512 / a.tmem_cols;
     const size_t floor_sm = 232448 / (size_t)(max_ctas + 1) + 1;
     p.smem = sm > floor_sm ? sm : floor_sm;
-    if (p.smem > 232448 - 2048) { delete st; return NNP_ERR_UNSUPPORTED; }
+    if (p.smem > (size_t)kMaxDynSmem) { delete st; return NNP_ERR_UNSUPPORTED; }
     p.stage_id = l.stage;
     st->plans.push_back(p);
   }
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 2048);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   if (e != cudaSuccess) { delete st; return NNP_ERR_CUDA; }
   *state_out = st;
   return NNP_OK;
