@@ -90,6 +90,12 @@ struct nnp_handle {
   size_t vjp_bytes = 0;
   int vjp_rows = 0;
   VjpBufs vb{};
+  // replay of a repeated call as a CUDA graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::string gsig;       // signature of the captured call
+  std::string last_sig;   // signature of the previous eager call
+  int last_launches_graph = 0;
   // optional per-stage CUDA-event timing
   bool profile = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
@@ -409,19 +415,12 @@ void split_box(double L, float* hi, float* lo) {
   *lo = (float)(L - (double)*hi);
 }
 
-// enqueue the whole chain for a batch whose descriptors are already validated
-int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st) {
+// the kernel chain of one batch on stream st (no host synchronisation)
+int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::vector<BatchParams>& chunks,
+                  int n_in, bool any_virial, cudaStream_t st, int* n_launch) {
   const Model& m = *h->model;
-  long long n_in_ll = 0;
-  for (int b = 0; b < n_sys; ++b) n_in_ll += sy[b].n_atoms;
-  if (n_in_ll > (1LL << 30)) return fail(NNP_ERR_ARG, "too many atoms in one call");
-  const int n_in = (int)n_in_ll;
-  int rc = ensure_arena(h, n_in, n_sys);
-  if (rc) return rc;
   Ws& ws = h->ws;
-  ws.n_sys = n_sys;
-  ws.n_in = n_in;
-  int launches = 0;
+  int launches = 0, rc = NNP_OK;
   // systems without atoms: the outputs are the empty sums
   for (int b = 0; b < n_sys; ++b)
     if (sy[b].n_atoms == 0) {
@@ -429,39 +428,12 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
       if (sy[b].virial) CU_TRY(cudaMemsetAsync(sy[b].virial, 0, 9 * sizeof(double), st));
       launches += 1 + (sy[b].virial ? 1 : 0);
     }
-  // per-chunk descriptors as kernel parameters
-  std::vector<BatchParams> chunks;
-  int in_base = 0;
-  for (int b0 = 0; b0 < n_sys; b0 += kMaxBatchParam) {
-    BatchParams bp{};
-    bp.sys_base = b0;
-    bp.n_sys = std::min(kMaxBatchParam, n_sys - b0);
-    for (int k = 0; k < bp.n_sys; ++k) {
-      const nnp_system_t& s = sy[b0 + k];
-      SysIn& si = bp.sys[k];
-      si.coords = s.coords;
-      si.species = s.species;
-      si.mask = s.mask;
-      si.energy = s.energy;
-      si.forces = s.forces;
-      si.virial = s.virial;
-      si.atom_e = s.atom_energies;
-      si.n_in = (int)s.n_atoms;
-      si.in_base = in_base;
-      si.periodic = s.periodic ? 1 : 0;
-      for (int c = 0; c < 3; ++c) split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c]);
-      in_base += (int)s.n_atoms;
-    }
-    chunks.push_back(bp);
-  }
   for (const auto& bp : chunks) { launch_init_chunk(ws, bp, st); ++launches; }
   for (const auto& bp : chunks) {
     int n_chunk = 0;
     for (int k = 0; k < bp.n_sys; ++k) n_chunk += bp.sys[k].n_in;
     if (n_chunk > 0) { launch_prep_atoms(ws, bp, n_chunk, m.ac.S, st); ++launches; }
   }
-  bool any_virial = false;
-  for (int b = 0; b < n_sys; ++b) any_virial |= (sy[b].virial != nullptr);
   if (n_in > 0) {
     {
       StageTimer t(h, st, 0);
@@ -487,6 +459,104 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
     }
     launches += 2;
   }
+  CU_TRY(cudaGetLastError());
+  *n_launch = launches;
+  return rc;
+}
+
+// enqueue the whole chain for a batch whose descriptors are already validated
+int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st) {
+  const Model& m = *h->model;
+  long long n_in_ll = 0;
+  for (int b = 0; b < n_sys; ++b) n_in_ll += sy[b].n_atoms;
+  if (n_in_ll > (1LL << 30)) return fail(NNP_ERR_ARG, "too many atoms in one call");
+  const int n_in = (int)n_in_ll;
+  int rc = ensure_arena(h, n_in, n_sys);
+  if (rc) return rc;
+  Ws& ws = h->ws;
+  ws.n_sys = n_sys;
+  ws.n_in = n_in;
+  // per-chunk descriptors as kernel parameters
+  std::vector<BatchParams> chunks;
+  int in_base = 0;
+  for (int b0 = 0; b0 < n_sys; b0 += kMaxBatchParam) {
+    BatchParams bp{};
+    bp.sys_base = b0;
+    bp.n_sys = std::min(kMaxBatchParam, n_sys - b0);
+    for (int k = 0; k < bp.n_sys; ++k) {
+      const nnp_system_t& s = sy[b0 + k];
+      SysIn& si = bp.sys[k];
+      si.coords = s.coords;
+      si.species = s.species;
+      si.mask = s.mask;
+      si.energy = s.energy;
+      si.forces = s.forces;
+      si.virial = s.virial;
+      si.atom_e = s.atom_energies;
+      si.n_in = (int)s.n_atoms;
+      si.in_base = in_base;
+      si.periodic = s.periodic ? 1 : 0;
+      for (int c = 0; c < 3; ++c) split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c]);
+      in_base += (int)s.n_atoms;
+    }
+    chunks.push_back(bp);
+  }
+  bool any_virial = false;
+  for (int b = 0; b < n_sys; ++b) any_virial |= (sy[b].virial != nullptr);
+  // a call identical to the previous one (descriptors, sizes, arena) is replayed
+  // from a CUDA graph: captured on its second occurrence, replayed afterwards
+  if (!h->profile) {
+    std::string sig;
+    sig.reserve(64 + chunks.size() * sizeof(BatchParams));
+    auto put = [&](const void* p, size_t nb) { sig.append(static_cast<const char*>(p), nb); };
+    put(&n_sys, sizeof(n_sys));
+    put(&n_in, sizeof(n_in));
+    put(&h->arena, sizeof(h->arena));
+    put(&ws.cap_r, sizeof(int));
+    put(&ws.cap_a, sizeof(int));
+    put(&ws.row_cap, sizeof(int));
+    put(&ws.cell_cap, sizeof(int));
+    for (const auto& bp : chunks) put(&bp, sizeof(BatchParams));
+    if (h->gexec && sig == h->gsig) {
+      CU_TRY(cudaGraphLaunch(h->gexec, st));
+      h->last_launches = h->last_launches_graph;
+      h->last_n_in = n_in;
+      return NNP_OK;
+    }
+    if (sig == h->last_sig) {
+      if (!h->cap_stream) CU_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      CU_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      int launches = 0;
+      rc = enqueue_batch(h, n_sys, sy, chunks, n_in, any_virial, h->cap_stream, &launches);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+      if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(NNP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+      }
+      if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+      const cudaError_t ei = cudaGraphInstantiate(&h->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) {
+        h->gexec = nullptr;
+        return fail(NNP_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(ei));
+      }
+      h->gsig = sig;
+      h->last_launches_graph = launches;
+      CU_TRY(cudaGraphLaunch(h->gexec, st));
+      h->last_launches = launches;
+      h->last_n_in = n_in;
+      return NNP_OK;
+    }
+    h->last_sig = sig;
+  }
+  int launches = 0;
+  rc = enqueue_batch(h, n_sys, sy, chunks, n_in, any_virial, st, &launches);
+  if (rc) return rc;
   h->last_launches = launches;
   h->last_n_in = n_in;
   CU_TRY(cudaGetLastError());
@@ -556,6 +626,8 @@ void nnp_destroy(nnp_handle* h) {
   if (!h) return;
   if (h->arena || h->stage || h->vjp_arena) cudaDeviceSynchronize();
   if (h->tc_state) mlp_tc_release(h->tc_state);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->arena) cudaFree(h->arena);
   if (h->stage) cudaFree(h->stage);
   if (h->vjp_arena) cudaFree(h->vjp_arena);
