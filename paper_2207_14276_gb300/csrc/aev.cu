@@ -145,6 +145,35 @@ __device__ __forceinline__ void decode_pair(int t, int same, int c, int cu, floa
   }
 }
 
+// Same pairs, numbered along diagonals so that consecutive lanes get distinct
+// j (and distinct k): same species: pair (q, q + g + 1) of diagonal g; else
+// d = t / cs, j = t % cs, k = (j + d) % cu.  Used where lanes add into
+// per-neighbour accumulators, to spread those atomics over different addresses.
+__device__ __forceinline__ void decode_pair_diag(int t, int same, int c, int cu, float inv_cs,
+                                                 float inv_cu, int* j, int* k) {
+  if (same) {
+    const float b = 2.f * c - 1.f;
+    int g = (int)((b - sqrtf(fmaxf(b * b - 8.f * t, 0.f))) * 0.5f);
+    g = max(0, min(g, c - 2));
+    if ((g + 1) * (2 * c - g - 2) / 2 <= t) ++g;
+    else if (g * (2 * c - g - 1) / 2 > t) --g;
+    const int q = t - g * (2 * c - g - 1) / 2;
+    *j = q;
+    *k = q + g + 1;
+  } else {
+    int d = (int)((t + 0.5f) * inv_cs);
+    int jj = t - d * c;
+    if (jj < 0) { --d; jj += c; }
+    else if (jj >= c) { ++d; jj -= c; }
+    const int x = jj + d;
+    int kk = x - (int)((x + 0.5f) * inv_cu) * cu;
+    if (kk < 0) kk += cu;
+    else if (kk >= cu) kk -= cu;
+    *j = jj;
+    *k = kk;
+  }
+}
+
 // after the call lane l holds the warp sum of v[l]
 __device__ __forceinline__ float transpose_reduce32(float (&v)[32], unsigned lane) {
 #pragma unroll
@@ -284,7 +313,7 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
     const Geo g = pair_geo(xi, ws.xyzq[la[t]], d);
     const float inv = 1.f / g.r;
     angv[t] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
-    angf[t] = make_float4(fcut(g.r, ac.rc_a), fcut_d(g.r, ac.rc_a), 0.f, 0.f);
+    angf[t] = make_float4(fcut(g.r, ac.rc_a), fcut_d(g.r, ac.rc_a), inv, 0.f);
     acc3[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncwarp();
@@ -329,8 +358,7 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
       const int same = (s == u);
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
       if (n_tri == 0) continue;
-      const float inv_cu = 1.f / (float)max(cu, 1);
-      // the block's 32 dE/dG values (index 8a + z), same for every lane
+      const float inv_cu = 1.f / (float)max(cu, 1), inv_cs = 1.f / (float)max(cs, 1);
       // the block's 32 dE/dG values (index 8a + z), transposed to [z][a] so that
       // each angle section is one broadcast 16-byte load
       __syncwarp();
@@ -340,14 +368,14 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
         const int t = t0 + lane;
         if (t >= n_tri) continue;
         int j, k;
-        decode_pair(t, same, cs, cu, inv_cu, &j, &k);
+        decode_pair_diag(t, same, cs, cu, inv_cs, inv_cu, &j, &k);
         const int tj = os + j, tk = ou + k;
         const float4 vj = angv[tj], vk = angv[tk];
         const float4 fj4 = angf[tj], fk4 = angf[tk];
         const float chat = vj.x * vk.x + vj.y * vk.y + vj.z * vk.z;
         const float c = ac.cos_scale * chat;
         const float sn = fmaxf(sin_theta(vj, vk, chat, ac.cos_scale), 1e-6f);
-        const float c_over_s = c / sn;
+        const float c_over_s = c * __frcp_rn(sn);
         const float rb = 0.5f * (vj.w + vk.w);
         float A[kNA], dA[kNA];
 #pragma unroll
@@ -375,7 +403,7 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
         tR *= ac.ang_pre * fjk;                    // dE/dRbar
         tf *= ac.ang_pre;                          // dE/d(f_j f_k)
         const float dEdchat = ac.cos_scale * tc;
-        const float sj = dEdchat / vj.w, sk = dEdchat / vk.w;
+        const float sj = dEdchat * fj4.z, sk = dEdchat * fk4.z;
         const float rj = 0.5f * tR + tf * fj4.y * fk4.x;
         const float rk = 0.5f * tR + tf * fj4.x * fk4.y;
         float4* Aj = acc3 + tj;

@@ -1,5 +1,6 @@
 // FP32 path of the per-species networks (paper Eq. 2): a tiled SIMT GEMM with
-// fused epilogues, run over 128-row species segments of the AEV matrix.
+// fused epilogues, run over 128-row species segments of the AEV matrix (a
+// 64-row tile never straddles two species).
 //
 // Forward per layer: Z = H W^T + b, H' = CELU(Z), D = CELU'(Z) (kept for the
 // backward).  The last hidden layer's epilogue also forms the atomic energy
@@ -14,6 +15,8 @@ namespace nnp {
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int TM = 8, TN = 4;                  // outputs per thread
+constexpr int kThreads = (BM / TM) * (BN / TN);  // 128
 
 __device__ __forceinline__ float celu_f(float z, float alpha, float inv_alpha) {
   return z > 0.f ? z : alpha * (__expf(z * inv_alpha) - 1.f);
@@ -22,10 +25,14 @@ __device__ __forceinline__ float celu_d(float z, float inv_alpha) {
   return z > 0.f ? 1.f : __expf(z * inv_alpha);
 }
 
+// 64 x 64 output tile per CTA, 128 threads with an 8 x 4 register tile each
+// (rows ty*8.., columns tx*4..).  16-wide K slices of A and B are staged
+// through registers into a double-buffered, transposed shared-memory copy, so
+// each thread reads its 8 rows and 4 columns of one K step as three 16-byte loads.
 template <int EPI>
-__global__ void __launch_bounds__(256) k_gemm_fp32(GemmArgs g) {
-  __shared__ __align__(16) float As[BK][BM + 4];
-  __shared__ __align__(16) float Bs[BK][BN + 4];
+__global__ void __launch_bounds__(kThreads) k_gemm_fp32(GemmArgs g) {
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
   const int m0 = blockIdx.x * BM;
   const int total = g.seg_start[g.S];
   if (m0 >= total) return;
@@ -37,60 +44,77 @@ __global__ void __launch_bounds__(256) k_gemm_fp32(GemmArgs g) {
   const float* A = static_cast<const float*>(g.A) + (size_t)e * g.a_net;
   const float* B = static_cast<const float*>(g.B) + e * g.b_e + s * g.b_s;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int lr = tid >> 2, lq = tid & 3;
-  float acc[4][4];
+  // loaders: A and B slices are 64 rows x 16 k = 256 float4 each, 2 per thread
+  float4 ra[2], rb[2];
+  auto load = [&](int k0) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  const float* a_ptr = A + (size_t)(m0 + lr) * g.lda + lq * 4;
-  const bool b_ok = (n0 + lr) < g.N;
-  const float* b_ptr = B + (size_t)(n0 + lr) * g.ldb + lq * 4;
-  float4 a_next = *reinterpret_cast<const float4*>(a_ptr);
-  float4 b_next = b_ok ? *reinterpret_cast<const float4*>(b_ptr) : make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    __syncthreads();
-    As[lq * 4 + 0][lr] = a_next.x; As[lq * 4 + 1][lr] = a_next.y;
-    As[lq * 4 + 2][lr] = a_next.z; As[lq * 4 + 3][lr] = a_next.w;
-    Bs[lq * 4 + 0][lr] = b_next.x; Bs[lq * 4 + 1][lr] = b_next.y;
-    Bs[lq * 4 + 2][lr] = b_next.z; Bs[lq * 4 + 3][lr] = b_next.w;
-    __syncthreads();
-    if (k0 + BK < g.K) {
-      a_next = *reinterpret_cast<const float4*>(a_ptr + k0 + BK);
-      if (b_ok) b_next = *reinterpret_cast<const float4*>(b_ptr + k0 + BK);
+    for (int i = 0; i < 2; ++i) {
+      const int idx = tid + i * kThreads, r = idx >> 2, q = idx & 3;
+      ra[i] = *reinterpret_cast<const float4*>(A + (size_t)(m0 + r) * g.lda + k0 + q * 4);
+      rb[i] = (n0 + r < g.N) ? *reinterpret_cast<const float4*>(B + (size_t)(n0 + r) * g.ldb + k0 + q * 4)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int idx = tid + i * kThreads, r = idx >> 2, q = idx & 3;
+      As[buf][q * 4 + 0][r] = ra[i].x; As[buf][q * 4 + 1][r] = ra[i].y;
+      As[buf][q * 4 + 2][r] = ra[i].z; As[buf][q * 4 + 3][r] = ra[i].w;
+      Bs[buf][q * 4 + 0][r] = rb[i].x; Bs[buf][q * 4 + 1][r] = rb[i].y;
+      Bs[buf][q * 4 + 2][r] = rb[i].z; Bs[buf][q * 4 + 3][r] = rb[i].w;
+    }
+  };
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    const bool more = k0 + BK < g.K;
+    if (more) load(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float a4[4] = {av.x, av.y, av.z, av.w};
-      const float b4[4] = {bv.x, bv.y, bv.z, bv.w};
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM + 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * TN]);
+      const float a[TM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[TN] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a4[i], b4[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
     }
   }
-  // ---- epilogue
-  const int nb = n0 + tx * 4;
-  const bool n_ok = nb < g.N;  // N is a multiple of 4
+  // ---- epilogue (N is a multiple of 16: a thread's 4 columns are all in or all out)
+  const int nb = n0 + tx * TN;
+  const bool n_ok = nb < g.N;
   const float alpha = g.alpha, inv_alpha = 1.f / g.alpha;
   if (EPI == kEpiCelu || EPI == kEpiCeluDot) {
-    float bias[4] = {0.f, 0.f, 0.f, 0.f}, w4[4] = {0.f, 0.f, 0.f, 0.f};
+    float bias[TN] = {0.f, 0.f, 0.f, 0.f}, w4[TN] = {0.f, 0.f, 0.f, 0.f};
     if (n_ok) {
       const float* bp = g.bias + e * g.bias_e + s * g.bias_s + nb;
-      for (int j = 0; j < 4; ++j) bias[j] = bp[j];
+      for (int j = 0; j < TN; ++j) bias[j] = bp[j];
       if (EPI == kEpiCeluDot) {
         const float* wp = g.w4 + e * g.w4_e + s * g.w4_s + nb;
-        for (int j = 0; j < 4; ++j) w4[j] = wp[j];
+        for (int j = 0; j < TN; ++j) w4[j] = wp[j];
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int m = m0 + ty * 4 + i;
-      float h[4], dd[4], dot = 0.f;
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + ty * TM + i;
+      float h[TN], dd[TN], dot = 0.f;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < TN; ++j) {
         const float zz = acc[i][j] + bias[j];
         h[j] = celu_f(zz, alpha, inv_alpha);
         dd[j] = celu_d(zz, inv_alpha);
@@ -107,6 +131,7 @@ __global__ void __launch_bounds__(256) k_gemm_fp32(GemmArgs g) {
         if (n_ok)
           *reinterpret_cast<float4*>(o) =
               make_float4(w4[0] * dd[0], w4[1] * dd[1], w4[2] * dd[2], w4[3] * dd[3]);
+        // the 16 threads of a row group hold the row's columns
 #pragma unroll
         for (int o2 = 1; o2 < 16; o2 <<= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o2);
         if (tx == 0) atomicAdd(g.e_row + (size_t)e * g.e_row_net + m, dot);
@@ -115,9 +140,9 @@ __global__ void __launch_bounds__(256) k_gemm_fp32(GemmArgs g) {
   } else {
     if (!n_ok) return;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int m = m0 + ty * 4 + i;
-      float v[4] = {acc[i][0], acc[i][1], acc[i][2], acc[i][3]};
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + ty * TM + i;
+      float v[TN] = {acc[i][0], acc[i][1], acc[i][2], acc[i][3]};
       float* o = static_cast<float*>(g.out) + (size_t)m * g.ldo + (size_t)e * g.out_net + nb;
       if (EPI == kEpiMul || EPI == kEpiStoreMul) {
         const float4 a = *reinterpret_cast<const float4*>(
@@ -138,11 +163,11 @@ __global__ void __launch_bounds__(256) k_gemm_fp32(GemmArgs g) {
 void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st, int n_nets) {
   dim3 grid((row_cap + BM - 1) / BM, (g.N + BN - 1) / BN, n_nets);
   switch (g.epi) {
-    case kEpiCelu: k_gemm_fp32<kEpiCelu><<<grid, 256, 0, st>>>(g); break;
-    case kEpiCeluDot: k_gemm_fp32<kEpiCeluDot><<<grid, 256, 0, st>>>(g); break;
-    case kEpiMul: k_gemm_fp32<kEpiMul><<<grid, 256, 0, st>>>(g); break;
-    case kEpiStoreMul: k_gemm_fp32<kEpiStoreMul><<<grid, 256, 0, st>>>(g); break;
-    default: k_gemm_fp32<kEpiStore><<<grid, 256, 0, st>>>(g); break;
+    case kEpiCelu: k_gemm_fp32<kEpiCelu><<<grid, kThreads, 0, st>>>(g); break;
+    case kEpiCeluDot: k_gemm_fp32<kEpiCeluDot><<<grid, kThreads, 0, st>>>(g); break;
+    case kEpiMul: k_gemm_fp32<kEpiMul><<<grid, kThreads, 0, st>>>(g); break;
+    case kEpiStoreMul: k_gemm_fp32<kEpiStoreMul><<<grid, kThreads, 0, st>>>(g); break;
+    default: k_gemm_fp32<kEpiStore><<<grid, kThreads, 0, st>>>(g); break;
   }
 }
 
