@@ -115,9 +115,11 @@ typedef struct {
  * periodic != 0: orthorhombic box of edges box[3] with the minimum-image
  * convention (each edge >= 2 * max(rc_r, rc_a)); otherwise box is ignored.
  * Outputs: energy (1 double, written), forces [n_atoms,3] (written; zero for
- * atoms outside the mask), virial [9] row-major -sum_edges u (x) dE/du (NULL =
- * not computed), atom_energies [n_atoms] float (NULL = not written; zero
- * outside the mask). */
+ * atoms outside the mask; NULL = not computed), virial [9] row-major
+ * -sum_edges u (x) dE/du (NULL = not computed), atom_energies [n_atoms] float
+ * (NULL = not written; zero outside the mask).  When no system of a call asks
+ * for forces or a virial, the backward kernels are skipped (energy-only
+ * re-evaluation, e.g. of stored snapshots for reweighting). */
 typedef struct {
   int64_t n_atoms;
   const float* coords;
@@ -160,7 +162,8 @@ int nnp_reserve(nnp_handle* h, int64_t max_atoms, int max_systems, int max_neigh
  *   species  device uint8 [n_atoms]
  *   box_host host double[3] orthorhombic edges, NULL = non-periodic
  *   mask     device uint8 [n_atoms] or NULL
- *   energy   device double[1]; forces device float32 [n_atoms,3];
+ *   energy   device double[1]; forces device float32 [n_atoms,3] or NULL
+ *            (energy only);
  *   virial   device double[9] or NULL
  * Returns NNP_OK once the work is enqueued; device-side failures are read with
  * nnp_sync_status. */
@@ -352,6 +355,11 @@ int nnp_energy_forces_noalloc(nnp_handle* h, int64_t n_atoms, const float* coord
  *   the angular-cutoff sub-list if angular != 0), -1 past the end; rows of
  *   atoms outside the mask are left untouched. */
 int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream);
+/* Exercises the failure path of the bounded device waits: one thread waits on
+ * an mbarrier phase that nothing completes, gives up after `limit` polls and
+ * records NNP_ERR_TIMEOUT in the handle's status word (read it with
+ * nnp_sync_status); the context stays usable. */
+int nnp_debug_wait_probe(nnp_handle* h, unsigned limit, void* stream);
 int nnp_debug_neighbors(nnp_handle* h, int angular, int cap, int* out, void* stream);
 
 #ifdef __cplusplus

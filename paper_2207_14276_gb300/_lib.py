@@ -40,7 +40,7 @@ EXPORTS = (
     "nnp_profile", "nnp_profile_read", "nnp_profile_stage_name", "nnp_energy_forces_noalloc",
     "nnp_server_create", "nnp_server_destroy", "nnp_server_register", "nnp_server_submit",
     "nnp_server_poll", "nnp_server_stats", "nnp_force_vjp_batch", "nnp_force_vjp",
-    "nnp_n_weights",
+    "nnp_n_weights", "nnp_debug_wait_probe",
 )
 
 
@@ -129,6 +129,7 @@ def lib():
     L.nnp_force_vjp.argtypes = [P, i64, P, P, P, P, ctypes.c_double, P, P, P, P, P, P]
     L.nnp_n_weights.argtypes = [P]
     L.nnp_n_weights.restype = i64
+    L.nnp_debug_wait_probe.argtypes = [P, ctypes.c_uint, P]
     L.nnp_profile.argtypes = [P, i]
     L.nnp_profile_read.argtypes = [P, i, P, P, i, P]
     L.nnp_profile_stage_name.restype = ctypes.c_char_p

@@ -26,11 +26,13 @@ using namespace nnp;
 namespace nnp {
 void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st);
 int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
-                  float alpha, cudaStream_t st, int* n_launch, StageHook* hook, void* state);
+                  float alpha, cudaStream_t st, int* n_launch, StageHook* hook, void* state,
+                  bool energy_only);
 int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, int row_cap,
                    const float* aev, float* dEdG, void** state);
 void mlp_tc_release(void* state);
 void launch_aev_to_bf16(const Ws& ws, int n_in, const AevConst& ac, void* out, cudaStream_t st);
+void launch_wait_probe(int* status, unsigned limit, cudaStream_t st);
 }  // namespace nnp
 
 namespace {
@@ -445,14 +447,20 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     { StageTimer t(h, st, 1); launch_neighbors(ws, n_in, m.ac, st); }
     { StageTimer t(h, st, 2); launch_aev_fwd(ws, n_in, m.ac, st); }
     launches += 6;
+    // energy only when no system asks for forces or a virial
+    bool energy_only = true;
+    for (int b = 0; b < n_sys; ++b) energy_only &= (sy[b].forces == nullptr && sy[b].virial == nullptr);
     StageHook hook{h, st};
     if (m.precision == NNP_BF16_MLP) {
-      rc = launch_mlp_tc(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, h->tc_state);
+      rc = launch_mlp_tc(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, h->tc_state, energy_only);
       if (rc) return rc;
     } else {
-      launch_mlp_fp32(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook);
+      launch_mlp_fp32(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, energy_only);
     }
-    { StageTimer t(h, st, 9); launch_aev_bwd(ws, n_in, m.ac, any_virial ? 1 : 0, st); }
+    if (!energy_only) {
+      StageTimer t(h, st, 9);
+      launch_aev_bwd(ws, n_in, m.ac, any_virial ? 1 : 0, st);
+    }
     {
       StageTimer t(h, st, 10);
       launch_finalize_e(ws, n_in, h->mb.e_row, m.md.E, ws.row_cap, m.ebias, st);
@@ -566,8 +574,8 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
 int validate_system(const nnp_handle* h, const nnp_system_t& s) {
   if (s.n_atoms < 0) return fail(NNP_ERR_ARG, "negative atom count");
   if (!s.energy) return fail(NNP_ERR_ARG, "energy output pointer is null");
-  if (s.n_atoms > 0 && (!s.coords || !s.species || !s.forces))
-    return fail(NNP_ERR_ARG, "coords, species and forces pointers are required");
+  if (s.n_atoms > 0 && (!s.coords || !s.species))
+    return fail(NNP_ERR_ARG, "coords and species pointers are required");
   if (s.periodic) {
     const double rc = std::max(h->model->ac.rc_r, h->model->ac.rc_a);
     for (int c = 0; c < 3; ++c) {
@@ -995,6 +1003,18 @@ extern "C" int64_t nnp_n_weights(const nnp_handle* h) {
 
 int nnp_aev_dim(const nnp_handle* h) { return h ? h->model->ac.D : -1; }
 int nnp_last_launch_count(const nnp_handle* h) { return h ? h->last_launches : -1; }
+
+int nnp_debug_wait_probe(nnp_handle* h, unsigned limit, void* stream) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  if (!h->arena) {
+    int rc = ensure_arena(h, 1, 1);
+    if (rc) return rc;
+  }
+  launch_wait_probe(h->ws.status, limit, static_cast<cudaStream_t>(stream));
+  CU_TRY(cudaGetLastError());
+  return NNP_OK;
+}
 
 int nnp_profile(nnp_handle* h, int enable) {
   if (!h) return fail(NNP_ERR_ARG, "null handle");

@@ -25,11 +25,13 @@ __global__ void k_finalize(Ws ws, const float* e_row, int E, int e_row_net,
     ws.atom_e[slot] = (float)Ei;
     const SysDev& d = ws.sys[b];
     const int local = ws.pos_src[p] - d.in.in_base;
-    const float4 f = ws.f_pos[p];
-    float* F = d.in.forces + 3 * (size_t)local;
-    F[0] = f.x;
-    F[1] = f.y;
-    F[2] = f.z;
+    if (d.in.forces) {
+      const float4 f = ws.f_pos[p];
+      float* F = d.in.forces + 3 * (size_t)local;
+      F[0] = f.x;
+      F[1] = f.y;
+      F[2] = f.z;
+    }
     if (d.in.atom_e) d.in.atom_e[local] = (float)Ei;
   }
   // segmented FP64 reduction over the systems present in this warp

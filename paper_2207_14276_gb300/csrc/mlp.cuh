@@ -75,6 +75,7 @@ struct StageHook {
 void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st);
 void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st, int n_nets);
 void launch_mlp_fp32(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
-                     float alpha, cudaStream_t st, int* n_launch, StageHook* hook);
+                     float alpha, cudaStream_t st, int* n_launch, StageHook* hook,
+                     bool energy_only = false);
 
 }  // namespace nnp

@@ -177,7 +177,8 @@ void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st) {
 
 // the six GEMMs of one forward + backward-to-input pass over every species
 void launch_mlp_fp32(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
-                     float alpha, cudaStream_t st, int* n_launch, StageHook* hook) {
+                     float alpha, cudaStream_t st, int* n_launch, StageHook* hook,
+                     bool energy_only) {
   const int E = md.E, S = md.S, Dp = md.Dp, h1 = md.h1, h2 = md.h2, h3 = md.h3;
   const int R = ws.row_cap;
   GemmArgs g{};
@@ -218,6 +219,10 @@ void launch_mlp_fp32(const Ws& ws, const MlpDims& md, const MlpWeights& mw, cons
   if (hook) hook->begin(5);
   launch_gemm_fp32(g, R, st, E);
   if (hook) hook->end();
+  if (energy_only) {   // no forces wanted: the backward to the input is skipped
+    if (n_launch) *n_launch += 4;
+    return;
+  }
   // B3: delta2 = (delta3 W3) * D2   (written over H2)
   g.A = mb.d3; g.lda = E * h3; g.a_net = h3;
   g.B = mw.W3T; g.b_s = (long long)h2 * h3; g.b_e = (long long)S * h2 * h3; g.ldb = h3;

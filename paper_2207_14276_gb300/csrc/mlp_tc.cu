@@ -339,6 +339,21 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
                  : "memory");
 }
 
+// Failure-path check of the bounded waits: one thread waits (with the limit
+// given) on an mbarrier whose phase nothing completes, gives up, and records
+// the timeout in the status word exactly as k_gemm_tc does.
+__global__ void k_wait_probe(int* status, unsigned limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_sh;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  abort_sh = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  bool ok = false;
+  for (unsigned it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(&bar, 0);
+  if (!ok) atomicOr(status, kStTimeout);
+}
+
 __global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
                           const int* seg_start, int S, int Dp) {
   const long long total = (long long)seg_start[S] * Dp / 4;
@@ -510,15 +525,22 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
 
 void mlp_tc_release(void* state) { delete static_cast<TcState*>(state); }
 
+void launch_wait_probe(int* status, unsigned limit, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(status, limit);
+}
+
 int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, float alpha,
-                  cudaStream_t st, int* n_launch, StageHook* hook, void* state) {
+                  cudaStream_t st, int* n_launch, StageHook* hook, void* state, bool energy_only) {
   (void)mw; (void)mb;
   TcState* s = static_cast<TcState*>(state);
   if (!s) return NNP_ERR_ARG;
   if (hook) hook->begin(11);
   k_to_bf16<<<4 * 152, 256, 0, st>>>(ws.aev, static_cast<__nv_bfloat16*>(s->aev_h), ws.seg_start, md.S, md.Dp);
   if (hook) hook->end();
-  for (auto& p : s->plans) {
+  // plans 0-2 are the forward layers, 3-5 the backward to the input
+  const size_t n_plans = energy_only ? 3 : s->plans.size();
+  for (size_t i = 0; i < n_plans; ++i) {
+    auto& p = s->plans[i];
     TcArgs a = p.a;
     a.alpha = alpha;
     a.seg_start = ws.seg_start;
@@ -528,7 +550,7 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
     k_gemm_tc<<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a);
     if (hook) hook->end();
   }
-  if (n_launch) *n_launch += 1 + (int)s->plans.size();
+  if (n_launch) *n_launch += 1 + (int)n_plans;
   return NNP_OK;
 }
 

@@ -79,9 +79,11 @@ __global__ void k_prep(Ws ws, BatchParams bp, int n_chunk, int S) {
     b = bp.sys_base + k;
     ml = (si.mask == nullptr) || (si.mask[local] != 0);
     // every output force starts at zero (atoms outside the mask keep it)
-    si.forces[3 * local + 0] = 0.f;
-    si.forces[3 * local + 1] = 0.f;
-    si.forces[3 * local + 2] = 0.f;
+    if (si.forces) {
+      si.forces[3 * local + 0] = 0.f;
+      si.forces[3 * local + 1] = 0.f;
+      si.forces[3 * local + 2] = 0.f;
+    }
     if (si.atom_e) si.atom_e[local] = 0.f;
     if (si.dLdR) {
       si.dLdR[3 * local + 0] = 0.f;

@@ -131,7 +131,7 @@ class Potential:
         return (E, F, V.view(3, 3)) if virial else (E, F)
 
     def energy_forces_batch(self, systems, stream=None, check_status=True, atom_energies=False,
-                            virial=False, outputs=None):
+                            virial=False, outputs=None, forces=True):
         """systems: list of dicts with coords, species, optional box and mask (cuda tensors).
         Returns a list of dicts with energy [1], forces [n,3] (and virial / atom energies)."""
         L = lib()
@@ -143,8 +143,9 @@ class Potential:
             for s in systems:
                 dev = s["coords"].device
                 n = s["coords"].shape[0]
-                o = {"energy": torch.empty(1, dtype=torch.float64, device=dev),
-                     "forces": torch.empty((n, 3), dtype=torch.float32, device=dev)}
+                o = {"energy": torch.empty(1, dtype=torch.float64, device=dev)}
+                if forces:
+                    o["forces"] = torch.empty((n, 3), dtype=torch.float32, device=dev)
                 if virial:
                     o["virial"] = torch.empty(9, dtype=torch.float64, device=dev)
                 if atom_energies:
@@ -162,7 +163,7 @@ class Potential:
                 for c in range(3):
                     d.box[c] = float(box[c])
             d.energy = o["energy"].data_ptr()
-            d.forces = o["forces"].data_ptr()
+            d.forces = o["forces"].data_ptr() if "forces" in o else None
             d.virial = o["virial"].data_ptr() if "virial" in o else None
             d.atom_energies = o["atom_energies"].data_ptr() if "atom_energies" in o else None
         for attempt in range(2):

@@ -269,3 +269,33 @@ def test_solvated100k_sampled(torch_cuda):
     G = pot.debug_rows(0, s.n_atoms)[torch.from_numpy(idx).cuda()].cpu().numpy()
     np.testing.assert_allclose(G, ref["aev"], rtol=2e-5, atol=1e-6)
     assert np.abs(F.astype(np.float64).sum(0)).max() < 1e-2
+
+
+def test_bounded_wait_times_out_and_context_survives(torch_cuda):
+    """A device wait on a barrier that nothing completes gives up after its limit,
+    the host reads NNP_ERR_TIMEOUT from the status word, and the next call works."""
+    import ctypes
+    import torch
+    from paper_2207_14276_gb300 import _lib
+    pot, orc = make("ani4")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert _lib.lib().nnp_debug_wait_probe(pot._h, 1 << 16, stream) == 0
+    assert pot.sync_status() == _lib.NNP_ERR_TIMEOUT
+    assert pot.sync_status() == 0          # the status word was cleared by the read
+    s = synth.workload("gas24")[0][0]
+    check_system(pot, orc, s, aev=False)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_energy_only_matches_full_evaluation(torch_cuda, precision):
+    """Energy-only re-evaluation (no forces requested: backward kernels skipped)
+    returns the energies of the full evaluation (same forward arithmetic)."""
+    pot, orc = make("ani4", precision=precision)
+    mols, _, _ = synth.workload("molecules64")
+    systems = [to_cuda(m) for m in mols[:20]] + [to_cuda(synth.water_box(200, 18.0, 6, seed=15))]
+    full = pot.energy_forces_batch(systems)
+    eonly = pot.energy_forces_batch(systems, forces=False)
+    for a, b in zip(full, eonly):
+        e0, e1 = float(a["energy"].cpu()[0]), float(b["energy"].cpu()[0])
+        assert e1 == pytest.approx(e0, rel=1e-6, abs=1e-6)
+        assert "forces" not in b
