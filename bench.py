@@ -106,6 +106,10 @@ def stage_work(stage, spec, counts, n_atoms, precision):
         return flops, "FLOP", "alu"
     if stage == "neighbors":
         return n_atoms * (16 + 4 * (nr + na) + 32), "B", "hbm"
+    if stage == "mlp":   # the fused FP32 chain: three layers, output dot, backward to G
+        fwd = D * h1 + h1 * h2 + h2 * h3 + h3
+        bwd = h3 * h2 + h2 * h1 + h1 * D
+        return 2.0 * n_atoms * E * (fwd + bwd), "FLOP", "alu"
     gemm = {"mlp_l1": (D, E * h1), "mlp_l2": (h1, h2 * E), "mlp_l3": (h2, h3 * E),
             "mlp_b3": (h3, h2 * E), "mlp_b2": (h2, h1 * E), "mlp_b1": (E * h1, D)}
     if stage in gemm:

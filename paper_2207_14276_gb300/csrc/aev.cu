@@ -102,6 +102,13 @@ __device__ __forceinline__ float sin_theta(const float4& a, const float4& b, flo
   return sqrtf(fmaf(1.f - k * k, chat * chat, s2));
 }
 
+// float4s of shared memory per warp of the backward kernel: neighbour geometry,
+// cutoffs and accumulators (3 cap_a), radial dE/dG (32), the angular blocks'
+// dE/dG (8 per block) and the block table (5 ints per block + 1)
+__host__ __device__ constexpr int aev_bwd_warp_f4(int cap_a, int n_pairs) {
+  return 3 * cap_a + 32 + 8 * n_pairs + (5 * n_pairs + 1 + 3) / 4;
+}
+
 // per-warp header: species offsets/counts of the radial and angular lists
 struct ListHdr {
   int off_r[kMaxSpecies + 1], off_a[kMaxSpecies + 1];
@@ -285,20 +292,28 @@ k_aev_fwd(Ws ws, AevConst ac) {
   for (int f = ac.D + lane; f < ac.Dp; f += 32) G[f] = 0.f;
 }
 
-template <int ZETA>
+template <int ZETA, bool VIR>
 __global__ void __launch_bounds__(kWarps * 32, 3)
-k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
+k_aev_bwd(Ws ws, AevConst ac) {
+  constexpr bool want_virial = VIR;
   extern __shared__ float4 sm4[];
   __shared__ ListHdr hdrs[kWarps];
   const int w = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31;
   const int p = blockIdx.x * kWarps + w;
   if (p >= ws.totals[0]) return;
-  float4* angv = sm4 + (size_t)w * (3 * ws.cap_a + 40);
+  float4* angv = sm4 + (size_t)w * aev_bwd_warp_f4(ws.cap_a, ac.n_pairs);
   float4* angf = angv + ws.cap_a;          // fc, dfc
-  float4* acc3 = angf + ws.cap_a;          // dE/du per angular neighbour
+  // dE/du per angular neighbour as three arrays (x, y, z): lanes adding into
+  // consecutive neighbours hit consecutive banks
+  float* accx = reinterpret_cast<float*>(angf + ws.cap_a);
+  float* accy = accx + ws.cap_a;
+  float* accz = accy + ws.cap_a;
+  float4* acc3 = angf + ws.cap_a;          // the region of the three arrays
   float* grad = reinterpret_cast<float*>(acc3 + ws.cap_a);  // S*16 radial dE/dG
-  float4* gblk = acc3 + ws.cap_a + 32;     // current angular block's dE/dG, [z][a]
+  float4* gall = acc3 + ws.cap_a + 32;     // every angular block's dE/dG, [block][z][a]
+  int4* bt_geo = reinterpret_cast<int4*>(gall + 8 * ac.n_pairs);     // [n_pairs]
+  int* bt_start = reinterpret_cast<int*>(bt_geo + ac.n_pairs);       // [n_pairs + 1]
   ListHdr& H = hdrs[w];
 
   const float4 xi = ws.xyzq[p];
@@ -314,7 +329,9 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
     const float inv = 1.f / g.r;
     angv[t] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
     angf[t] = make_float4(fcut(g.r, ac.rc_a), fcut_d(g.r, ac.rc_a), inv, 0.f);
-    acc3[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    accx[t] = 0.f;
+    accy[t] = 0.f;
+    accz[t] = 0.f;
   }
   __syncwarp();
   float fi[3] = {0.f, 0.f, 0.f};
@@ -347,28 +364,62 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
       }
     }
   }
-  // ---- angular triplets, one lane per (j, k) pair
+  // ---- angular triplets, one lane per (j, k) pair, numbered continuously over
+  // all species-pair blocks of the centre so that a warp's 32 lanes stay busy
+  // across block boundaries
   const float ca_ = -ac.eta_a * kLog2e;
   const float m2eta = -2.f * ac.eta_a;
-  int pidx = 0;
-  for (int s = 0; s < ac.S; ++s)
-    for (int u = s; u < ac.S; ++u, ++pidx) {
-      const int os = H.off_a[s], cs = H.off_a[s + 1] - os;
+  const int np = ac.n_pairs;
+  // block table: geometry (os, cs, ou, cu | same << 16) and first triplet number
+  for (int q0 = 0, carry = 0; q0 < np; q0 += 32) {
+    const int q = q0 + lane;
+    int n_tri = 0;
+    if (q < np) {
+      int sp = 0, rem = q;
+      while (rem >= ac.S - sp) { rem -= ac.S - sp; ++sp; }
+      const int u = sp + rem;
+      const int os = H.off_a[sp], cs = H.off_a[sp + 1] - os;
       const int ou = H.off_a[u], cu = H.off_a[u + 1] - ou;
-      const int same = (s == u);
-      const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
-      if (n_tri == 0) continue;
-      const float inv_cu = 1.f / (float)max(cu, 1), inv_cs = 1.f / (float)max(cs, 1);
-      // the block's 32 dE/dG values (index 8a + z), transposed to [z][a] so that
-      // each angle section is one broadcast 16-byte load
-      __syncwarp();
-      reinterpret_cast<float*>(gblk)[(lane & 7) * 4 + (lane >> 3)] = g_row[ac.S * kNR + pidx * 32 + lane];
-      __syncwarp();
-      for (int t0 = 0; t0 < n_tri; t0 += 32) {
-        const int t = t0 + lane;
-        if (t >= n_tri) continue;
-        int j, k;
-        decode_pair_diag(t, same, cs, cu, inv_cs, inv_cu, &j, &k);
+      const int same = (sp == u);
+      n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
+      bt_geo[q] = make_int4(os, cs, ou, cu | (same << 16));
+    }
+    int incl = n_tri;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, o);
+      if ((int)lane >= o) incl += v;
+    }
+    if (q < np) bt_start[q] = carry + incl - n_tri;
+    carry += __shfl_sync(kFull, incl, 31);
+    if (q0 + 32 >= np && lane == 0) bt_start[np] = carry;
+  }
+  // every block's 32 dE/dG values (index 8a + z), transposed to [z][a] so that
+  // an angle section is one 16-byte load
+  {
+    const float* ga = g_row + ac.S * kNR;
+    float* gf = reinterpret_cast<float*>(gall);
+    for (int f = lane; f < np * 32; f += 32)
+      gf[(f & ~31) + (f & 7) * 4 + ((f >> 3) & 3)] = ga[f];
+  }
+  __syncwarp();
+  const int T = bt_start[np];
+  int bl = 0, cur = -1;
+  int os = 0, cs = 0, ou = 0, cu = 0, same = 0;
+  float inv_cs = 0.f, inv_cu = 0.f;
+  for (int t = lane; t < T; t += 32) {
+    while (bt_start[bl + 1] <= t) ++bl;
+    if (bl != cur) {
+      cur = bl;
+      const int4 g4 = bt_geo[bl];
+      os = g4.x; cs = g4.y; ou = g4.z; cu = g4.w & 0xffff; same = g4.w >> 16;
+      inv_cs = 1.f / (float)max(cs, 1);
+      inv_cu = 1.f / (float)max(cu, 1);
+    }
+    int j, k;
+    decode_pair_diag(t - bt_start[bl], same, cs, cu, inv_cs, inv_cu, &j, &k);
+    const float4* gblk = gall + bl * 8;
+    {
         const int tj = os + j, tk = ou + k;
         const float4 vj = angv[tj], vk = angv[tk];
         const float4 fj4 = angf[tj], fk4 = angf[tk];
@@ -406,19 +457,17 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
         const float sj = dEdchat * fj4.z, sk = dEdchat * fk4.z;
         const float rj = 0.5f * tR + tf * fj4.y * fk4.x;
         const float rk = 0.5f * tR + tf * fj4.x * fk4.y;
-        float4* Aj = acc3 + tj;
-        float4* Ak = acc3 + tk;
-        atomicAdd(&Aj->x, sj * (vk.x - chat * vj.x) + rj * vj.x);
-        atomicAdd(&Aj->y, sj * (vk.y - chat * vj.y) + rj * vj.y);
-        atomicAdd(&Aj->z, sj * (vk.z - chat * vj.z) + rj * vj.z);
-        atomicAdd(&Ak->x, sk * (vj.x - chat * vk.x) + rk * vk.x);
-        atomicAdd(&Ak->y, sk * (vj.y - chat * vk.y) + rk * vk.y);
-        atomicAdd(&Ak->z, sk * (vj.z - chat * vk.z) + rk * vk.z);
-      }
+        atomicAdd(accx + tj, sj * (vk.x - chat * vj.x) + rj * vj.x);
+        atomicAdd(accy + tj, sj * (vk.y - chat * vj.y) + rj * vj.y);
+        atomicAdd(accz + tj, sj * (vk.z - chat * vj.z) + rj * vj.z);
+        atomicAdd(accx + tk, sk * (vj.x - chat * vk.x) + rk * vk.x);
+        atomicAdd(accy + tk, sk * (vj.y - chat * vk.y) + rk * vk.y);
+        atomicAdd(accz + tk, sk * (vj.z - chat * vk.z) + rk * vk.z);
     }
+  }
   __syncwarp();
   for (int t = lane; t < na_tot; t += 32) {
-    const float4 a = acc3[t];
+    const float4 a = make_float4(accx[t], accy[t], accz[t], 0.f);
     const float4 v = angv[t];
     atomicAdd(&ws.f_pos[la[t]], make_float4(-a.x, -a.y, -a.z, 0.f));
     fi[0] += a.x; fi[1] += a.y; fi[2] += a.z;
@@ -451,8 +500,8 @@ k_aev_bwd(Ws ws, AevConst ac, int want_virial) {
 size_t aev_fwd_smem(const Ws& ws) {
   return (size_t)kWarps * (ws.cap_a + ws.cap_a / 4 + ws.cap_r / 2 + 2) * sizeof(float4);
 }
-size_t aev_bwd_smem(const Ws& ws) {
-  return (size_t)kWarps * (3 * ws.cap_a + 40) * sizeof(float4);
+size_t aev_bwd_smem(const Ws& ws, int n_pairs) {
+  return (size_t)kWarps * aev_bwd_warp_f4(ws.cap_a, n_pairs) * sizeof(float4);
 }
 
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st) {
@@ -466,10 +515,15 @@ void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st)
 void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
                     cudaStream_t st) {
   if (n_in <= 0) return;
-  const size_t sm = aev_bwd_smem(ws);
+  const size_t sm = aev_bwd_smem(ws, ac.n_pairs);
   const int grid = (n_in + kWarps - 1) / kWarps;
-  if (ac.zeta == 32) k_aev_bwd<32><<<grid, kWarps * 32, sm, st>>>(ws, ac, want_virial);
-  else k_aev_bwd<0><<<grid, kWarps * 32, sm, st>>>(ws, ac, want_virial);
+  if (ac.zeta == 32) {
+    if (want_virial) k_aev_bwd<32, true><<<grid, kWarps * 32, sm, st>>>(ws, ac);
+    else k_aev_bwd<32, false><<<grid, kWarps * 32, sm, st>>>(ws, ac);
+  } else {
+    if (want_virial) k_aev_bwd<0, true><<<grid, kWarps * 32, sm, st>>>(ws, ac);
+    else k_aev_bwd<0, false><<<grid, kWarps * 32, sm, st>>>(ws, ac);
+  }
 }
 
 cudaError_t aev_set_smem_limits(const Ws& ws) {
@@ -477,8 +531,11 @@ cudaError_t aev_set_smem_limits(const Ws& ws) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_aev_fwd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, f))) return e;
   if ((e = cudaFuncSetAttribute(k_aev_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, f))) return e;
-  if ((e = cudaFuncSetAttribute(k_aev_bwd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-  return cudaFuncSetAttribute(k_aev_bwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  const void* bwd[4] = {(const void*)k_aev_bwd<32, false>, (const void*)k_aev_bwd<32, true>,
+                        (const void*)k_aev_bwd<0, false>, (const void*)k_aev_bwd<0, true>};
+  for (const void* fn : bwd)
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+  return cudaSuccess;
 }
 
 // raise (never lower) the dynamic shared-memory limit of the AEV kernels to what
@@ -486,9 +543,10 @@ cudaError_t aev_set_smem_limits(const Ws& ws) {
 cudaError_t aev_ensure_smem(const Ws& ws) {
   const int need_f = (int)aev_fwd_smem(ws), need_b = (int)aev_bwd_smem(ws);
   const void* fwd[2] = {(const void*)k_aev_fwd<32>, (const void*)k_aev_fwd<0>};
-  const void* bwd[2] = {(const void*)k_aev_bwd<32>, (const void*)k_aev_bwd<0>};
+  const void* bwd[4] = {(const void*)k_aev_bwd<32, false>, (const void*)k_aev_bwd<32, true>,
+                        (const void*)k_aev_bwd<0, false>, (const void*)k_aev_bwd<0, true>};
   for (int pass = 0; pass < 2; ++pass)
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < (pass == 0 ? 2 : 4); ++i) {
       const void* fn = pass == 0 ? fwd[i] : bwd[i];
       const int need = pass == 0 ? need_f : need_b;
       cudaFuncAttributes attr;

@@ -346,6 +346,7 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
   h->arena_bytes = bytes;
   carve(h, static_cast<char*>(p));
   CU_TRY(aev_set_smem_limits(h->ws));
+  CU_TRY(mlp_fused_ensure_smem(h->model->md));
   if (h->model->precision == NNP_BF16_MLP) {
     int rc = mlp_tc_prepare(h->model->md, h->model->mw, h->mb, h->ws.row_cap, h->ws.aev,
                             h->ws.dEdG, &h->tc_state);
@@ -357,8 +358,9 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
 
 // stage names (index = stage id) reported by nnp_profile_read
 const char* kStageNames[] = {"prep", "neighbors", "aev_fwd", "mlp_l1", "mlp_l2", "mlp_l3",
-                             "mlp_b3", "mlp_b2", "mlp_b1", "aev_bwd", "finalize", "mlp_cvt"};
-constexpr int kNumStages = 12;
+                             "mlp_b3", "mlp_b2", "mlp_b1", "aev_bwd", "finalize", "mlp_cvt",
+                             "mlp"};
+constexpr int kNumStages = 13;
 
 cudaEvent_t prof_event(nnp_handle* h) {
   if (!h->prof_pool.empty()) {
@@ -1200,6 +1202,7 @@ extern "C" int nnp_energy_forces_noalloc(nnp_handle* h, int64_t n_atoms, const f
   cudaGetLastError();  // a stale error of an earlier runtime call is not this call's
   // the fixed neighbour lists may need more shared memory than other handles set up
   CU_TRY(aev_ensure_smem(ws));
+  CU_TRY(mlp_fused_ensure_smem(m.md));
   // the status word starts at zero on every call; the kernels clear the rest
   CU_TRY(cudaMemsetAsync(ws.status, 0, 4 * sizeof(int), st));
   if (n_atoms == 0) {

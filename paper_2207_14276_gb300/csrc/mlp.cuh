@@ -74,6 +74,11 @@ struct StageHook {
 
 void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st);
 void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st, int n_nets);
+// the whole FP32 chain of one-network models as a single kernel per 32-row tile
+bool mlp_fused_supported(const MlpDims& md);
+cudaError_t mlp_fused_ensure_smem(const MlpDims& md);
+void launch_mlp_fused(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
+                      float alpha, bool energy_only, cudaStream_t st);
 void launch_mlp_fp32(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
                      float alpha, cudaStream_t st, int* n_launch, StageHook* hook,
                      bool energy_only = false);

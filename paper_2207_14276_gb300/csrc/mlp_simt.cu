@@ -176,9 +176,17 @@ void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st) {
 }
 
 // the six GEMMs of one forward + backward-to-input pass over every species
+// (one fused kernel where the network shape has a compiled variant)
 void launch_mlp_fp32(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
                      float alpha, cudaStream_t st, int* n_launch, StageHook* hook,
                      bool energy_only) {
+  if (mlp_fused_supported(md)) {  // one kernel for the whole chain
+    if (hook) hook->begin(12);
+    launch_mlp_fused(ws, md, mw, mb, alpha, energy_only, st);
+    if (hook) hook->end();
+    if (n_launch) *n_launch += 1;
+    return;
+  }
   const int E = md.E, S = md.S, Dp = md.Dp, h1 = md.h1, h2 = md.h2, h3 = md.h3;
   const int R = ws.row_cap;
   GemmArgs g{};

@@ -131,7 +131,7 @@ void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
 cudaError_t aev_set_smem_limits(const Ws& ws);
 cudaError_t aev_ensure_smem(const Ws& ws);
 size_t aev_fwd_smem(const Ws& ws);
-size_t aev_bwd_smem(const Ws& ws);
+size_t aev_bwd_smem(const Ws& ws, int n_pairs = kMaxSpecies * (kMaxSpecies + 1) / 2);
 // ---- finalize.cu
 void launch_finalize_e(const Ws& ws, int n_in, const float* e_row, int E, int e_row_net,
                        const double* ebias, cudaStream_t st);
