@@ -12,6 +12,8 @@
 //   k_scatter  packed (cell-ordered) float4 coordinates and index maps
 //   k_neighbors one warp per centre: scan the 27 neighbour cells, keep pairs
 //              with R <= rc_r, mark R <= rc_a, write species-sorted lists
+#include <algorithm>
+
 #include "nnp_internal.cuh"
 
 namespace nnp {
@@ -221,14 +223,16 @@ __global__ void k_setup(Ws ws, AevConst ac) {
   }
 }
 
+// periodic systems: the coordinate wrapped into [0, L] (the value the cell index
+// is taken from and the one stored for the kernels); else the coordinate itself
+__device__ __forceinline__ float wrap_coord(float x, const SysDev& d, int c) {
+  if (!d.in.periodic) return x;
+  const float L = d.in.box_hi[c];
+  return x - floorf(x / L) * L;   // exact for x already in [0, L)
+}
+
 __device__ __forceinline__ int cell_coord(float x, const SysDev& d, int c) {
-  float u;
-  if (d.in.periodic) {
-    const float L = d.in.box_hi[c];
-    u = x - floorf(x / L) * L;   // exact for x already in [0, L)
-  } else {
-    u = x - d.origin[c];
-  }
+  const float u = d.in.periodic ? wrap_coord(x, d, c) : x - d.origin[c];
   int k = (int)floorf(u * d.inv_cell[c]);
   return min(max(k, 0), d.nc[c] - 1);
 }
@@ -305,8 +309,10 @@ __global__ void k_scatter(Ws ws, int n_in) {
   const int gcell = ws.in_cell[gi];
   const int pos = ws.cell_start[gcell] + ws.in_rank[gi];
   const int slot = ws.in_slot[gi];
-  ws.xyzq[pos] = make_float4(d.in.coords[3 * local + 0], d.in.coords[3 * local + 1],
-                             d.in.coords[3 * local + 2], __int_as_float((int)d.in.species[local]));
+  ws.xyzq[pos] = make_float4(wrap_coord(d.in.coords[3 * local + 0], d, 0),
+                             wrap_coord(d.in.coords[3 * local + 1], d, 1),
+                             wrap_coord(d.in.coords[3 * local + 2], d, 2),
+                             __int_as_float((int)d.in.species[local]));
   ws.pos_src[pos] = gi;
   ws.pos_slot[pos] = slot;
   ws.pos_sys[pos] = b;
@@ -314,16 +320,14 @@ __global__ void k_scatter(Ws ws, int n_in) {
   ws.slot_pos[slot] = pos;
 }
 
-// one warp per centre; staged candidates in shared memory, then species-sorted
-constexpr int kNbWarps = 8;
-
-__global__ void __launch_bounds__(kNbWarps * 32) k_neighbors(Ws ws, AevConst ac) {
-  __shared__ int st_j[kNbWarps][kStageCap];
-  __shared__ uint8_t st_t[kNbWarps][kStageCap];   // species | (angular << 7)
-  const int w = threadIdx.x >> 5;
+// Neighbour lists of centre p by one warp, candidates read from global memory
+// and staged in st_j / st_t (kStageCap each), then species-sorted.  Used for
+// home cells whose 27-cell neighbourhood does not fit the shared-memory stage
+// of k_neighbors.
+__device__ void centre_lists_global(const Ws& ws, const AevConst& ac, int p, int* st_j,
+                                    uint8_t* st_t) {
   const unsigned lane = threadIdx.x & 31;
-  const int p = blockIdx.x * kNbWarps + w;
-  if (p >= ws.totals[0]) return;
+  __syncwarp();   // the stage may still be read by the warp's previous centre
   const float4 xi = ws.xyzq[p];
   const int b = ws.pos_sys[p];
   const SysDev& d = ws.sys[b];
@@ -402,8 +406,8 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_neighbors(Ws ws, AevConst ac)
           if (keep) {
             const int at = cnt + __popc(bal & lanemask_lt());
             if (at < kStageCap) {
-              st_j[w][at] = j;
-              st_t[w][at] = (uint8_t)(sj | (ang ? 0x80 : 0));
+              st_j[at] = j;
+              st_t[at] = (uint8_t)(sj | (ang ? 0x80 : 0));
             }
           }
           cnt += __popc(bal);
@@ -423,8 +427,8 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_neighbors(Ws ws, AevConst ac)
       bool mr = false, ma = false;
       int j = 0;
       if (t < nst) {
-        const int tt = st_t[w][t];
-        j = st_j[w][t];
+        const int tt = st_t[t];
+        j = st_j[t];
         mr = (tt & 0x7f) == s;
         ma = mr && (tt & 0x80);
       }
@@ -458,6 +462,213 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_neighbors(Ws ws, AevConst ac)
       atomicMax(ws.status + 1, cnt);
       atomicMax(ws.status + 2, wr_a);
     }
+  }
+}
+
+
+// Species-sorted radial (R <= rc_r) and angular (R <= rc_a) lists of centre p
+// from the candidates cand[t] / cand_j[t], t in [sp_start[s], sp_start[s+1])
+// for species s (coordinates already shifted to the centre's periodic image;
+// dimensions flagged in min_img take the minimum image per pair instead).
+__device__ __forceinline__ void centre_lists_staged(const Ws& ws, const AevConst& ac, int p,
+                                                    const float4* cand, const int* cand_j,
+                                                    const int* sp_start, const int* min_img,
+                                                    const SysDev& d) {
+  const unsigned lane = threadIdx.x & 31;
+  const float4 xi = ws.xyzq[p];
+  const float rr2 = ac.rc_r * ac.rc_r, ra2 = ac.rc_a * ac.rc_a;
+  const bool any_mi = min_img[0] | min_img[1] | min_img[2];
+  uint16_t* hdr = ws.nb_cnt + (size_t)p * 16;
+  int* out_r = ws.nb_r + (size_t)p * ws.cap_r;
+  int* out_a = ws.nb_a + (size_t)p * ws.cap_a;
+  int wr_r = 0, wr_a = 0;
+  for (int s = 0; s < ac.S; ++s) {
+    int cr = 0, ca = 0;
+    const int end = sp_start[s + 1];
+    for (int t0 = sp_start[s]; t0 < end; t0 += 32) {
+      const int t = t0 + lane;
+      bool keep = false, ang = false;
+      int j = 0;
+      if (t < end) {
+        const float4 xj = cand[t];
+        j = cand_j[t];
+        float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        if (any_mi) {
+          float n;
+          if (min_img[0]) { n = rintf(dx / d.in.box_hi[0]); dx = fmaf(-n, d.in.box_hi[0], dx); dx = fmaf(-n, d.in.box_lo[0], dx); }
+          if (min_img[1]) { n = rintf(dy / d.in.box_hi[1]); dy = fmaf(-n, d.in.box_hi[1], dy); dy = fmaf(-n, d.in.box_lo[1], dy); }
+          if (min_img[2]) { n = rintf(dz / d.in.box_hi[2]); dz = fmaf(-n, d.in.box_hi[2], dz); dz = fmaf(-n, d.in.box_lo[2], dz); }
+        }
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        keep = (r2 <= rr2) && (r2 > 1e-12f) && (j != p);
+        ang = keep && (r2 <= ra2);
+      }
+      const unsigned br = __ballot_sync(0xffffffffu, keep);
+      const unsigned ba = __ballot_sync(0xffffffffu, ang);
+      if (keep) {
+        const int at = wr_r + cr + __popc(br & lanemask_lt());
+        if (at < ws.cap_r) out_r[at] = j;
+      }
+      if (ang) {
+        const int at = wr_a + ca + __popc(ba & lanemask_lt());
+        if (at < ws.cap_a) out_a[at] = j;
+      }
+      cr += __popc(br);
+      ca += __popc(ba);
+    }
+    const int keep_r = max(0, min(cr, ws.cap_r - wr_r));
+    const int keep_a = max(0, min(ca, ws.cap_a - wr_a));
+    if (lane == 0) {
+      hdr[s] = (uint16_t)keep_r;
+      hdr[8 + s] = (uint16_t)keep_a;
+    }
+    wr_r += cr;
+    wr_a += ca;
+  }
+  if (lane == 0) {
+    for (int s = ac.S; s < 8; ++s) { hdr[s] = 0; hdr[8 + s] = 0; }
+    if (wr_r > ws.cap_r || wr_a > ws.cap_a || wr_r > kStageCap) {
+      atomicOr(ws.status, kStCapacity);
+      atomicMax(ws.status + 1, wr_r);
+      atomicMax(ws.status + 2, wr_a);
+    }
+  }
+}
+
+constexpr int kNbThreads = 256;   // 8 warps
+constexpr int kCandCap = 2048;    // staged candidates of one home cell
+
+// One CTA per home cell (grid-stride over the cells of the batch).  The atoms of
+// the 27 neighbour cells are staged once in shared memory, shifted to the home
+// cell's periodic image and stably sorted by species; then one warp per centre
+// of the home cell scans them species by species and appends the accepted
+// neighbours to its lists, which come out species-sorted without a sort pass.
+__global__ void __launch_bounds__(kNbThreads) k_neighbors(Ws ws, AevConst ac) {
+  __shared__ float4 cand[kCandCap];
+  __shared__ int cand_j[kCandCap];
+  __shared__ uint16_t chunk_cnt[kCandCap / 32][kMaxSpecies];
+  __shared__ int r_beg[27], r_off[28];
+  __shared__ float r_shift[27][3];
+  __shared__ int sp_start[kMaxSpecies + 1];
+  __shared__ int min_img[3];
+  const int tid = threadIdx.x, w = tid >> 5;
+  const unsigned lane = tid & 31;
+  const int n_cells = ws.totals[1];
+  for (int gc = blockIdx.x; gc < n_cells; gc += gridDim.x) {
+    const int cbeg = ws.cell_start[gc], cend = ws.cell_start[gc + 1];
+    if (cbeg == cend) continue;   // uniform across the CTA
+    const int b = ws.pos_sys[cbeg];
+    const SysDev& d = ws.sys[b];
+    const int per = d.in.periodic;
+    const int nc[3] = {d.nc[0], d.nc[1], d.nc[2]};
+    const int lc = gc - d.cell_base;
+    const int cc[3] = {lc / (nc[1] * nc[2]), (lc / nc[2]) % nc[1], lc % nc[2]};
+    // ---- the 27 (or fewer) neighbour cells: thread t < 27 takes offset (t/9, t/3%3, t%3)
+    if (w == 0) {
+      int cnt = 0, beg = 0;
+      float sh[3] = {0.f, 0.f, 0.f};
+      if (lane < 27) {
+        const int o[3] = {(int)lane / 9, ((int)lane / 3) % 3, (int)lane % 3};
+        bool ok = true;
+        int k[3];
+        for (int c = 0; c < 3; ++c) {
+          if (per && nc[c] < 3) {
+            // every cell of this dimension once, minimum image per pair
+            k[c] = o[c];
+            ok &= o[c] < nc[c];
+          } else {
+            k[c] = cc[c] + o[c] - 1;
+            if (per) {
+              if (k[c] < 0) { k[c] += nc[c]; sh[c] = -d.in.box_hi[c]; }
+              else if (k[c] >= nc[c]) { k[c] -= nc[c]; sh[c] = d.in.box_hi[c]; }
+            } else {
+              ok &= (k[c] >= 0 && k[c] < nc[c]);
+            }
+          }
+        }
+        if (ok) {
+          const int g = d.cell_base + (k[0] * nc[1] + k[1]) * nc[2] + k[2];
+          beg = ws.cell_start[g];
+          cnt = ws.cell_start[g + 1] - beg;
+        }
+        r_beg[lane] = beg;
+        r_shift[lane][0] = sh[0]; r_shift[lane][1] = sh[1]; r_shift[lane][2] = sh[2];
+      }
+      int incl = cnt;
+      for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o2);
+        if ((int)lane >= o2) incl += u;
+      }
+      if (lane < 27) r_off[lane] = incl - cnt;
+      if (lane == 26) r_off[27] = incl;
+      if (lane < 3) min_img[lane] = (per && nc[lane] < 3) ? 1 : 0;
+    }
+    __syncthreads();
+    const int total = r_off[27];
+    if (total > kCandCap) {
+      // too many candidates to stage: per-centre search from global memory,
+      // with the candidate arrays as the warps' staging space
+      int* stj = reinterpret_cast<int*>(cand) + w * kStageCap;
+      uint8_t* stt = reinterpret_cast<uint8_t*>(reinterpret_cast<int*>(cand) + 8 * kStageCap) + w * kStageCap;
+      for (int p = cbeg + w; p < cend; p += kNbThreads / 32) centre_lists_global(ws, ac, p, stj, stt);
+      __syncthreads();
+      continue;
+    }
+    const int n_chunks = (total + 31) >> 5;
+    // ---- stable species sort of the candidates: counts per 32-chunk, offsets, placement
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int ch = w; ch < n_chunks; ch += kNbThreads / 32) {
+        const int q = ch * 32 + (int)lane;
+        const bool valid = q < total;
+        int r = 0;
+        if (valid) {
+          int lo = 0, hi = 26;   // last range with r_off <= q
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (r_off[mid] <= q) lo = mid; else hi = mid - 1;
+          }
+          r = lo;
+        }
+        const int j = valid ? r_beg[r] + q - r_off[r] : 0;
+        const float4 xj = valid ? ws.xyzq[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int sp = valid ? __float_as_int(xj.w) : -1;
+        if (pass == 0) {
+          for (int s = 0; s < ac.S; ++s) {
+            const unsigned bal = __ballot_sync(0xffffffffu, sp == s);
+            if (lane == 0) chunk_cnt[ch][s] = (uint16_t)__popc(bal);
+          }
+        } else {
+          const unsigned same = __match_any_sync(0xffffffffu, sp);
+          if (valid) {
+            const int pos = sp_start[sp] + chunk_cnt[ch][sp] + __popc(same & lanemask_lt());
+            cand[pos] = make_float4(xj.x + r_shift[r][0], xj.y + r_shift[r][1], xj.z + r_shift[r][2], xj.w);
+            cand_j[pos] = j;
+          }
+        }
+      }
+      __syncthreads();
+      if (pass == 0) {
+        if (tid < ac.S) {   // thread s: exclusive offsets of species s over the chunks
+          int run = 0;
+          for (int ch = 0; ch < n_chunks; ++ch) {
+            const int v = chunk_cnt[ch][tid];
+            chunk_cnt[ch][tid] = (uint16_t)run;
+            run += v;
+          }
+          sp_start[tid + 1] = run;   // count for now
+        }
+        __syncthreads();
+        if (tid == 0) {
+          sp_start[0] = 0;
+          for (int s = 0; s < ac.S; ++s) sp_start[s + 1] += sp_start[s];
+        }
+        __syncthreads();
+      }
+    }
+    // ---- one warp per centre of the home cell
+    for (int p = cbeg + w; p < cend; p += kNbThreads / 32)
+      centre_lists_staged(ws, ac, p, cand, cand_j, sp_start, min_img, d);
+    __syncthreads();   // the stage is rebuilt for the next home cell
   }
 }
 
@@ -496,7 +707,11 @@ void launch_scatter(const Ws& ws, int n_in, cudaStream_t st) {
 
 void launch_neighbors(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st) {
   if (n_in <= 0) return;
-  k_neighbors<<<(n_in + kNbWarps - 1) / kNbWarps, kNbWarps * 32, 0, st>>>(ws, ac);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(ws.cell_cap, 4 * std::max(sms, 1)));
+  k_neighbors<<<grid, kNbThreads, 0, st>>>(ws, ac);
 }
 
 }  // namespace nnp

@@ -101,6 +101,16 @@ def test_gas24_energy_forces_aev_neighbours(torch_cuda):
     np.testing.assert_allclose(g, ref, rtol=1e-4, atol=1e-7)
 
 
+def test_dense_box_neighbourhood_beyond_the_stage(torch_cuda):
+    # three times liquid density: the 27-cell neighbourhood of every home cell
+    # (about 3000 atoms) exceeds the shared-memory candidate stage of the
+    # neighbour kernel, so every centre takes the per-centre global-memory search
+    pot, orc = make("ani4")
+    s = synth.water_box(1000, 18.0, 10, seed=21)
+    check_system(pot, orc, s, rel_f=3e-4, aev=False)
+    compare_neighbours(pot, s, pot.spec)
+
+
 def test_water9000_fp32(torch_cuda):
     pot, orc = make("ani4")
     systems, _, _ = synth.workload("water9000")
