@@ -1,26 +1,31 @@
 // Tensor-core path of the per-species networks (paper Eq. 2): BF16 operands,
 // FP32 accumulation in tensor memory, on the 5th-generation tensor cores.
 //
-// Each CTA computes one 128-row x n_tile output tile of one layer GEMM
+// A persistent CTA (one or two per SM) walks a static list of 128-row x n_tile
+// output tiles of one layer GEMM
 //   C[m, n] = sum_k A[m, e*K + k] * B_{e,s}[n, k]
-// for the species s of its 128-row segment and the ensemble member e.
-//   warp 4   TMA producer: 64-wide K slices of A and B into a ring of shared
+// for the species s of the tile's 128-row segment and the ensemble member e.
+//   warp 8   TMA producer: 64-wide K slices of A and B into a ring of shared
 //            memory stages (128-byte swizzle), completion on mbarriers
-//   warp 5   MMA issuer: tcgen05.mma kind::f16 (M = 128, N = n_tile, K = 16)
-//            into a TMEM accumulator; tcgen05.commit frees a stage
-//   warps 0-3 epilogue: tcgen05.ld of its 32 accumulator rows, bias, CELU,
-//            the width-1 output layer as a dot product, and in the backward the
-//            product with CELU'(z) rebuilt from the stored activation
-//            (1 for h > 0, 1 + h/alpha otherwise); BF16 (FP32 for dE/dG) stores.
-// The N tiles of a row tile are adjacent in launch order (they share A in L2);
-// tiles are at most 128 columns with 3 stages so that two CTAs share an SM and
-// one CTA's epilogue overlaps the other's MMAs.
+//   warp 9   MMA issuer: tcgen05.mma kind::f16 (M = 128, N = n_tile, K = 16)
+//            into one of two TMEM accumulators; tcgen05.commit frees a stage
+//            and, after the tile's last K slice, hands the accumulator over
+//   warps 0-7 epilogue: warp w reads accumulator rows 32 (w % 4).. and every
+//            other 16-column chunk (w / 4 picks which); bias, CELU, the width-1
+//            output layer as a dot product, and in the backward the product
+//            with CELU'(z) rebuilt from the stored activation (1 for h > 0,
+//            1 + h/alpha otherwise); BF16 (FP32 for dE/dG) stores; then it
+//            releases the accumulator to the MMA warp.
+// With two accumulators the epilogue of one tile overlaps the MMAs of the next.
+// The N tiles of a row tile are adjacent in the tile order (concurrent CTAs
+// share the row tile of A in L2).
 // Every mbarrier wait is bounded; a CTA that gives up sets the status word,
-// drains the copies it issued, frees its tensor memory and returns.
+// drains the copies and MMAs it issued, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
@@ -33,7 +38,9 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;           // bf16 elements per K slice (one 128-byte swizzle row)
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr int kMaxStages = 4;
 constexpr unsigned kWaitLimit = 1u << 24;
 // dynamic shared memory limit: the 227 KB per block minus the kernel's static
@@ -41,7 +48,7 @@ constexpr unsigned kWaitLimit = 1u << 24;
 constexpr int kMaxDynSmem = 232448 - 8192;
 
 struct TcArgs {
-  int N, K, n_tile, n_k, tmem_cols, stages;
+  int N, K, n_tile, n_k, tmem_cols, stages, nets;
   int a_c1_per_e;       // A map coordinate 1 = e * a_c1_per_e (net slice)
   int b_c2_per_e;       // B map coordinate 2 = e * b_c2_per_e + s
   uint32_t idesc;
@@ -69,6 +76,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
@@ -154,13 +165,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float celu_f(float z, float alpha, float inv_alpha) {
-  return z > 0.f ? z : alpha * (__expf(z * inv_alpha) - 1.f);
-}
-__device__ __forceinline__ float celu_d(float z, float inv_alpha) {
-  return z > 0.f ? 1.f : __expf(z * inv_alpha);
-}
-
 __device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float (&v)[16]) {
   uint32_t w[8];
 #pragma unroll
@@ -186,24 +190,42 @@ __device__ __forceinline__ void load_bf16x16(const __nv_bfloat16* src, float (&v
   }
 }
 
+__device__ __forceinline__ void load_f32x16(const float* src, float (&v)[16]) {
+  const float4* s = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 t = __ldg(s + q);
+    v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+  }
+}
+
+struct Tile {
+  int m0, n0, e, s;
+};
+
+__device__ __forceinline__ Tile tile_of(int t, int n_tiles_n, int row_tiles, int n_tile,
+                                        const int* seg_start, int S) {
+  Tile tl;
+  const int ni = t % n_tiles_n, rest = t / n_tiles_n;
+  tl.m0 = (rest % row_tiles) * kBM;
+  tl.e = rest / row_tiles;
+  tl.n0 = ni * n_tile;
+  int s = 0;
+  while (s + 1 < S && tl.m0 >= seg_start[s + 1]) ++s;
+  tl.s = s;
+  return tl;
+}
+
+template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, TcArgs g) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
-  __shared__ float bias_sh[256], w4_sh[256];
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
-  // the N tiles of one row tile are adjacent in launch order, so they run
-  // together and share the row tile of A in L2
-  const int m0 = blockIdx.y * kBM;
-  const int total = g.seg_start[g.S];
-  if (m0 >= total) return;
-  int s = 0;
-  while (s + 1 < g.S && m0 >= g.seg_start[s + 1]) ++s;
-  const int e = blockIdx.z;
-  const int n0 = blockIdx.x * g.n_tile;
-  const int kStages = g.stages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kStages = g.stages;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int a_bytes = kBM * kBK * 2, b_bytes = g.n_tile * kBK * 2;
   const int stage_bytes = a_bytes + b_bytes;   // multiple of 1024
@@ -214,6 +236,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       mbar_init(&full_bar[i], 1);
       mbar_init(&empty_bar[i], 1);
     }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull_bar[i], 1);
+      mbar_init(&tempty_bar[i], kEpiWarps);
+    }
     mbar_init(&done_bar, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -221,121 +247,165 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_sh)),
-                 "r"((uint32_t)g.tmem_cols)
+                 "r"((uint32_t)(2 * g.tmem_cols))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  for (int c = threadIdx.x; c < g.n_tile; c += blockDim.x) {
-    const int n = n0 + c;
-    const bool ok = n < g.N;
-    bias_sh[c] = (ok && g.bias) ? g.bias[e * g.bias_e + s * g.bias_s + n] : 0.f;
-    w4_sh[c] = (ok && g.w4) ? g.w4[e * g.w4_e + s * g.w4_s + n] : 0.f;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
+  // tiles: (net, row tile, N tile) with the N tiles innermost; the row tiles
+  // counted from the device-side segment table
+  const int row_tiles = g.seg_start[g.S] / kBM;
+  const int n_tiles_n = (g.N + g.n_tile - 1) / g.n_tile;
+  const int T = n_tiles_n * row_tiles * g.nets;
 
-  int issued = 0, consumed = 0;
-  if (warp == 4 && lane == 0) {
-    // ---- TMA producer
-    const int a_c1 = e * g.a_c1_per_e, b_c2 = e * g.b_c2_per_e + s;
-    for (int kb = 0; kb < g.n_k; ++kb) {
-      const int st = kb % kStages;
-      const unsigned round = kb / kStages;
-      if (kb >= kStages && !mbar_wait(&empty_bar[st], (round - 1) & 1, abort_flag)) break;
-      uint8_t* sa = smem + st * stage_bytes;
-      uint8_t* sb = sa + a_bytes;
-      mbar_expect_tx(&full_bar[st], (unsigned)stage_bytes);
-      tma_load_3d(sa, &ta, &full_bar[st], kb * kBK, a_c1, m0);
-      tma_load_3d(sb, &tb, &full_bar[st], kb * kBK, n0, b_c2);
-      ++issued;
+  if (warp == kProdWarp) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
+        const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.n_tile, g.seg_start, g.S);
+        const int a_c1 = tl.e * g.a_c1_per_e, b_c2 = tl.e * g.b_c2_per_e + tl.s;
+        for (int kb = 0; kb < g.n_k; ++kb, ++it) {
+          const int st = it % kStages;
+          const unsigned round = it / kStages;
+          if (it >= kStages && !mbar_wait(&empty_bar[st], (round - 1) & 1, abort_flag)) { ok = false; break; }
+          uint8_t* sa = smem + st * stage_bytes;
+          uint8_t* sb = sa + a_bytes;
+          mbar_expect_tx(&full_bar[st], (unsigned)stage_bytes);
+          tma_load_3d(sa, &ta, &full_bar[st], kb * kBK, a_c1, tl.m0);
+          tma_load_3d(sb, &tb, &full_bar[st], kb * kBK, tl.n0, b_c2);
+        }
+      }
+      // every issued copy has landed before the CTA may exit
+      if (*abort_flag)
+        for (int k = it - kStages < 0 ? 0 : it - kStages; k < it; ++k)
+          mbar_drain(&full_bar[k % kStages], (k / kStages) & 1);
     }
-    // make sure every issued copy has landed before the CTA may exit
-    if (*abort_flag)
-      for (int kb = 0; kb < issued; ++kb) mbar_drain(&full_bar[kb % kStages], (kb / kStages) & 1);
-  } else if (warp == 5 && lane == 0) {
-    // ---- MMA issuer
-    for (int kb = 0; kb < g.n_k; ++kb) {
-      const int st = kb % kStages;
-      if (!mbar_wait(&full_bar[st], (kb / kStages) & 1, abort_flag)) break;
-      tc_fence_after();
-      const uint32_t sa = smem_u32(smem + st * stage_bytes);
-      const uint32_t sb = sa + a_bytes;
-      const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sb);
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      int it = 0, j = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < T && ok; t += gridDim.x, ++j) {
+        const int ab = j & 1;
+        if (j >= 2 && !mbar_wait(&tempty_bar[ab], ((j >> 1) - 1) & 1, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(ab * g.tmem_cols);
+        for (int kb = 0; kb < g.n_k; ++kb, ++it) {
+          const int st = it % kStages;
+          if (!mbar_wait(&full_bar[st], (it / kStages) & 1, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + st * stage_bytes);
+          const uint32_t sb = sa + a_bytes;
+          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sb);
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk)
-        umma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), g.idesc,
-                  (kb > 0 || kk > 0) ? 1u : 0u);
-      umma_commit(&empty_bar[st]);
-      ++consumed;
+          for (int kk = 0; kk < kBK / 16; ++kk)
+            umma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), g.idesc,
+                      (kb > 0 || kk > 0) ? 1u : 0u);
+          umma_commit(&empty_bar[st]);
+        }
+        if (ok) umma_commit(&tfull_bar[ab]);
+      }
+      umma_commit(&done_bar);   // arrives when every MMA issued above has completed
+      mbar_drain(&done_bar, 0);
     }
-    umma_commit(&done_bar);   // arrives when every MMA issued above has completed
-  }
-  (void)consumed;
-
-  if (warp < 4) {
-    // ---- epilogue: thread owns accumulator row m
-    const bool ok = mbar_wait(&done_bar, 0, abort_flag);
-    tc_fence_after();
-    if (ok && !*abort_flag) {
-      const int m = m0 + warp * 32 + lane;
-      const float alpha = g.alpha, inv_alpha = 1.f / g.alpha;
+  } else {
+    // ---- epilogue: warp w owns accumulator rows 32 (w % 4).. and every other
+    // 16-column chunk starting at chunk w / 4
+    const int q = warp & 3, half = warp >> 2;
+    const float alpha = g.alpha, inv_alpha = 1.f / g.alpha;
+    int j = 0;
+    constexpr int kMaxChunks = 256 / 32;   // 16-column chunks of one warp per tile
+    for (int t = blockIdx.x; t < T; t += gridDim.x, ++j) {
+      const int ab = j & 1;
+      const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.n_tile, g.seg_start, g.S);
+      const int m = tl.m0 + q * 32 + lane;
+      // the backward's stored activations do not depend on the MMAs: their loads
+      // are issued before the wait for the accumulator
+      uint4 pre[EPI == kEpiMul ? kMaxChunks : 1][2];
+      if (EPI == kEpiMul) {
+        const __nv_bfloat16* arow = static_cast<const __nv_bfloat16*>(g.aux) + (size_t)m * g.ld_aux +
+                                    (size_t)tl.e * g.aux_net + tl.n0;
+#pragma unroll
+        for (int ci = 0; ci < kMaxChunks; ++ci) {
+          const int c0 = half * 16 + 32 * ci;
+          if (c0 < g.n_tile && tl.n0 + c0 < g.N) {
+            const uint4* src = reinterpret_cast<const uint4*>(arow + c0);
+            pre[ci][0] = src[0];
+            pre[ci][1] = src[1];
+          }
+        }
+      }
+      if (!mbar_wait(&tfull_bar[ab], (j >> 1) & 1, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * g.tmem_cols);
       float dot = 0.f;
-      for (int c0 = 0; c0 < g.n_tile; c0 += 16) {
-        const int n = n0 + c0;
+#pragma unroll(EPI == kEpiMul ? kMaxChunks : 1)
+      for (int ci = 0; ci < kMaxChunks; ++ci) {
+        const int c0 = half * 16 + 32 * ci;
+        if (c0 >= g.n_tile) break;
+        const int n = tl.n0 + c0;
         float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld16(trow + (uint32_t)c0, v);
         if (n >= g.N) continue;
-        if (g.epi == kEpiCelu || g.epi == kEpiCeluDot) {
-          float h[16], dd[16];
+        if (EPI == kEpiCelu || EPI == kEpiCeluDot) {
+          float b[16];
+          load_f32x16(g.bias + tl.e * g.bias_e + tl.s * g.bias_s + n, b);
+          float w4[16];
+          if (EPI == kEpiCeluDot) load_f32x16(g.w4 + tl.e * g.w4_e + tl.s * g.w4_s + n, w4);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const float z = v[i] + bias_sh[c0 + i];
-            h[i] = celu_f(z, alpha, inv_alpha);
-            dd[i] = celu_d(z, inv_alpha);
-          }
-          __nv_bfloat16* o = static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)e * g.out_net + n;
-          if (g.epi == kEpiCelu) {
-            store_bf16x16(o, h);   // CELU' is rebuilt from h where it is needed
-          } else {
-            float d3[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              dot = fmaf(h[i], w4_sh[c0 + i], dot);
-              d3[i] = w4_sh[c0 + i] * dd[i];
+            const float z = v[i] + b[i];
+            const float ez = __expf(z * inv_alpha);
+            const float h = z > 0.f ? z : alpha * (ez - 1.f);
+            if (EPI == kEpiCeluDot) {
+              dot = fmaf(h, w4[i], dot);
+              v[i] = w4[i] * (z > 0.f ? 1.f : ez);   // delta3 = w4 * CELU'(z)
+            } else {
+              v[i] = h;   // CELU' is rebuilt from h where it is needed
             }
-            store_bf16x16(o, d3);
           }
-        } else if (g.epi == kEpiMul) {
+          store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)tl.e * g.out_net + n, v);
+        } else if (EPI == kEpiMul) {
           // aux holds the layer's stored activation h = CELU(z): CELU'(z) = 1 for h > 0,
           // 1 + h / alpha otherwise (exp(z/alpha) = 1 + h/alpha on that branch)
           float a[16];
-          load_bf16x16(static_cast<const __nv_bfloat16*>(g.aux) + (size_t)m * g.ld_aux + (size_t)e * g.aux_net + n, a);
+          {
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(pre[EPI == kEpiMul ? ci : 0]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+              a[2 * i] = f.x;
+              a[2 * i + 1] = f.y;
+            }
+          }
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] *= (a[i] > 0.f) ? 1.f : fmaf(a[i], inv_alpha, 1.f);
-          store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)e * g.out_net + n, v);
+          store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)tl.e * g.out_net + n, v);
         } else {
           float4* o = reinterpret_cast<float4*>(static_cast<float*>(g.out) + (size_t)m * g.ldo + n);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          for (int k = 0; k < 4; ++k) o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
         }
       }
-      if (g.epi == kEpiCeluDot) g.e_row[(size_t)e * g.e_row_net + m] = dot;
+      // the two warps of a row each add their half of the output-layer dot product
+      // (e_row starts at zero; a sum of two terms does not depend on their order)
+      if (EPI == kEpiCeluDot) atomicAdd(g.e_row + (size_t)tl.e * g.e_row_net + m, dot);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[ab]);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (*abort_flag) {
-    if (threadIdx.x == 0) {
-      atomicOr(g.status, kStTimeout);
-      mbar_drain(&done_bar, 0);   // outstanding MMAs finish before the memory is freed
-    }
-    __syncthreads();
-  }
+  if (*abort_flag && threadIdx.x == 0) atomicOr(g.status, kStTimeout);
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)g.tmem_cols)
+                 "r"((uint32_t)(2 * g.tmem_cols))
                  : "memory");
 }
 
@@ -411,17 +481,15 @@ struct TcState {
   int row_cap = 0, Dp = 0, E = 1;
 };
 
-int pick_n_tile(int N, int row_tiles, bool single) {
-  // at most 128 columns (two CTAs share an SM's tensor memory) unless the
-  // output-layer dot product needs the whole row in one tile
+int pick_n_tile(int N, int tiles_per_col, bool single, int sms) {
+  // the output-layer dot product needs the whole row in one tile; otherwise the
+  // widest multiple of 16 up to 256 that divides N, narrowed while the tiles
+  // would not cover every SM
   if (single) return N <= 256 ? N : 256;
   int nt = 16;
-  for (int c = 128; c >= 16; c -= 16)
+  for (int c = 256; c >= 16; c -= 16)
     if (N % c == 0) { nt = c; break; }
-  if (!single) {
-    // more CTAs for small problems: split N while there is less than one wave
-    while (row_tiles * ((N + nt - 1) / nt) < 148 && nt % 32 == 0 && nt > 64) nt /= 2;
-  }
+  while (tiles_per_col * (N / nt) < sms && nt % 32 == 0 && nt > 64) nt /= 2;
   return nt;
 }
 
@@ -448,6 +516,12 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
   const int S = md.S, E = md.E, Dp = md.Dp, h1 = md.h1, h2 = md.h2, h3 = md.h3;
   const uint64_t R = (uint64_t)row_cap;
   const int row_tiles = (row_cap + kBM - 1) / kBM;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    delete st;
+    return NNP_ERR_CUDA;
+  }
   struct L {
     int stage, epi, N, K, nets;
     const void* A; uint64_t a_d0, a_d1, a_st1, a_st2;
@@ -486,7 +560,7 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
   for (const L& l : layers) {
     TcGemmPlan p{};
     const bool single = (l.epi == kEpiCeluDot);
-    const int nt = pick_n_tile(l.N, row_tiles * l.nets, single);
+    const int nt = pick_n_tile(l.N, row_tiles * l.nets, single, sms);
     if (nt % 16 != 0 || nt > 256 || (single && nt < l.N)) { delete st; return NNP_ERR_UNSUPPORTED; }
     if (!make_map(&p.ta, l.A, l.a_d0, l.a_d1, R, l.a_st1, l.a_st2, 1, kBM) ||
         !make_map(&p.tb, l.B, l.b_d0, l.b_d1, l.b_d2, l.b_d0, l.b_d0 * l.b_d1, (uint32_t)nt, 1)) {
@@ -496,6 +570,7 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     TcArgs& a = p.a;
     a.N = l.N; a.K = l.K; a.n_tile = nt; a.n_k = (l.K + kBK - 1) / kBK;
     a.tmem_cols = tmem_cols_for(nt);
+    a.nets = l.nets;
     a.a_c1_per_e = (l.nets > 1) ? 1 : 0;
     a.b_c2_per_e = l.b_c2_per_e;
     a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
@@ -505,20 +580,32 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     a.out = l.out; a.ldo = l.ldo; a.out_net = l.out_net; a.out2 = l.out2;
     a.aux = l.aux; a.ld_aux = l.ld_aux; a.aux_net = l.aux_net;
     a.e_row = mb.e_row; a.e_row_net = row_cap;
-    p.grid = dim3((l.N + nt - 1) / nt, row_tiles, l.nets);
-    // shared memory: stages plus 1 KB for alignment; never so little that more CTAs
-    // would share an SM than its 512 tensor-memory columns can hold
-    a.stages = a.n_k < 3 ? (a.n_k < 1 ? 1 : a.n_k) : 3;
-    size_t sm = (size_t)a.stages * (kBM * kBK * 2 + nt * kBK * 2) + 1024;
-    const int max_ctas = 512 / a.tmem_cols;
-    const size_t floor_sm = 232448 / (size_t)(max_ctas + 1) + 1;
+    // CTAs per SM: as many as the 512 tensor-memory columns hold (two accumulators
+    // each), at most two; the shared memory is split between them and never so
+    // small that more CTAs could share an SM than its tensor memory holds
+    const int ctas = std::min(2, 512 / (2 * a.tmem_cols));
+    const size_t stage_bytes = (size_t)(kBM * kBK * 2 + nt * kBK * 2);
+    const size_t budget = std::min((size_t)kMaxDynSmem, (size_t)232448 / ctas - 2048);
+    int stages = (int)std::min<size_t>(kMaxStages, (budget - 1024) / stage_bytes);
+    stages = std::min(stages, std::max(a.n_k, 1));
+    if (stages < 1) { delete st; return NNP_ERR_UNSUPPORTED; }
+    a.stages = stages;
+    size_t sm = (size_t)stages * stage_bytes + 1024;
+    const size_t floor_sm = 232448 / (size_t)(ctas + 1) + 1;
     p.smem = sm > floor_sm ? sm : floor_sm;
     if (p.smem > (size_t)kMaxDynSmem) { delete st; return NNP_ERR_UNSUPPORTED; }
+    const long long tiles = (long long)((l.N + nt - 1) / nt) * row_tiles * l.nets;
+    p.grid = dim3((unsigned)std::max(1LL, std::min(tiles, (long long)sms * ctas)));
     p.stage_id = l.stage;
     st->plans.push_back(p);
   }
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-  if (e != cudaSuccess) { delete st; return NNP_ERR_CUDA; }
+  const void* fns[4] = {(const void*)k_gemm_tc<kEpiCelu>, (const void*)k_gemm_tc<kEpiCeluDot>,
+                        (const void*)k_gemm_tc<kEpiMul>, (const void*)k_gemm_tc<kEpiStore>};
+  for (const void* fn : fns)
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess) {
+      delete st;
+      return NNP_ERR_CUDA;
+    }
   *state_out = st;
   return NNP_OK;
 }
@@ -547,7 +634,16 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
     a.S = md.S;
     a.status = ws.status;
     if (hook) hook->begin(p.stage_id);
-    k_gemm_tc<<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a);
+    switch (a.epi) {
+      case kEpiCelu: k_gemm_tc<kEpiCelu><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a); break;
+      case kEpiCeluDot:
+        // the two epilogue warps of a row add their halves of the dot product
+        cudaMemsetAsync(a.e_row, 0, sizeof(float) * (size_t)md.E * a.e_row_net, st);
+        k_gemm_tc<kEpiCeluDot><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a);
+        break;
+      case kEpiMul: k_gemm_tc<kEpiMul><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a); break;
+      default: k_gemm_tc<kEpiStore><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a); break;
+    }
     if (hook) hook->end();
   }
   if (n_launch) *n_launch += 1 + (int)n_plans;
