@@ -26,6 +26,8 @@
 //   dE/du_j and dE/du_k and adds them to per-neighbour accumulators in shared
 //   memory; afterwards each neighbour receives one vector atomic and the centre
 //   one warp-reduced atomic.
+#include <cuda_bf16.h>
+
 #include "nnp_internal.cuh"
 
 namespace nnp {
@@ -181,6 +183,12 @@ __device__ __forceinline__ void decode_pair_diag(int t, int same, int c, int cu,
   }
 }
 
+// one AEV element: the FP32 row and, for the tensor-core path, its BF16 copy
+__device__ __forceinline__ void put_g(float* G, uint16_t* Gh, int f, float v) {
+  G[f] = v;
+  if (Gh) Gh[f] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
 // after the call lane l holds the warp sum of v[l]
 __device__ __forceinline__ float transpose_reduce32(float (&v)[32], unsigned lane) {
 #pragma unroll
@@ -212,7 +220,9 @@ k_aev_fwd(Ws ws, AevConst ac) {
 
   const float4 xi = ws.xyzq[p];
   const SysDev& d = ws.sys[ws.pos_sys[p]];
-  float* G = ws.aev + (size_t)ws.pos_slot[p] * ac.Dp;
+  const size_t row = (size_t)ws.pos_slot[p] * ac.Dp;
+  float* G = ws.aev + row;
+  uint16_t* Gh = ws.aev_h ? ws.aev_h + row : nullptr;
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
   const int nr_tot = H.off_r[ac.S], na_tot = H.off_a[ac.S];
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
@@ -241,7 +251,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
       acc = fmaf(fast_exp2(cr_ * x * x), q.y, acc);
     }
     acc += __shfl_xor_sync(kFull, acc, 16);
-    if (lane < 16) G[s * kNR + lane] = acc;
+    if (lane < 16) put_g(G, Gh, s * kNR + lane, acc);
   }
   // ---- angular, Eq. 5
   const float ca_ = -ac.eta_a * kLog2e;
@@ -252,9 +262,9 @@ k_aev_fwd(Ws ws, AevConst ac) {
       const int ou = H.off_a[u], cu = H.off_a[u + 1] - ou;
       const int same = (s == u);
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
-      float* Gb = G + ac.S * kNR + pidx * 32;
+      const int fb = ac.S * kNR + pidx * 32;
       if (n_tri == 0) {
-        Gb[lane] = 0.f;
+        put_g(G, Gh, fb + lane, 0.f);
         continue;
       }
       const float inv_cu = 1.f / (float)max(cu, 1);
@@ -287,9 +297,9 @@ k_aev_fwd(Ws ws, AevConst ac) {
           }
         }
       }
-      Gb[lane] = transpose_reduce32(acc, lane);
+      put_g(G, Gh, fb + lane, transpose_reduce32(acc, lane));
     }
-  for (int f = ac.D + lane; f < ac.Dp; f += 32) G[f] = 0.f;
+  for (int f = ac.D + lane; f < ac.Dp; f += 32) put_g(G, Gh, f, 0.f);
 }
 
 template <int ZETA, bool VIR>

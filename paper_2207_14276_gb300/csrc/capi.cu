@@ -297,15 +297,24 @@ size_t carve(nnp_handle* h, char* base) {
   ws.dEdG = c.take<float>(rows * Dp);
   ws.atom_e = c.take<float>(rows);
   ws.f_pos = c.take<float4>(n);
-  const size_t esz = (m.precision == NNP_BF16_MLP) ? 2 : 4;
+  const bool bf16 = (m.precision == NNP_BF16_MLP);
+  const size_t esz = bf16 ? 2 : 4;
   MlpBufs& mb = h->mb;
-  mb.H1 = c.take<char>(rows * E * m.md.h1 * esz);
-  mb.D1 = c.take<char>(rows * E * m.md.h1 * esz);
-  mb.H2 = c.take<char>(rows * E * m.md.h2 * esz);
-  mb.D2 = c.take<char>(rows * E * m.md.h2 * esz);
-  mb.d3 = c.take<char>(rows * E * m.md.h3 * esz);
+  mb = MlpBufs{};
+  // the fused FP32 kernel keeps its activations on chip; the tensor-core path
+  // rebuilds CELU' from the activations and stores no derivative buffers
+  if (bf16 || !mlp_fused_supported(m.md)) {
+    mb.H1 = c.take<char>(rows * E * m.md.h1 * esz);
+    mb.H2 = c.take<char>(rows * E * m.md.h2 * esz);
+    mb.d3 = c.take<char>(rows * E * m.md.h3 * esz);
+    if (!bf16) {
+      mb.D1 = c.take<char>(rows * E * m.md.h1 * esz);
+      mb.D2 = c.take<char>(rows * E * m.md.h2 * esz);
+    }
+  }
   mb.e_row = c.take<float>((size_t)E * rows);
-  mb.aev_h = (m.precision == NNP_BF16_MLP) ? c.take<char>(rows * Dp * 2) : nullptr;
+  mb.aev_h = bf16 ? c.take<char>(rows * Dp * 2) : nullptr;
+  ws.aev_h = static_cast<uint16_t*>(mb.aev_h);
   return align_up(c.off, 256);
 }
 
@@ -1152,13 +1161,17 @@ size_t noalloc_carve(const Model& m, int n_atoms, char* base, Ws* ws, MlpBufs* m
   ws->dEdG = c.take<float>(rows * Dp);
   ws->atom_e = c.take<float>(rows);
   ws->f_pos = c.take<float4>(n);
-  mb->H1 = c.take<float>(rows * E * m.md.h1);
-  mb->D1 = c.take<float>(rows * E * m.md.h1);
-  mb->H2 = c.take<float>(rows * E * m.md.h2);
-  mb->D2 = c.take<float>(rows * E * m.md.h2);
-  mb->d3 = c.take<float>(rows * E * m.md.h3);
+  *mb = MlpBufs{};
+  if (!mlp_fused_supported(m.md)) {   // the fused kernel needs no activation buffers
+    mb->H1 = c.take<float>(rows * E * m.md.h1);
+    mb->D1 = c.take<float>(rows * E * m.md.h1);
+    mb->H2 = c.take<float>(rows * E * m.md.h2);
+    mb->D2 = c.take<float>(rows * E * m.md.h2);
+    mb->d3 = c.take<float>(rows * E * m.md.h3);
+  }
   mb->e_row = c.take<float>((size_t)E * rows);
   mb->aev_h = nullptr;
+  ws->aev_h = nullptr;
   return align_up(c.off, 256);
 }
 

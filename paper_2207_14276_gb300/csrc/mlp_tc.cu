@@ -424,18 +424,6 @@ __global__ void k_wait_probe(int* status, unsigned limit) {
   if (!ok) atomicOr(status, kStTimeout);
 }
 
-__global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
-                          const int* seg_start, int S, int Dp) {
-  const long long total = (long long)seg_start[S] * Dp / 4;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float4 v = reinterpret_cast<const float4*>(src)[i];
-    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-    uint2 w = make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
-    reinterpret_cast<uint2*>(dst)[i] = w;
-  }
-}
-
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -621,9 +609,6 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
   (void)mw; (void)mb;
   TcState* s = static_cast<TcState*>(state);
   if (!s) return NNP_ERR_ARG;
-  if (hook) hook->begin(11);
-  k_to_bf16<<<4 * 152, 256, 0, st>>>(ws.aev, static_cast<__nv_bfloat16*>(s->aev_h), ws.seg_start, md.S, md.Dp);
-  if (hook) hook->end();
   // plans 0-2 are the forward layers, 3-5 the backward to the input
   const size_t n_plans = energy_only ? 3 : s->plans.size();
   for (size_t i = 0; i < n_plans; ++i) {
@@ -646,7 +631,7 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
     }
     if (hook) hook->end();
   }
-  if (n_launch) *n_launch += 1 + (int)n_plans;
+  if (n_launch) *n_launch += (int)n_plans;
   return NNP_OK;
 }
 

@@ -110,6 +110,7 @@ struct Ws {
   int* nb_a;            // [n_in][cap_a]
   // AEV / gradient
   float* aev;           // [row_cap][Dp]
+  uint16_t* aev_h;      // [row_cap][Dp] BF16 copy (bit patterns) for the tensor-core path, or null
   float* dEdG;          // [row_cap][Dp]
   float* atom_e;        // [row_cap] per-row energy (mean over the ensemble, incl. shift)
   float4* f_pos;        // [n_in] forces on packed atoms
