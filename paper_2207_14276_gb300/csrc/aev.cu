@@ -45,6 +45,19 @@ __device__ __forceinline__ float fast_exp2(float x) {
   return y;
 }
 
+// hardware approximations (relative error of a few 1e-8): square root of the
+// squared distance and the sine, reciprocals of distances and of sin(theta)
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // x^e for an integer exponent; compile-time E > 0 unrolls, E == 0 reads e
 template <int E>
 __device__ __forceinline__ float ipow(float x, int e) {
@@ -81,16 +94,24 @@ __device__ __forceinline__ Geo pair_geo(const float4& xi, const float4& xj, cons
   }
   Geo g;
   g.dx = dx; g.dy = dy; g.dz = dz;
-  g.r = sqrtf(dx * dx + dy * dy + dz * dz);
+  g.r = sqrt_approx(dx * dx + dy * dy + dz * dz);
   return g;
 }
 
-// cosine cutoff (Eq. 3) and its derivative
-__device__ __forceinline__ float fcut(float r, float rc) {
-  return r < rc ? 0.5f * cospif(r / rc) + 0.5f : 0.f;
+// cosine cutoff (Eq. 3) and its derivative (inv_rc = 1 / rc)
+__device__ __forceinline__ float fcut(float r, float rc, float inv_rc) {
+  return r < rc ? 0.5f * cospif(r * inv_rc) + 0.5f : 0.f;
 }
-__device__ __forceinline__ float fcut_d(float r, float rc) {
-  return r < rc ? -0.5f * (kPi / rc) * sinpif(r / rc) : 0.f;
+__device__ __forceinline__ void fcut_both(float r, float rc, float inv_rc, float* f, float* df) {
+  if (r < rc) {
+    float sn, cs;
+    sincospif(r * inv_rc, &sn, &cs);
+    *f = 0.5f * cs + 0.5f;
+    *df = -0.5f * kPi * inv_rc * sn;
+  } else {
+    *f = 0.f;
+    *df = 0.f;
+  }
 }
 
 // sin(theta) with theta = acos(k cos_hat): sqrt(1 - k^2 cos_hat^2) written as
@@ -101,7 +122,7 @@ __device__ __forceinline__ float sin_theta(const float4& a, const float4& b, flo
   const float cy = a.z * b.x - a.x * b.z;
   const float cz = a.x * b.y - a.y * b.x;
   const float s2 = cx * cx + cy * cy + cz * cz;
-  return sqrtf(fmaf(1.f - k * k, chat * chat, s2));
+  return sqrt_approx(fmaf(1.f - k * k, chat * chat, s2));
 }
 
 // float4s of shared memory per warp of the backward kernel: neighbour geometry,
@@ -138,7 +159,7 @@ __device__ __forceinline__ void decode_pair(int t, int same, int c, int cu, floa
                                             int* j, int* k) {
   if (same) {
     const float b = 2.f * c - 1.f;
-    int jj = (int)((b - sqrtf(fmaxf(b * b - 8.f * t, 0.f))) * 0.5f);
+    int jj = (int)((b - sqrt_approx(fmaxf(b * b - 8.f * t, 0.f))) * 0.5f);
     jj = max(0, min(jj, c - 2));
     if ((jj + 1) * (2 * c - jj - 2) / 2 <= t) ++jj;
     else if (jj * (2 * c - jj - 1) / 2 > t) --jj;
@@ -162,7 +183,7 @@ __device__ __forceinline__ void decode_pair_diag(int t, int same, int c, int cu,
                                                  float inv_cu, int* j, int* k) {
   if (same) {
     const float b = 2.f * c - 1.f;
-    int g = (int)((b - sqrtf(fmaxf(b * b - 8.f * t, 0.f))) * 0.5f);
+    int g = (int)((b - sqrt_approx(fmaxf(b * b - 8.f * t, 0.f))) * 0.5f);
     g = max(0, min(g, c - 2));
     if ((g + 1) * (2 * c - g - 2) / 2 <= t) ++g;
     else if (g * (2 * c - g - 1) / 2 > t) --g;
@@ -205,7 +226,7 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32], unsigned lan
 }
 
 template <int ZETA>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 4)
 k_aev_fwd(Ws ws, AevConst ac) {
   extern __shared__ float4 sm4[];
   __shared__ ListHdr hdrs[kWarps];
@@ -227,15 +248,16 @@ k_aev_fwd(Ws ws, AevConst ac) {
   const int nr_tot = H.off_r[ac.S], na_tot = H.off_a[ac.S];
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
+  const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
   for (int t = lane; t < nr_tot; t += 32) {
     const Geo g = pair_geo(xi, ws.xyzq[lr[t]], d);
-    rad[t] = make_float2(g.r, fcut(g.r, ac.rc_r));
+    rad[t] = make_float2(g.r, fcut(g.r, ac.rc_r, inv_rc_r));
   }
   for (int t = lane; t < na_tot; t += 32) {
     const Geo g = pair_geo(xi, ws.xyzq[la[t]], d);
-    const float inv = 1.f / g.r;
+    const float inv = rcp_approx(g.r);
     angv[t] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
-    angf[t] = fcut(g.r, ac.rc_a);
+    angf[t] = fcut(g.r, ac.rc_a, inv_rc_a);
   }
   __syncwarp();
   // ---- radial, Eq. 4
@@ -303,7 +325,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
 }
 
 template <int ZETA, bool VIR>
-__global__ void __launch_bounds__(kWarps * 32, 3)
+__global__ void __launch_bounds__(kWarps * 32, 4)
 k_aev_bwd(Ws ws, AevConst ac) {
   constexpr bool want_virial = VIR;
   extern __shared__ float4 sm4[];
@@ -333,12 +355,15 @@ k_aev_bwd(Ws ws, AevConst ac) {
   const int na_tot = H.off_a[ac.S];
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
+  const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
   for (int f = lane; f < ac.S * kNR; f += 32) grad[f] = g_row[f];
   for (int t = lane; t < na_tot; t += 32) {
     const Geo g = pair_geo(xi, ws.xyzq[la[t]], d);
-    const float inv = 1.f / g.r;
+    const float inv = rcp_approx(g.r);
     angv[t] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
-    angf[t] = make_float4(fcut(g.r, ac.rc_a), fcut_d(g.r, ac.rc_a), inv, 0.f);
+    float fc, dfc;
+    fcut_both(g.r, ac.rc_a, inv_rc_a, &fc, &dfc);
+    angf[t] = make_float4(fc, dfc, inv, 0.f);
     accx[t] = 0.f;
     accy[t] = 0.f;
     accz[t] = 0.f;
@@ -355,7 +380,8 @@ k_aev_bwd(Ws ws, AevConst ac) {
     for (int t = H.off_r[s] + lane; t < H.off_r[s + 1]; t += 32) {
       const int j = lr[t];
       const Geo g = pair_geo(xi, ws.xyzq[j], d);
-      const float fc = fcut(g.r, ac.rc_r), dfc = fcut_d(g.r, ac.rc_r);
+      float fc, dfc;
+      fcut_both(g.r, ac.rc_r, inv_rc_r, &fc, &dfc);
       float dEdR = 0.f;
 #pragma unroll
       for (int r = 0; r < kNR; ++r) {
@@ -363,7 +389,7 @@ k_aev_bwd(Ws ws, AevConst ac) {
         const float e = fast_exp2(cr_ * x * x);
         dEdR = fmaf(gs[r], e * fmaf(-2.f * ac.eta_r * x, fc, dfc), dEdR);
       }
-      const float sc = dEdR / g.r;
+      const float sc = dEdR * rcp_approx(g.r);
       const float gx = sc * g.dx, gy = sc * g.dy, gz = sc * g.dz;
       atomicAdd(&ws.f_pos[j], make_float4(-gx, -gy, -gz, 0.f));
       fi[0] += gx; fi[1] += gy; fi[2] += gz;
@@ -436,28 +462,40 @@ k_aev_bwd(Ws ws, AevConst ac) {
         const float chat = vj.x * vk.x + vj.y * vk.y + vj.z * vk.z;
         const float c = ac.cos_scale * chat;
         const float sn = fmaxf(sin_theta(vj, vk, chat, ac.cos_scale), 1e-6f);
-        const float c_over_s = c * __frcp_rn(sn);
+        const float c_over_s = c * rcp_approx(sn);
         const float rb = 0.5f * (vj.w + vk.w);
-        float A[kNA], dA[kNA];
-#pragma unroll
-        for (int a = 0; a < kNA; ++a) {
-          const float x = rb - ac.shf_a[a];
-          A[a] = fast_exp2(ca_ * x * x);
-          dA[a] = m2eta * x * A[a];
-        }
-        float tc = 0.f, tR = 0.f, tf = 0.f;
+        // contract the block's dE/dG over the 8 angle sections first:
+        //   F_a = sum_z g[a][z] B_z,  dF_a = sum_z g[a][z] dB_z/dc
+        float F[kNA] = {0.f, 0.f, 0.f, 0.f}, dF[kNA] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int z = 0; z < kNZ; ++z) {
           const float base = fmaf(sn, ac.sin_z[z], fmaf(c, ac.cos_z[z], 1.f));
-          const float B1 = ipow<(ZETA > 0 ? ZETA - 1 : 0)>(base, ac.zeta - 1);
-          const float B = B1 * base;
+          float B, B1;
+          if constexpr (ZETA == 32) {
+            // base >= 1 + cos(15 pi / 16) > 0: base^31 = base^32 / base
+            const float p2 = base * base, p4 = p2 * p2, p8 = p4 * p4, p16 = p8 * p8;
+            B = p16 * p16;
+            B1 = B * rcp_approx(base);
+          } else {
+            B1 = ipow<0>(base, ac.zeta - 1);
+            B = B1 * base;
+          }
           const float dB = B1 * fmaf(-ac.sin_z[z], c_over_s, ac.cos_z[z]);
           const float4 gz = gblk[z];
-          const float P = fmaf(gz.x, A[0], fmaf(gz.y, A[1], fmaf(gz.z, A[2], gz.w * A[3])));
-          const float Q = fmaf(gz.x, dA[0], fmaf(gz.y, dA[1], fmaf(gz.z, dA[2], gz.w * dA[3])));
-          tc = fmaf(dB, P, tc);
-          tR = fmaf(B, Q, tR);
-          tf = fmaf(B, P, tf);
+          F[0] = fmaf(gz.x, B, F[0]); F[1] = fmaf(gz.y, B, F[1]);
+          F[2] = fmaf(gz.z, B, F[2]); F[3] = fmaf(gz.w, B, F[3]);
+          dF[0] = fmaf(gz.x, dB, dF[0]); dF[1] = fmaf(gz.y, dB, dF[1]);
+          dF[2] = fmaf(gz.z, dB, dF[2]); dF[3] = fmaf(gz.w, dB, dF[3]);
+        }
+        float tc = 0.f, tR = 0.f, tf = 0.f;
+#pragma unroll
+        for (int a = 0; a < kNA; ++a) {
+          const float x = rb - ac.shf_a[a];
+          const float A = fast_exp2(ca_ * x * x);
+          const float AF = A * F[a];
+          tf += AF;
+          tR = fmaf(m2eta * x, AF, tR);
+          tc = fmaf(A, dF[a], tc);
         }
         const float fjk = fj4.x * fk4.x;
         tc *= ac.ang_pre * (float)ac.zeta * fjk;  // dE/dc, c = cos_scale * cos_hat
