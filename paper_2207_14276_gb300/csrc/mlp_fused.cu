@@ -163,7 +163,7 @@ __device__ __forceinline__ void block_gemm(float (&acc)[8][N / 32], const float*
     const float* arow = AG ? As + buf * kRows * (KS + 4) + (w * 8) * (KS + 4)
                            : A + (size_t)(w * 8) * lda + sl * KS;
     const int lds = AG ? KS + 4 : lda;
-#pragma unroll 2
+#pragma unroll
     for (int kk = 0; kk < KS; kk += 4) {
       float4 a[8];
 #pragma unroll
