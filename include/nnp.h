@@ -287,6 +287,30 @@ int nnp_aev_dim(const nnp_handle* h);
 /* Number of kernels the last compute call enqueued (for launch accounting). */
 int nnp_last_launch_count(const nnp_handle* h);
 
+/* Persistent neighbour lists with a Verlet skin (paper Sec. "Neighbour lists":
+ * the lists are rebuilt only when atoms have moved far enough, as in the MD
+ * engine's multiple-time-step loop).
+ *
+ * nnp_set_skin(h, skin): skin in [0, 3] A; 0 (the default) rebuilds the cell
+ * and neighbour lists on every call.  With skin > 0 the lists of energy/force
+ * calls on this handle (nnp_energy_forces, nnp_energy_forces_batch and the host
+ * entry point) are built with cutoffs Rc + skin and kept: a later call reuses
+ * them when its batch has the same layout (number of systems, atom counts,
+ * species and mask pointers, boxes) and no ML atom has moved more than skin/2
+ * (minimum image) since the build; the check runs on the device, so calls stay
+ * asynchronous.  The AEV kernels drop list entries beyond the true cutoffs, so
+ * results equal those of rebuilt lists up to FP32 summation order.  The caller
+ * must not change the contents of the species or mask arrays while the lists
+ * persist (pass other arrays, or call nnp_set_skin again, to force a rebuild).
+ * A force VJP call on the handle rebuilds lists at the cutoffs; the next energy
+ * call rebuilds the skin lists.  Returns NNP_OK or NNP_ERR_ARG.
+ *
+ * nnp_list_stats(h, stream, &builds, &calls): synchronises `stream`; builds =
+ * list builds on the device since the skin was set (or the arena last grew),
+ * calls = energy/force calls made with a skin. */
+int nnp_set_skin(nnp_handle* h, float skin);
+int nnp_list_stats(nnp_handle* h, void* stream, int64_t* builds, int64_t* calls);
+
 /* Per-stage timing with CUDA events recorded on the caller's stream around the
  * kernels of each stage (prep, neighbors, aev_fwd, mlp_l1 .. mlp_b1, aev_bwd,
  * finalize, mlp_cvt).  nnp_profile(h, 1) enables recording for later calls;

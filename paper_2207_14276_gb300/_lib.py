@@ -40,7 +40,7 @@ EXPORTS = (
     "nnp_profile", "nnp_profile_read", "nnp_profile_stage_name", "nnp_energy_forces_noalloc",
     "nnp_server_create", "nnp_server_destroy", "nnp_server_register", "nnp_server_submit",
     "nnp_server_poll", "nnp_server_stats", "nnp_force_vjp_batch", "nnp_force_vjp",
-    "nnp_n_weights", "nnp_debug_wait_probe",
+    "nnp_n_weights", "nnp_debug_wait_probe", "nnp_set_skin", "nnp_list_stats",
 )
 
 
@@ -130,6 +130,8 @@ def lib():
     L.nnp_n_weights.argtypes = [P]
     L.nnp_n_weights.restype = i64
     L.nnp_debug_wait_probe.argtypes = [P, ctypes.c_uint, P]
+    L.nnp_set_skin.argtypes = [P, ctypes.c_float]
+    L.nnp_list_stats.argtypes = [P, P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.nnp_profile.argtypes = [P, i]
     L.nnp_profile_read.argtypes = [P, i, P, P, i, P]
     L.nnp_profile_stage_name.restype = ctypes.c_char_p

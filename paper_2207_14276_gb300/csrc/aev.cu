@@ -98,6 +98,53 @@ __device__ __forceinline__ Geo pair_geo(const float4& xi, const float4& xj, cons
   return g;
 }
 
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// One lane per entry of a species-sorted neighbour list with species blocks
+// off[0..S]: visit(slot, j, geometry) stages entry j at slot.  With `compact`
+// (lists built with a skin), entries at R >= rc are dropped, the kept ones keep
+// their order, and off[] is rewritten to the kept blocks.
+template <class Visit>
+__device__ __forceinline__ void stage_list(int* off, int S, const int* lst, bool compact, float rc,
+                                           const float4& xi, const SysDev& d, const float4* xyzq,
+                                           unsigned lane, Visit visit) {
+  if (!compact) {
+    const int n = off[S];
+    for (int t = (int)lane; t < n; t += 32) {
+      const int j = lst[t];
+      visit(t, j, pair_geo(xi, xyzq[j], d));
+    }
+    return;
+  }
+  int w_off = 0;
+  for (int s = 0; s < S; ++s) {
+    const int beg = off[s], end = off[s + 1], start = w_off;
+    for (int t0 = beg; t0 < end; t0 += 32) {
+      const int t = t0 + (int)lane;
+      bool keep = false;
+      Geo g{0.f, 0.f, 0.f, 0.f};
+      int j = 0;
+      if (t < end) {
+        j = lst[t];
+        g = pair_geo(xi, xyzq[j], d);
+        keep = g.r < rc;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) visit(w_off + __popc(bal & lanemask_lt()), j, g);
+      w_off += __popc(bal);
+    }
+    __syncwarp();   // every lane has read off[s] and off[s + 1]
+    if (lane == 0) off[s] = start;
+  }
+  __syncwarp();
+  if (lane == 0) off[S] = w_off;
+  __syncwarp();
+}
+
 // cosine cutoff (Eq. 3) and its derivative (inv_rc = 1 / rc)
 __device__ __forceinline__ float fcut(float r, float rc, float inv_rc) {
   return r < rc ? 0.5f * cospif(r * inv_rc) + 0.5f : 0.f;
@@ -245,20 +292,20 @@ k_aev_fwd(Ws ws, AevConst ac) {
   float* G = ws.aev + row;
   uint16_t* Gh = ws.aev_h ? ws.aev_h + row : nullptr;
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
-  const int nr_tot = H.off_r[ac.S], na_tot = H.off_a[ac.S];
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
   const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
-  for (int t = lane; t < nr_tot; t += 32) {
-    const Geo g = pair_geo(xi, ws.xyzq[lr[t]], d);
-    rad[t] = make_float2(g.r, fcut(g.r, ac.rc_r, inv_rc_r));
-  }
-  for (int t = lane; t < na_tot; t += 32) {
-    const Geo g = pair_geo(xi, ws.xyzq[la[t]], d);
-    const float inv = rcp_approx(g.r);
-    angv[t] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
-    angf[t] = fcut(g.r, ac.rc_a, inv_rc_a);
-  }
+  const bool compact = ac.skin > 0.f;
+  stage_list(H.off_r, ac.S, lr, compact, ac.rc_r, xi, d, ws.xyzq, lane,
+             [&](int slot, int, const Geo& g) {
+               rad[slot] = make_float2(g.r, fcut(g.r, ac.rc_r, inv_rc_r));
+             });
+  stage_list(H.off_a, ac.S, la, compact, ac.rc_a, xi, d, ws.xyzq, lane,
+             [&](int slot, int, const Geo& g) {
+               const float inv = rcp_approx(g.r);
+               angv[slot] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
+               angf[slot] = fcut(g.r, ac.rc_a, inv_rc_a);
+             });
   __syncwarp();
   // ---- radial, Eq. 4
   const float cr_ = -ac.eta_r * kLog2e;
@@ -352,22 +399,23 @@ k_aev_bwd(Ws ws, AevConst ac) {
   const SysDev& d = ws.sys[ws.pos_sys[p]];
   const float* g_row = ws.dEdG + (size_t)ws.pos_slot[p] * ac.Dp;
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
-  const int na_tot = H.off_a[ac.S];
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
   const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
   for (int f = lane; f < ac.S * kNR; f += 32) grad[f] = g_row[f];
-  for (int t = lane; t < na_tot; t += 32) {
-    const Geo g = pair_geo(xi, ws.xyzq[la[t]], d);
-    const float inv = rcp_approx(g.r);
-    angv[t] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
-    float fc, dfc;
-    fcut_both(g.r, ac.rc_a, inv_rc_a, &fc, &dfc);
-    angf[t] = make_float4(fc, dfc, inv, 0.f);
-    accx[t] = 0.f;
-    accy[t] = 0.f;
-    accz[t] = 0.f;
-  }
+  // angular neighbours: unit vector and R, (f_c, f_c', 1/R, packed index)
+  stage_list(H.off_a, ac.S, la, ac.skin > 0.f, ac.rc_a, xi, d, ws.xyzq, lane,
+             [&](int slot, int j, const Geo& g) {
+               const float inv = rcp_approx(g.r);
+               angv[slot] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
+               float fc, dfc;
+               fcut_both(g.r, ac.rc_a, inv_rc_a, &fc, &dfc);
+               angf[slot] = make_float4(fc, dfc, inv, __int_as_float(j));
+               accx[slot] = 0.f;
+               accy[slot] = 0.f;
+               accz[slot] = 0.f;
+             });
+  const int na_tot = H.off_a[ac.S];
   __syncwarp();
   float fi[3] = {0.f, 0.f, 0.f};
   float vir[9];
@@ -380,6 +428,7 @@ k_aev_bwd(Ws ws, AevConst ac) {
     for (int t = H.off_r[s] + lane; t < H.off_r[s + 1]; t += 32) {
       const int j = lr[t];
       const Geo g = pair_geo(xi, ws.xyzq[j], d);
+      if (g.r >= ac.rc_r) continue;   // inside the list's skin only
       float fc, dfc;
       fcut_both(g.r, ac.rc_r, inv_rc_r, &fc, &dfc);
       float dEdR = 0.f;
@@ -517,7 +566,7 @@ k_aev_bwd(Ws ws, AevConst ac) {
   for (int t = lane; t < na_tot; t += 32) {
     const float4 a = make_float4(accx[t], accy[t], accz[t], 0.f);
     const float4 v = angv[t];
-    atomicAdd(&ws.f_pos[la[t]], make_float4(-a.x, -a.y, -a.z, 0.f));
+    atomicAdd(&ws.f_pos[__float_as_int(angf[t].w)], make_float4(-a.x, -a.y, -a.z, 0.f));
     fi[0] += a.x; fi[1] += a.y; fi[2] += a.z;
     if (want_virial) {
       const float ux = v.x * v.w, uy = v.y * v.w, uz = v.z * v.w;
@@ -572,18 +621,6 @@ void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
     if (want_virial) k_aev_bwd<0, true><<<grid, kWarps * 32, sm, st>>>(ws, ac);
     else k_aev_bwd<0, false><<<grid, kWarps * 32, sm, st>>>(ws, ac);
   }
-}
-
-cudaError_t aev_set_smem_limits(const Ws& ws) {
-  const int f = (int)aev_fwd_smem(ws), b = (int)aev_bwd_smem(ws);
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_aev_fwd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, f))) return e;
-  if ((e = cudaFuncSetAttribute(k_aev_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, f))) return e;
-  const void* bwd[4] = {(const void*)k_aev_bwd<32, false>, (const void*)k_aev_bwd<32, true>,
-                        (const void*)k_aev_bwd<0, false>, (const void*)k_aev_bwd<0, true>};
-  for (const void* fn : bwd)
-    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-  return cudaSuccess;
 }
 
 // raise (never lower) the dynamic shared-memory limit of the AEV kernels to what

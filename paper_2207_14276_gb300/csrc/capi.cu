@@ -98,6 +98,11 @@ struct nnp_handle {
   std::string gsig;       // signature of the captured call
   std::string last_sig;   // signature of the previous eager call
   int last_launches_graph = 0;
+  // persistent neighbour lists with a Verlet skin (0: rebuilt on every call)
+  float skin = 0.f;
+  bool lists_valid = false;   // the lists in the arena belong to list_sig's batch layout
+  std::string list_sig;
+  long long skin_calls = 0;
   // optional per-stage CUDA-event timing
   bool profile = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
@@ -297,6 +302,16 @@ size_t carve(nnp_handle* h, char* base) {
   ws.dEdG = c.take<float>(rows * Dp);
   ws.atom_e = c.take<float>(rows);
   ws.f_pos = c.take<float4>(n);
+  if (h->skin > 0.f) {
+    ws.skin_state = c.take<int>(4);
+    ws.ref = c.take<float4>(n);
+    ws.in_pos = c.take<int>(n);
+  } else {
+    ws.skin_state = nullptr;
+    ws.ref = nullptr;
+    ws.in_pos = nullptr;
+  }
+  ws.half_skin = 0.5f * h->skin;
   const bool bf16 = (m.precision == NNP_BF16_MLP);
   const size_t esz = bf16 ? 2 : 4;
   MlpBufs& mb = h->mb;
@@ -353,8 +368,10 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
   CU_TRY(cudaMemset(p, 0, bytes));
   h->arena = p;
   h->arena_bytes = bytes;
+  h->lists_valid = false;
   carve(h, static_cast<char*>(p));
-  CU_TRY(aev_set_smem_limits(h->ws));
+  // raise-only: other handles of the process may need larger limits
+  CU_TRY(aev_ensure_smem(h->ws));
   CU_TRY(mlp_fused_ensure_smem(h->model->md));
   if (h->model->precision == NNP_BF16_MLP) {
     int rc = mlp_tc_prepare(h->model->md, h->model->mw, h->mb, h->ws.row_cap, h->ws.aev,
@@ -441,22 +458,48 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
       if (sy[b].virial) CU_TRY(cudaMemsetAsync(sy[b].virial, 0, 9 * sizeof(double), st));
       launches += 1 + (sy[b].virial ? 1 : 0);
     }
+  // persistent lists: the displacement check decides on the device whether this
+  // call rebuilds them (a new batch layout or a capacity change always does)
+  AevConst ac = m.ac;
+  ac.skin = ws.skin_state ? h->skin : 0.f;
+  // a launch that fails is reported with the name of its stage
+  auto chk = [&](const char* name) -> int {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? NNP_OK : fail(NNP_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
+  };
+  if (ws.skin_state) {
+    const bool forced = !h->lists_valid;
+    CU_TRY(cudaMemsetAsync(ws.skin_state, 0, sizeof(int), st));
+    CU_TRY(cudaMemsetAsync(ws.skin_state + 1, forced ? 1 : 0, sizeof(int), st));
+    launches += 2;
+    if (!forced)
+      for (const auto& bp : chunks) {
+        int n_chunk = 0;
+        for (int k = 0; k < bp.n_sys; ++k) n_chunk += bp.sys[k].n_in;
+        if (n_chunk > 0) { launch_skin_check(ws, bp, n_chunk, st); ++launches; }
+      }
+    if ((rc = chk("displacement check"))) return rc;
+  }
   for (const auto& bp : chunks) { launch_init_chunk(ws, bp, st); ++launches; }
   for (const auto& bp : chunks) {
     int n_chunk = 0;
     for (int k = 0; k < bp.n_sys; ++k) n_chunk += bp.sys[k].n_in;
     if (n_chunk > 0) { launch_prep_atoms(ws, bp, n_chunk, m.ac.S, st); ++launches; }
   }
+  if ((rc = chk("init/prep"))) return rc;
   if (n_in > 0) {
     {
       StageTimer t(h, st, 0);
-      launch_setup(ws, m.ac, st);
+      launch_setup(ws, ac, st);
       launch_bin(ws, n_in, st);
       launch_scan(ws, st);
       launch_scatter(ws, n_in, st);
     }
-    { StageTimer t(h, st, 1); launch_neighbors(ws, n_in, m.ac, st); }
-    { StageTimer t(h, st, 2); launch_aev_fwd(ws, n_in, m.ac, st); }
+    if ((rc = chk("cell lists"))) return rc;
+    { StageTimer t(h, st, 1); launch_neighbors(ws, n_in, ac, st); }
+    if ((rc = chk("neighbors"))) return rc;
+    { StageTimer t(h, st, 2); launch_aev_fwd(ws, n_in, ac, st); }
+    if ((rc = chk("aev_fwd"))) return rc;
     launches += 6;
     // energy only when no system asks for forces or a virial
     bool energy_only = true;
@@ -468,10 +511,12 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     } else {
       launch_mlp_fp32(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, energy_only);
     }
+    if ((rc = chk("mlp"))) return rc;
     if (!energy_only) {
       StageTimer t(h, st, 9);
-      launch_aev_bwd(ws, n_in, m.ac, any_virial ? 1 : 0, st);
+      launch_aev_bwd(ws, n_in, ac, any_virial ? 1 : 0, st);
     }
+    if ((rc = chk("aev_bwd"))) return rc;
     {
       StageTimer t(h, st, 10);
       launch_finalize_e(ws, n_in, h->mb.e_row, m.md.E, ws.row_cap, m.ebias, st);
@@ -522,6 +567,25 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
   }
   bool any_virial = false;
   for (int b = 0; b < n_sys; ++b) any_virial |= (sy[b].virial != nullptr);
+  if (ws.skin_state) {
+    // the lists persist while the batch layout (sizes, species and mask arrays,
+    // boxes) stays the same; coordinates and outputs may change between calls
+    std::string topo;
+    auto put = [&](const void* p, size_t nb) { topo.append(static_cast<const char*>(p), nb); };
+    put(&n_sys, sizeof(n_sys));
+    for (int b = 0; b < n_sys; ++b) {
+      put(&sy[b].n_atoms, sizeof(sy[b].n_atoms));
+      put(&sy[b].species, sizeof(sy[b].species));
+      put(&sy[b].mask, sizeof(sy[b].mask));
+      put(&sy[b].periodic, sizeof(sy[b].periodic));
+      put(sy[b].box, sizeof(sy[b].box));
+    }
+    if (topo != h->list_sig) {
+      h->lists_valid = false;
+      h->list_sig = topo;
+    }
+    ++h->skin_calls;
+  }
   // a call identical to the previous one (descriptors, sizes, arena) is replayed
   // from a CUDA graph: captured on its second occurrence, replayed afterwards
   if (!h->profile) {
@@ -535,11 +599,15 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
     put(&ws.cap_a, sizeof(int));
     put(&ws.row_cap, sizeof(int));
     put(&ws.cell_cap, sizeof(int));
+    const int skin_mode = ws.skin_state ? (h->lists_valid ? 1 : 2) : 0;
+    put(&skin_mode, sizeof(skin_mode));
+    put(&h->skin, sizeof(h->skin));
     for (const auto& bp : chunks) put(&bp, sizeof(BatchParams));
     if (h->gexec && sig == h->gsig) {
       CU_TRY(cudaGraphLaunch(h->gexec, st));
       h->last_launches = h->last_launches_graph;
       h->last_n_in = n_in;
+      h->lists_valid = true;
       return NNP_OK;
     }
     if (sig == h->last_sig) {
@@ -569,6 +637,7 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
       CU_TRY(cudaGraphLaunch(h->gexec, st));
       h->last_launches = launches;
       h->last_n_in = n_in;
+      h->lists_valid = true;
       return NNP_OK;
     }
     h->last_sig = sig;
@@ -578,6 +647,7 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
   if (rc) return rc;
   h->last_launches = launches;
   h->last_n_in = n_in;
+  h->lists_valid = true;
   CU_TRY(cudaGetLastError());
   return NNP_OK;
 }
@@ -938,6 +1008,15 @@ extern "C" int nnp_force_vjp_batch(nnp_handle* h, int n_sys, const nnp_vjp_syste
   Ws& ws = h->ws;
   ws.n_sys = n_sys;
   ws.n_in = n_in;
+  // the force VJP builds its own lists at the cutoffs in the shared buffers:
+  // persistent lists of energy calls are rebuilt on the next such call
+  struct SkinOff {
+    Ws& w;
+    int* saved;
+    explicit SkinOff(Ws& w_) : w(w_), saved(w_.skin_state) { w.skin_state = nullptr; }
+    ~SkinOff() { w.skin_state = saved; }
+  } skin_off(ws);
+  h->lists_valid = false;
   int in_base = 0;
   std::vector<BatchParams> chunks;
   for (int b0 = 0; b0 < n_sys; b0 += kMaxBatchParam) {
@@ -1014,6 +1093,31 @@ extern "C" int64_t nnp_n_weights(const nnp_handle* h) {
 
 int nnp_aev_dim(const nnp_handle* h) { return h ? h->model->ac.D : -1; }
 int nnp_last_launch_count(const nnp_handle* h) { return h ? h->last_launches : -1; }
+
+int nnp_set_skin(nnp_handle* h, float skin) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  if (!(skin >= 0.f) || skin > 3.f) return fail(NNP_ERR_ARG, "skin must be in [0, 3] A");
+  if (skin != h->skin) {
+    h->skin = skin;
+    h->dirty = true;          // the arena gains or drops the reference coordinates
+    h->lists_valid = false;
+  }
+  return NNP_OK;
+}
+
+int nnp_list_stats(nnp_handle* h, void* stream, int64_t* builds, int64_t* calls) {
+  g_err.clear();
+  if (!h || !builds || !calls) return fail(NNP_ERR_ARG, "null argument");
+  *builds = 0;
+  *calls = h->skin_calls;
+  if (!h->arena || !h->ws.skin_state) return NNP_OK;
+  CU_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int st[4];
+  CU_TRY(cudaMemcpy(st, h->ws.skin_state, sizeof(st), cudaMemcpyDeviceToHost));
+  *builds = st[2];
+  return NNP_OK;
+}
 
 int nnp_debug_wait_probe(nnp_handle* h, unsigned limit, void* stream) {
   g_err.clear();

@@ -10,6 +10,11 @@ namespace {
 __global__ void k_finalize(Ws ws, const float* e_row, int E, int e_row_net,
                            const double* ebias) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0 && ws.skin_state && lists_rebuild(ws)) {
+    // the lists built in this call serve later calls unless they overflowed
+    ws.skin_state[2] += 1;
+    ws.skin_state[3] = (ws.status[0] & (kStCapacity | kStCells)) ? 0 : 1;
+  }
   const unsigned lane = threadIdx.x & 31;
   const int total = ws.totals[0];
   const bool live = p < total;

@@ -40,6 +40,15 @@ __device__ __forceinline__ int find_sys(const BatchParams& bp, int idx) {
 __global__ void k_init(Ws ws, BatchParams bp, int zero_all, int n_in) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
+  const bool rebuild = lists_rebuild(ws);
+  if (!rebuild) {
+    // persistent lists: the grids and counts of the last build stay; only this
+    // call's pointers are new, and the forces start again from zero
+    if (tid < bp.n_sys) ws.sys[bp.sys_base + tid].in = bp.sys[tid];
+    if (zero_all)
+      for (int i = tid; i < n_in; i += stride) ws.f_pos[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
   if (tid < bp.n_sys) {
     SysDev d;
     d.in = bp.sys[tid];
@@ -112,6 +121,8 @@ __global__ void k_prep(Ws ws, BatchParams bp, int n_chunk, int S) {
     }
     ws.in_sys[gi] = ml ? b : -1;
   }
+  if (!lists_rebuild(ws)) return;   // persistent lists: counts and boxes of the last build
+  if (live && ws.in_pos) ws.in_pos[gi] = -1;
   // per-system ML atom counts and bounding boxes (warp-aggregated)
   const unsigned act = __ballot_sync(0xffffffffu, live && ml);
   if (live && ml) {
@@ -162,7 +173,8 @@ __device__ int block_exclusive_scan(int v, int* total) {
 }
 
 __global__ void k_setup(Ws ws, AevConst ac) {
-  const float rc = fmaxf(ac.rc_r, ac.rc_a);
+  if (!lists_rebuild(ws)) return;
+  const float rc = fmaxf(ac.rc_r, ac.rc_a) + ac.skin;
   int run_atoms = 0, run_cells = 0;
   for (int b0 = 0; b0 < ws.n_sys; b0 += blockDim.x) {
     const int b = b0 + threadIdx.x;
@@ -238,6 +250,7 @@ __device__ __forceinline__ int cell_coord(float x, const SysDev& d, int c) {
 }
 
 __global__ void k_bin(Ws ws, int n_in) {
+  if (!lists_rebuild(ws)) return;
   const int gi = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lane = threadIdx.x & 31;
   int b = -1;
@@ -268,6 +281,7 @@ __global__ void k_bin(Ws ws, int n_in) {
 // single-block exclusive scan of the cell counts (1024 threads)
 __global__ void k_scan(Ws ws) {
   __shared__ int warp_sums[32];
+  if (!lists_rebuild(ws)) return;
   const int T = ws.totals[1];
   const int nt = blockDim.x;
   const int per = (T + nt - 1) / nt;
@@ -302,6 +316,17 @@ __global__ void k_scan(Ws ws) {
 __global__ void k_scatter(Ws ws, int n_in) {
   const int gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= n_in) return;
+  if (!lists_rebuild(ws)) {
+    // persistent lists: new coordinates into the packed order of the last build
+    const int pos = ws.in_pos[gi];
+    if (pos < 0) return;
+    const SysDev& d = ws.sys[ws.pos_sys[pos]];
+    const int local = gi - d.in.in_base;
+    ws.xyzq[pos] = make_float4(wrap_coord(d.in.coords[3 * local + 0], d, 0),
+                               wrap_coord(d.in.coords[3 * local + 1], d, 1),
+                               wrap_coord(d.in.coords[3 * local + 2], d, 2), ws.xyzq[pos].w);
+    return;
+  }
   const int b = ws.in_sys[gi];
   if (b < 0) return;
   const SysDev& d = ws.sys[b];
@@ -318,6 +343,39 @@ __global__ void k_scatter(Ws ws, int n_in) {
   ws.pos_sys[pos] = b;
   ws.pos_cell[pos] = gcell - d.cell_base;
   ws.slot_pos[slot] = pos;
+  if (ws.in_pos) {   // the reference the displacement check of later calls compares with
+    ws.in_pos[gi] = pos;
+    ws.ref[gi] = make_float4(d.in.coords[3 * local + 0], d.in.coords[3 * local + 1],
+                             d.in.coords[3 * local + 2], 0.f);
+  }
+}
+
+// Largest displacement of an atom of the last build's lists since that build
+// (minimum image in periodic directions), as float bits into skin_state[0]
+// (positive floats order like their bit patterns).
+__global__ void k_skin_check(Ws ws, BatchParams bp, int n_chunk) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  float d2 = 0.f;
+  if (t < n_chunk) {
+    const int k = find_sys(bp, t);
+    const SysIn& si = bp.sys[k];
+    const int local = t - (si.in_base - bp.sys[0].in_base);
+    const int gi = si.in_base + local;
+    if (ws.in_pos[gi] >= 0) {
+      const float4 r0 = ws.ref[gi];
+      float d[3] = {si.coords[3 * local + 0] - r0.x, si.coords[3 * local + 1] - r0.y,
+                    si.coords[3 * local + 2] - r0.z};
+      if (si.periodic)
+        for (int c = 0; c < 3; ++c) {
+          const float n = rintf(d[c] / si.box_hi[c]);
+          d[c] = fmaf(-n, si.box_lo[c], fmaf(-n, si.box_hi[c], d[c]));
+        }
+      d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (!(d2 == d2)) d2 = 3.0e38f;   // a non-finite coordinate forces a rebuild
+    }
+  }
+  const int key = (int)__reduce_max_sync(0xffffffffu, __float_as_uint(sqrtf(d2)));
+  if ((threadIdx.x & 31) == 0 && key > 0) atomicMax(ws.skin_state, key);
 }
 
 // Neighbour lists of centre p by one warp, candidates read from global memory
@@ -335,7 +393,8 @@ __device__ void centre_lists_global(const Ws& ws, const AevConst& ac, int p, int
   const int lc = ws.pos_cell[p];
   const int nc0 = d.nc[0], nc1 = d.nc[1], nc2 = d.nc[2];
   const int c2 = lc % nc2, c1 = (lc / nc2) % nc1, c0 = lc / (nc1 * nc2);
-  const float rr2 = ac.rc_r * ac.rc_r, ra2 = ac.rc_a * ac.rc_a;
+  const float rl = ac.rc_r + ac.skin, al = ac.rc_a + ac.skin;   // list cutoffs
+  const float rr2 = rl * rl, ra2 = al * al;
   const float Lh0 = d.in.box_hi[0], Lh1 = d.in.box_hi[1], Lh2 = d.in.box_hi[2];
   const float Ll0 = d.in.box_lo[0], Ll1 = d.in.box_lo[1], Ll2 = d.in.box_lo[2];
   const float iL0 = per ? 1.f / Lh0 : 0.f, iL1 = per ? 1.f / Lh1 : 0.f, iL2 = per ? 1.f / Lh2 : 0.f;
@@ -476,7 +535,8 @@ __device__ __forceinline__ void centre_lists_staged(const Ws& ws, const AevConst
                                                     const SysDev& d) {
   const unsigned lane = threadIdx.x & 31;
   const float4 xi = ws.xyzq[p];
-  const float rr2 = ac.rc_r * ac.rc_r, ra2 = ac.rc_a * ac.rc_a;
+  const float rl = ac.rc_r + ac.skin, al = ac.rc_a + ac.skin;   // list cutoffs
+  const float rr2 = rl * rl, ra2 = al * al;
   const bool any_mi = min_img[0] | min_img[1] | min_img[2];
   uint16_t* hdr = ws.nb_cnt + (size_t)p * 16;
   int* out_r = ws.nb_r + (size_t)p * ws.cap_r;
@@ -553,6 +613,7 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbors(Ws ws, AevConst ac) {
   __shared__ int min_img[3];
   const int tid = threadIdx.x, w = tid >> 5;
   const unsigned lane = tid & 31;
+  if (!lists_rebuild(ws)) return;
   const int n_cells = ws.totals[1];
   for (int gc = blockIdx.x; gc < n_cells; gc += gridDim.x) {
     const int cbeg = ws.cell_start[gc], cend = ws.cell_start[gc + 1];
@@ -703,6 +764,11 @@ void launch_scan(const Ws& ws, cudaStream_t st) { k_scan<<<1, 1024, 0, st>>>(ws)
 void launch_scatter(const Ws& ws, int n_in, cudaStream_t st) {
   if (n_in <= 0) return;
   k_scatter<<<(n_in + 255) / 256, 256, 0, st>>>(ws, n_in);
+}
+
+void launch_skin_check(const Ws& ws, const BatchParams& bp, int n_in_chunk, cudaStream_t st) {
+  if (n_in_chunk <= 0 || !ws.skin_state) return;
+  k_skin_check<<<(n_in_chunk + 255) / 256, 256, 0, st>>>(ws, bp, n_in_chunk);
 }
 
 void launch_neighbors(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st) {

@@ -37,6 +37,7 @@ struct AevConst {
   float cos_scale;
   int zeta;         // integer exponent
   float ang_pre;    // 2^(1-zeta)
+  float skin;       // Verlet skin of the neighbour lists (0: lists at the cutoffs)
 };
 
 // per-system descriptor as passed in kernel parameters (host-filled part)
@@ -114,7 +115,19 @@ struct Ws {
   float* dEdG;          // [row_cap][Dp]
   float* atom_e;        // [row_cap] per-row energy (mean over the ensemble, incl. shift)
   float4* f_pos;        // [n_in] forces on packed atoms
+  // persistent neighbour lists with a skin (null skin_state: rebuilt every call)
+  int* skin_state;      // [4]: max displacement (float bits), forced rebuild, builds, lists valid
+  float half_skin;      // rebuild when an atom moved farther than this since the build
+  float4* ref;          // [n_in] input coordinates at the last build
+  int* in_pos;          // [n_in] packed position of an input atom at the last build (-1: none)
 };
+
+// whether this call rebuilds the cell lists and neighbour lists
+__device__ __forceinline__ bool lists_rebuild(const Ws& ws) {
+  if (!ws.skin_state) return true;
+  const volatile int* k = ws.skin_state;
+  return k[1] != 0 || k[3] == 0 || __int_as_float(k[0]) > ws.half_skin;
+}
 
 // ---- launchers (nl.cu)
 void launch_init_chunk(const Ws& ws, const BatchParams& bp, cudaStream_t st);
@@ -125,11 +138,11 @@ void launch_bin(const Ws& ws, int n_in, cudaStream_t st);
 void launch_scan(const Ws& ws, cudaStream_t st);
 void launch_scatter(const Ws& ws, int n_in, cudaStream_t st);
 void launch_neighbors(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st);
+void launch_skin_check(const Ws& ws, const BatchParams& bp, int n_in_chunk, cudaStream_t st);
 // ---- aev.cu
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st);
 void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
                     cudaStream_t st);
-cudaError_t aev_set_smem_limits(const Ws& ws);
 cudaError_t aev_ensure_smem(const Ws& ws);
 size_t aev_fwd_smem(const Ws& ws);
 size_t aev_bwd_smem(const Ws& ws, int n_pairs = kMaxSpecies * (kMaxSpecies + 1) / 2);

@@ -615,10 +615,21 @@ __global__ void k_vjp_zero(VjpBufs vb, int n_in) {
 size_t vjp_jvp_smem(const Ws& ws) { return (size_t)kWarps * (3 * ws.cap_a + ws.cap_r) * sizeof(float4); }
 size_t vjp_dual_smem(const Ws& ws) { return (size_t)kWarps * (4 * ws.cap_a + 64) * sizeof(float4); }
 
+// raise (never lower) the kernels' dynamic shared-memory limits: other handles
+// of the process may need larger ones
 cudaError_t vjp_set_smem(const Ws& ws) {
-  cudaError_t e = cudaFuncSetAttribute(k_aev_jvp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_jvp_smem(ws));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_aev_bwd_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_dual_smem(ws));
+  const void* fn[2] = {(const void*)k_aev_jvp, (const void*)k_aev_bwd_dual};
+  const int need[2] = {(int)vjp_jvp_smem(ws), (int)vjp_dual_smem(ws)};
+  for (int i = 0; i < 2; ++i) {
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, fn[i]);
+    if (e != cudaSuccess) return e;
+    if (attr.maxDynamicSharedSizeBytes < need[i]) {
+      e = cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize, need[i]);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 void launch_vjp_zero(const Ws& ws, const VjpBufs& vb, int n_in, cudaStream_t st) {

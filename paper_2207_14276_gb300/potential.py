@@ -99,6 +99,17 @@ class Potential:
     def launch_count(self):
         return lib().nnp_last_launch_count(self._h)
 
+    def set_skin(self, skin):
+        """Keep neighbour lists between calls, rebuilt once an atom has moved more
+        than skin/2 A since the last build (0 disables)."""
+        check(lib().nnp_set_skin(self._h, float(skin)))
+
+    def list_stats(self, stream=None):
+        """(list builds, calls made with a skin) since the skin was set."""
+        b, c = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().nnp_list_stats(self._h, _stream_ptr(stream), ctypes.byref(b), ctypes.byref(c)))
+        return b.value, c.value
+
     def energy_forces_into(self, coords, species, box, mask, energy, forces, virial=None,
                            stream=None):
         """Asynchronous call on preallocated device tensors (no synchronisation)."""
