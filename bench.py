@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serving-rates", default="1000,10000,50000",
                     help="Poisson request rates (req/s) of the serving stream; '' to skip")
     ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--md-steps", type=int, default=100,
+                    help="MD-like trajectory steps for the persistent-list (skin) measurement; 0 to skip")
     return ap.parse_args()
 
 
@@ -339,6 +341,41 @@ def run_serving(rates, n_requests, precision="bf16", lanes=2, max_systems=256,
 
 
 # ------------------------------------------------------------------ our arm
+def md_trajectory(spec, w, precision, x0, sp, box, mask, n_eval, steps, skin, sigma, flush, dev):
+    """Energy+force calls along a random-walk trajectory (each coordinate moves by
+    N(0, sigma) A per step), every frame copied into one coordinate buffer as an
+    integrator would update it.  Returns (ms per step incl. the copy, list builds)."""
+    import torch
+    from paper_2207_14276_gb300 import Potential
+    pot = Potential(spec, w, precision=precision)
+    pot.set_skin(skin)
+    gen = torch.Generator(device=dev).manual_seed(11)
+    frames = [x0]
+    for _ in range(steps):
+        frames.append(frames[-1] + sigma * torch.randn(x0.shape, device=dev, generator=gen))
+    xb = x0.clone()
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    F = torch.empty((x0.shape[0], 3), dtype=torch.float32, device=dev)
+    pot.energy_forces(xb, sp, box, mask)      # establishes capacities
+    for _ in range(3):
+        pot.energy_forces_into(xb, sp, box, mask, E, F)
+    stream = torch.cuda.current_stream(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    b0 = pot.list_stats()[0]
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        starts[k].record(stream)
+        xb.copy_(frames[k + 1])
+        pot.energy_forces_into(xb, sp, box, mask, E, F)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if pot.sync_status() != 0:
+        raise RuntimeError("device status after the trajectory")
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
+    return ms, pot.list_stats()[0] - b0
+
+
 def run_ours(args):
     import torch
     from paper_2207_14276_gb300 import Potential
@@ -472,6 +509,52 @@ def run_ours(args):
             # whole-job e2e rate: every rank's replica, limited by the slowest rank
             e2e["value"] = world * n_eval / max_over_ranks(n_eval / e2e["value"], dist, dev)
 
+    md = None
+    if args.md_steps > 0 and rank == 0:
+        sigma = 0.01
+        t_rb, b_rb = md_trajectory(spec, w, args.precision, x, sp, box, mask, n_eval,
+                                   args.md_steps, 0.0, sigma, flush, dev)
+        md = {"workload": f"{args.workload} along a random-walk trajectory, every coordinate "
+                          f"N(0, {sigma} A) per step, frame copied into the coordinate buffer "
+                          "inside the timed step; L2 flushed between steps",
+              "steps": args.md_steps,
+              "lists_rebuilt_every_step": {"ms_per_step": t_rb, "value": n_eval / (t_rb / 1e3),
+                                           "unit": UNIT}}
+        for skin in (0.5, 1.0):
+            t_sk, b_sk = md_trajectory(spec, w, args.precision, x, sp, box, mask, n_eval,
+                                       args.md_steps, skin, sigma, flush, dev)
+            md[f"skin_{skin}A"] = {"ms_per_step": t_sk, "value": n_eval / (t_sk / 1e3),
+                                   "unit": UNIT, "list_builds": b_sk}
+
+    # energy-only re-evaluation of a batch of snapshots (reweighting, no forces)
+    snap = None
+    if args.md_steps > 0 and rank == 0:
+        n_frames = 16
+        gen = torch.Generator(device=dev).manual_seed(12)
+        frames = [{"coords": x + 0.05 * torch.randn(x.shape, device=dev, generator=gen),
+                   "species": sp, "box": box, "mask": mask} for _ in range(n_frames)]
+        snap = {"workload": f"{n_frames} snapshots of {args.workload} (coordinates "
+                            "perturbed by N(0, 0.05 A)) as one batch call; L2 flushed between calls"}
+        for name, want_f in (("energy_only", False), ("energy_forces", True)):
+            pb = Potential(spec, w, precision=args.precision)
+            outs = pb.energy_forces_batch(frames, forces=want_f)
+            for _ in range(3):
+                outs = pb.energy_forces_batch(frames, forces=want_f, check_status=False,
+                                              outputs=outs)
+            reps = 10
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+            for k in range(reps):
+                flush.fill_(k & 0xff)
+                ev[2 * k].record(stream)
+                outs = pb.energy_forces_batch(frames, forces=want_f, check_status=False,
+                                              outputs=outs)
+                ev[2 * k + 1].record(stream)
+            torch.cuda.synchronize()
+            if pb.sync_status() != 0:
+                raise RuntimeError("device status after the snapshot batch")
+            ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+            snap[name] = {"ms_per_batch": ms, "value": n_frames * n_eval / (ms / 1e3), "unit": UNIT}
+
     serving = None
     if args.serving_rates and rank == 0:
         rates = [float(r) for r in args.serving_rates.split(",") if r]
@@ -515,6 +598,8 @@ def run_ours(args):
         "stage_pass_ms_per_step": sum(prof_ms) / len(prof_ms),
         "neighbours_per_atom": {"radial": counts[0], "angular": counts[1]},
         "serving": serving,
+        "persistent_lists": md,
+        "snapshot_batch": snap,
     }
     print(json.dumps(out))
     if dist is not None:

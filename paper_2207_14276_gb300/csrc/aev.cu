@@ -98,51 +98,14 @@ __device__ __forceinline__ Geo pair_geo(const float4& xi, const float4& xj, cons
   return g;
 }
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
-// One lane per entry of a species-sorted neighbour list with species blocks
-// off[0..S]: visit(slot, j, geometry) stages entry j at slot.  With `compact`
-// (lists built with a skin), entries at R >= rc are dropped, the kept ones keep
-// their order, and off[] is rewritten to the kept blocks.
+// One lane per entry of a neighbour list: visit(slot, j, geometry) stages entry j.
 template <class Visit>
-__device__ __forceinline__ void stage_list(int* off, int S, const int* lst, bool compact, float rc,
-                                           const float4& xi, const SysDev& d, const float4* xyzq,
-                                           unsigned lane, Visit visit) {
-  if (!compact) {
-    const int n = off[S];
-    for (int t = (int)lane; t < n; t += 32) {
-      const int j = lst[t];
-      visit(t, j, pair_geo(xi, xyzq[j], d));
-    }
-    return;
+__device__ __forceinline__ void stage_list(int n, const int* lst, const float4& xi, const SysDev& d,
+                                           const float4* xyzq, unsigned lane, Visit visit) {
+  for (int t = (int)lane; t < n; t += 32) {
+    const int j = lst[t];
+    visit(t, j, pair_geo(xi, xyzq[j], d));
   }
-  int w_off = 0;
-  for (int s = 0; s < S; ++s) {
-    const int beg = off[s], end = off[s + 1], start = w_off;
-    for (int t0 = beg; t0 < end; t0 += 32) {
-      const int t = t0 + (int)lane;
-      bool keep = false;
-      Geo g{0.f, 0.f, 0.f, 0.f};
-      int j = 0;
-      if (t < end) {
-        j = lst[t];
-        g = pair_geo(xi, xyzq[j], d);
-        keep = g.r < rc;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      if (keep) visit(w_off + __popc(bal & lanemask_lt()), j, g);
-      w_off += __popc(bal);
-    }
-    __syncwarp();   // every lane has read off[s] and off[s + 1]
-    if (lane == 0) off[s] = start;
-  }
-  __syncwarp();
-  if (lane == 0) off[S] = w_off;
-  __syncwarp();
 }
 
 // cosine cutoff (Eq. 3) and its derivative (inv_rc = 1 / rc)
@@ -295,12 +258,11 @@ k_aev_fwd(Ws ws, AevConst ac) {
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
   const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
-  const bool compact = ac.skin > 0.f;
-  stage_list(H.off_r, ac.S, lr, compact, ac.rc_r, xi, d, ws.xyzq, lane,
+  stage_list(H.off_r[ac.S], lr, xi, d, ws.xyzq, lane,
              [&](int slot, int, const Geo& g) {
                rad[slot] = make_float2(g.r, fcut(g.r, ac.rc_r, inv_rc_r));
              });
-  stage_list(H.off_a, ac.S, la, compact, ac.rc_a, xi, d, ws.xyzq, lane,
+  stage_list(H.off_a[ac.S], la, xi, d, ws.xyzq, lane,
              [&](int slot, int, const Geo& g) {
                const float inv = rcp_approx(g.r);
                angv[slot] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
@@ -404,7 +366,7 @@ k_aev_bwd(Ws ws, AevConst ac) {
   const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
   for (int f = lane; f < ac.S * kNR; f += 32) grad[f] = g_row[f];
   // angular neighbours: unit vector and R, (f_c, f_c', 1/R, packed index)
-  stage_list(H.off_a, ac.S, la, ac.skin > 0.f, ac.rc_a, xi, d, ws.xyzq, lane,
+  stage_list(H.off_a[ac.S], la, xi, d, ws.xyzq, lane,
              [&](int slot, int j, const Geo& g) {
                const float inv = rcp_approx(g.r);
                angv[slot] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
@@ -428,7 +390,6 @@ k_aev_bwd(Ws ws, AevConst ac) {
     for (int t = H.off_r[s] + lane; t < H.off_r[s + 1]; t += 32) {
       const int j = lr[t];
       const Geo g = pair_geo(xi, ws.xyzq[j], d);
-      if (g.r >= ac.rc_r) continue;   // inside the list's skin only
       float fc, dfc;
       fcut_both(g.r, ac.rc_r, inv_rc_r, &fc, &dfc);
       float dEdR = 0.f;

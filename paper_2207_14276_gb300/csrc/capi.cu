@@ -306,10 +306,16 @@ size_t carve(nnp_handle* h, char* base) {
     ws.skin_state = c.take<int>(4);
     ws.ref = c.take<float4>(n);
     ws.in_pos = c.take<int>(n);
+    ws.nbs_cnt = c.take<uint16_t>(n * 16);
+    ws.nbs_r = c.take<int>(n * h->cap_r);
+    ws.nbs_a = c.take<int>(n * h->cap_a);
   } else {
     ws.skin_state = nullptr;
     ws.ref = nullptr;
     ws.in_pos = nullptr;
+    ws.nbs_cnt = nullptr;
+    ws.nbs_r = nullptr;
+    ws.nbs_a = nullptr;
   }
   ws.half_skin = 0.5f * h->skin;
   const bool bf16 = (m.precision == NNP_BF16_MLP);
@@ -498,6 +504,7 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     if ((rc = chk("cell lists"))) return rc;
     { StageTimer t(h, st, 1); launch_neighbors(ws, n_in, ac, st); }
     if ((rc = chk("neighbors"))) return rc;
+    if (ws.skin_state) ++launches;   // the list refresh
     { StageTimer t(h, st, 2); launch_aev_fwd(ws, n_in, ac, st); }
     if ((rc = chk("aev_fwd"))) return rc;
     launches += 6;

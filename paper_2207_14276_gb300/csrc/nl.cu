@@ -733,6 +733,62 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbors(Ws ws, AevConst ac) {
   }
 }
 
+// Lists at the cutoffs from the persistent lists at the cutoffs + skin, one warp
+// per centre: the entries of each species block of the longer radial list whose
+// current distance is within rc_r (radial) or rc_a (angular), in their order.
+__global__ void __launch_bounds__(256) k_list_refresh(Ws ws, AevConst ac) {
+  const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const unsigned lane = threadIdx.x & 31;
+  if (p >= ws.totals[0]) return;
+  const float4 xi = ws.xyzq[p];
+  const SysDev& d = ws.sys[ws.pos_sys[p]];
+  const int per = d.in.periodic;
+  const float rr2 = ac.rc_r * ac.rc_r, ra2 = ac.rc_a * ac.rc_a;
+  const uint16_t* hm = ws.nbs_cnt + (size_t)p * 16;
+  const int* lm = ws.nbs_r + (size_t)p * ws.cap_r;
+  uint16_t* hdr = ws.nb_cnt + (size_t)p * 16;
+  int* out_r = ws.nb_r + (size_t)p * ws.cap_r;
+  int* out_a = ws.nb_a + (size_t)p * ws.cap_a;
+  int off = 0, wr_r = 0, wr_a = 0;
+  for (int s = 0; s < ac.S; ++s) {
+    const int end = off + hm[s];
+    int cr = 0, ca = 0;
+    for (int t0 = off; t0 < end; t0 += 32) {
+      const int t = t0 + (int)lane;
+      bool keep = false, ang = false;
+      int j = 0;
+      if (t < end) {
+        j = lm[t];
+        const float4 xj = ws.xyzq[j];
+        float dv[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+        if (per)
+          for (int c = 0; c < 3; ++c) {
+            const float n = rintf(dv[c] / d.in.box_hi[c]);
+            dv[c] = fmaf(-n, d.in.box_lo[c], fmaf(-n, d.in.box_hi[c], dv[c]));
+          }
+        const float r2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+        keep = r2 <= rr2 && r2 > 1e-12f;
+        ang = keep && r2 <= ra2;
+      }
+      const unsigned br = __ballot_sync(0xffffffffu, keep);
+      const unsigned ba = __ballot_sync(0xffffffffu, ang);
+      if (keep) out_r[wr_r + cr + __popc(br & lanemask_lt())] = j;
+      if (ang) out_a[wr_a + ca + __popc(ba & lanemask_lt())] = j;
+      cr += __popc(br);
+      ca += __popc(ba);
+    }
+    if (lane == 0) {
+      hdr[s] = (uint16_t)cr;
+      hdr[8 + s] = (uint16_t)ca;
+    }
+    wr_r += cr;
+    wr_a += ca;
+    off = end;
+  }
+  if (lane == 0)
+    for (int s = ac.S; s < 8; ++s) { hdr[s] = 0; hdr[8 + s] = 0; }
+}
+
 }  // namespace
 
 void launch_init_chunk(const Ws& ws, const BatchParams& bp, cudaStream_t st) {
@@ -777,7 +833,18 @@ void launch_neighbors(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t s
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min(ws.cell_cap, 4 * std::max(sms, 1)));
-  k_neighbors<<<grid, kNbThreads, 0, st>>>(ws, ac);
+  if (ws.skin_state && ac.skin > 0.f) {
+    // persistent lists: the search (when it runs) fills the lists at the cutoffs
+    // + skin; every call then derives the lists at the cutoffs from them
+    Ws wm = ws;
+    wm.nb_cnt = ws.nbs_cnt;
+    wm.nb_r = ws.nbs_r;
+    wm.nb_a = ws.nbs_a;
+    k_neighbors<<<grid, kNbThreads, 0, st>>>(wm, ac);
+    k_list_refresh<<<(n_in + 7) / 8, 256, 0, st>>>(ws, ac);
+  } else {
+    k_neighbors<<<grid, kNbThreads, 0, st>>>(ws, ac);
+  }
 }
 
 }  // namespace nnp

@@ -120,6 +120,9 @@ struct Ws {
   float half_skin;      // rebuild when an atom moved farther than this since the build
   float4* ref;          // [n_in] input coordinates at the last build
   int* in_pos;          // [n_in] packed position of an input atom at the last build (-1: none)
+  uint16_t* nbs_cnt;    // [n_in][16] lists at the cutoffs + skin, as nb_cnt / nb_r / nb_a
+  int* nbs_r;           // [n_in][cap_r]
+  int* nbs_a;           // [n_in][cap_a]
 };
 
 // whether this call rebuilds the cell lists and neighbour lists
