@@ -48,6 +48,8 @@ WORKLOAD_DESC = {
     "solvated100k": "solvated100k: 1000-atom branched solute in 33,000 waters, 100,000 atoms, "
                     "periodic 99.9 A box; 7-species 1008-dim AEV; 8 networks 1008-256-192-160-1",
     "gas24": "gas24: one 24-atom molecule (H12 C7 N3 O2), non-periodic",
+    "solvated20k": "solvated20k: 50-atom solute in 6,667 waters, ~20,000 atoms, periodic 58.4 A "
+                   "box; 7-species 1008-dim AEV; 8 networks 1008-256-192-160-1",
 }
 
 
@@ -87,6 +89,30 @@ FP32_LANES_PER_SM = 128
 def fp32_alu_peak_tflops(sm_mhz):
     """FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP per clock."""
     return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+STAGE_SOURCE = {"mlp": "mlp_fused.cu", "aev_bwd": "aev.cu", "aev_fwd": "aev.cu",
+                "neighbors": "nl.cu", "mlp_l1": "mlp_tc.cu", "mlp_l2": "mlp_tc.cu",
+                "mlp_l3": "mlp_tc.cu", "mlp_b3": "mlp_tc.cu", "mlp_b2": "mlp_tc.cu",
+                "mlp_b1": "mlp_tc.cu"}
+
+
+def recorded_traffic(stage, workload):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu summary, or
+    None if there is none for this workload or the kernel source changed since."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = STAGE_SOURCE.get(stage)
+    path = os.path.join(here, "profiles", "dram_traffic.txt")
+    if src is None or not os.path.exists(path):
+        return None
+    with open(os.path.join(here, "paper_2207_14276_gb300", "csrc", src), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == stage and f[1] == workload:
+            return int(f[2]) if f[3] == sha else None
+    return None
 
 
 def stage_work(stage, spec, counts, n_atoms, precision):
@@ -481,6 +507,7 @@ def run_ours(args):
             peak = fp32_alu_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
             roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None}
+        roof["traffic"] = recorded_traffic(dom, args.workload)
         roof.update({"kernel": dom, "launch_ms": dom_ms, "peak_source": peak_src,
                      "work_per_launch": amount, "work_unit": unit,
                      "timing": "CUDA events around the kernel on its launching stream, "

@@ -216,6 +216,10 @@ def workload(name: str):
         return [water_box(3000, 44.77, 15, seed=1, name="water9000")], "ani4", 1
     if name == "solvated100k":
         return [solvated_solute(33000, 1000, 99.9, seed=2, name="solvated100k")], "ani7x8", 1
+    if name == "solvated20k":
+        # the serving stream's resident box size (6,667 waters + a 30-80 atom solute,
+        # 58.4 A) with the 8-network model; the whole box is the ML region
+        return [solvated_solute(6667, 50, 58.4, seed=5, name="solvated20k")], "ani7x8", 1
     if name == "molecules64":
         rng = _rng(4)
         mols = []
