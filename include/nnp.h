@@ -311,6 +311,23 @@ int nnp_last_launch_count(const nnp_handle* h);
 int nnp_set_skin(nnp_handle* h, float skin);
 int nnp_list_stats(nnp_handle* h, void* stream, int64_t* builds, int64_t* calls);
 
+/* Velocity-Verlet kick and drift for a multiple-time-step driver that evaluates
+ * the potential on the ML region every outer step (paper Eq. 7: the hybrid
+ * energy V_MM + V_ML(P) - V_MM(P), integrated with RESPA; the MM terms belong to
+ * the host engine).  For every atom i with mask == NULL or mask[i] != 0:
+ *   v_i += dt_kick_fs * 4.184e-4 * F_i * inv_masses[i]   (F in kcal/mol/A,
+ *                                                         masses in g/mol, v in A/fs)
+ *   x_i += dt_drift_fs * v_i
+ * coords, velocities: device float [n][3], updated in place; forces: device
+ * float [n][3] or NULL (no kick); inv_masses: device float [n] (0 freezes an
+ * atom); mask: device uint8 [n] or NULL.  kinetic: device double or NULL; when
+ * given it receives sum_i m_i |v_i|^2 / 2 in kcal/mol over the masked atoms
+ * after the kick.  Asynchronous on `stream`.  Returns NNP_OK, NNP_ERR_ARG or
+ * NNP_ERR_CUDA (launch failure). */
+int nnp_integrate(int64_t n_atoms, float* coords, float* velocities, const float* forces,
+                  const float* inv_masses, const uint8_t* mask, float dt_kick_fs,
+                  float dt_drift_fs, double* kinetic, void* stream);
+
 /* Per-stage timing with CUDA events recorded on the caller's stream around the
  * kernels of each stage (prep, neighbors, aev_fwd, mlp_l1 .. mlp_b1, aev_bwd,
  * finalize, mlp_cvt).  nnp_profile(h, 1) enables recording for later calls;

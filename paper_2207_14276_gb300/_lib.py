@@ -41,6 +41,7 @@ EXPORTS = (
     "nnp_server_create", "nnp_server_destroy", "nnp_server_register", "nnp_server_submit",
     "nnp_server_poll", "nnp_server_stats", "nnp_force_vjp_batch", "nnp_force_vjp",
     "nnp_n_weights", "nnp_debug_wait_probe", "nnp_set_skin", "nnp_list_stats",
+    "nnp_integrate",
 )
 
 
@@ -132,6 +133,7 @@ def lib():
     L.nnp_debug_wait_probe.argtypes = [P, ctypes.c_uint, P]
     L.nnp_set_skin.argtypes = [P, ctypes.c_float]
     L.nnp_list_stats.argtypes = [P, P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.nnp_integrate.argtypes = [i64, P, P, P, P, P, ctypes.c_float, ctypes.c_float, P, P]
     L.nnp_profile.argtypes = [P, i]
     L.nnp_profile_read.argtypes = [P, i, P, P, i, P]
     L.nnp_profile_stage_name.restype = ctypes.c_char_p
