@@ -13,24 +13,28 @@
 // CELU'(Z) is rebuilt from the stored activation: 1 for H > 0, else 1 + H/alpha
 // (CELU(z) = alpha (exp(z/alpha) - 1) on the negative branch).
 //
-// Each phase is a 32 x N block product: warp w owns rows 8w..8w+7 and each
-// lane N/32 columns, so a thread keeps an 8 x N/32 accumulator tile.  A lane's
-// columns are 4 consecutive ones in every 128-wide group (then 2 of a 64-wide
-// and 1 of a 32-wide remainder), so that a K-slice row of the weights is read
-// with one 16-byte load per group and the activation operand is a broadcast
-// 16-byte load of 4 consecutive k of one row.  Weight K-slices (k-major, from
-// the transposed or plain layout as the phase needs) are double-buffered in
-// shared memory with cp.async; they come from L2, which holds every network's
-// weights.
+// Each phase is a 32 x N block product on 8 warps: warp w owns rows
+// 8 (w % 4)..+7 of the tile and one of two column halves (w / 4; the first half
+// is the smallest multiple of 32 that is at least N/2), so every row of the
+// tile is worked on by two warps and a CTA keeps 8 warps busy.  A thread keeps
+// an 8 x C accumulator tile; inside its half a lane owns 4 consecutive columns
+// per 128-wide group (then 2 of a 64-wide and 1 of a 32-wide remainder), so a
+// K-slice row of the weights is read with 16-byte loads, and the activation
+// operand is a broadcast 16-byte load of 4 consecutive k of one row.  Weight
+// K-slices (k-major, from the transposed or plain layout as the phase needs) are
+// double-buffered in shared memory with cp.async; they come from L2, which holds
+// every network's weights.
+#include <type_traits>
+
 #include "mlp.cuh"
 
 namespace nnp {
 
 namespace {
 
-constexpr int kRows = 32;     // rows per CTA
-constexpr int kThreads = 128; // 4 warps x 8 rows
-constexpr int KS = 16;        // K-slice of one pipeline stage
+constexpr int kRows = 32;       // rows per CTA
+constexpr int kThreads = 256;   // 8 warps: 4 row groups x 2 column halves
+constexpr int KS = 16;          // K-slice of one pipeline stage
 constexpr int kOutChunk = 128;  // B1 output columns per pass
 
 struct FusedArgs {
@@ -90,13 +94,9 @@ struct Cols {
   static constexpr int Q = N / 128;
   static constexpr int P = (N % 128) >= 64 ? 1 : 0;
   static constexpr int S1 = (N % 64) ? 1 : 0;
-  __device__ static __forceinline__ int col(int c, int lane) {
-    return c < 4 * Q ? 128 * (c / 4) + 4 * lane + (c % 4)
-         : c < 4 * Q + 2 * P ? 128 * Q + 2 * lane + (c - 4 * Q)
-                             : 128 * Q + 64 * P + lane;
-  }
-  // v[c] = row[col(c)]   (row 16-byte aligned)
-  __device__ static __forceinline__ void load(float (&v)[C], const float* row, int lane) {
+  // v[c] = row[col(c)] for c < C   (row 16-byte aligned; v may be longer)
+  template <int CM>
+  __device__ static __forceinline__ void load(float (&v)[CM], const float* row, int lane) {
 #pragma unroll
     for (int g = 0; g < Q; ++g) {
       const float4 t = *reinterpret_cast<const float4*>(row + 128 * g + 4 * lane);
@@ -108,7 +108,8 @@ struct Cols {
     }
     if (S1) v[C - 1] = row[128 * Q + 64 * P + lane];
   }
-  __device__ static __forceinline__ void store(const float (&v)[C], float* row, int lane) {
+  template <int CM>
+  __device__ static __forceinline__ void store(const float (&v)[CM], float* row, int lane) {
 #pragma unroll
     for (int g = 0; g < Q; ++g)
       *reinterpret_cast<float4*>(row + 128 * g + 4 * lane) =
@@ -118,21 +119,40 @@ struct Cols {
   }
 };
 
-// acc[r][c] = sum_k A[8w + r][k] * B[k][n0 + col(c)] over k < K (K a multiple of KS).
-// A: shared [32][lda] (AG = false) or global rows Ag[row][ldg] starting at the
-// tile (AG = true, staged through As).  B: global [K][ldb]; columns n0 + j >= Nv
-// read as zero.
+// the two column halves of an N-wide phase
+template <int N>
+struct Halves {
+  static constexpr int N0 = 32 * ((N + 63) / 64);
+  static constexpr int N1 = N - N0;
+  static constexpr int C = N0 / 32;   // accumulator columns (the wider half)
+};
+
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+// f(IC<width>, first column) for the calling warp's column half
+template <int N, class F>
+__device__ __forceinline__ void on_half(int h, F f) {
+  if (h == 0) f(IC<Halves<N>::N0>{}, 0);
+  else if (Halves<N>::N1 > 0) f(IC<Halves<N>::N1>{}, Halves<N>::N0);
+}
+
+// acc[r][c] = sum_k A[row r][k] * B[k][n0 + half column c] over k < K (K a multiple
+// of KS), rows 8 (w % 4) + r.  A: shared [32][lda] (AG = false) or global rows
+// Ag[row][ldg] starting at the tile (AG = true, staged through As).  B: global
+// [K][ldb]; columns n0 + j >= Nv read as zero.
 template <int N, bool AG>
-__device__ __forceinline__ void block_gemm(float (&acc)[8][N / 32], const float* A, int lda,
+__device__ __forceinline__ void block_gemm(float (&acc)[8][Halves<N>::C], const float* A, int lda,
                                            const float* Ag, int ldg, float* As, int K,
                                            const float* B, int ldb, int n0, int Nv, float* Bs) {
-  constexpr int C = N / 32;
+  constexpr int CM = Halves<N>::C;
   constexpr int kVec = KS * N / 4;  // float4s per B slice
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int rg = w & 3, h = w >> 2;
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[r][c] = 0.f;
+    for (int c = 0; c < CM; ++c) acc[r][c] = 0.f;
   auto issue = [&](int k0, int buf) {
     float* bs = Bs + buf * KS * N;
 #pragma unroll
@@ -144,8 +164,7 @@ __device__ __forceinline__ void block_gemm(float (&acc)[8][N / 32], const float*
         cp_async16(bs + row * N + col, B + (size_t)(k0 + row) * ldb + (ok ? n0 + col : 0), ok);
       }
     }
-    if (AG) {  // 32 rows x KS k of the AEV: one float4 per thread
-      static_assert(kRows * KS / 4 == kThreads, "A stage");
+    if (AG && tid < kRows * KS / 4) {  // 32 rows x KS k of the AEV: one float4 per thread
       const int row = tid / (KS / 4), q = tid % (KS / 4);
       cp_async16(As + buf * kRows * (KS + 4) + row * (KS + 4) + q * 4,
                  Ag + (size_t)row * ldg + k0 + q * 4, true);
@@ -160,26 +179,30 @@ __device__ __forceinline__ void block_gemm(float (&acc)[8][N / 32], const float*
     __syncthreads();
     if (sl + 1 < n_slices) issue((sl + 1) * KS, buf ^ 1);
     const float* bs = Bs + buf * KS * N;
-    const float* arow = AG ? As + buf * kRows * (KS + 4) + (w * 8) * (KS + 4)
-                           : A + (size_t)(w * 8) * lda + sl * KS;
+    const float* arow = AG ? As + buf * kRows * (KS + 4) + (rg * 8) * (KS + 4)
+                           : A + (size_t)(rg * 8) * lda + sl * KS;
     const int lds = AG ? KS + 4 : lda;
+    on_half<N>(h, [&](auto nw, int col0) {
+      constexpr int NW = decltype(nw)::value;
+      constexpr int C = NW / 32;
 #pragma unroll
-    for (int kk = 0; kk < KS; kk += 4) {
-      float4 a[8];
+      for (int kk = 0; kk < KS; kk += 4) {
+        float4 a[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) a[r] = *reinterpret_cast<const float4*>(arow + r * lds + kk);
+        for (int r = 0; r < 8; ++r) a[r] = *reinterpret_cast<const float4*>(arow + r * lds + kk);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float b[C];
-        Cols<N>::load(b, bs + (kk + q) * N, lane);
+        for (int q = 0; q < 4; ++q) {
+          float b[CM];
+          Cols<NW>::load(b, bs + (kk + q) * N + col0, lane);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const float av = comp(a[r], q);
+          for (int r = 0; r < 8; ++r) {
+            const float av = comp(a[r], q);
 #pragma unroll
-          for (int c = 0; c < C; ++c) acc[r][c] = fmaf(av, b[c], acc[r][c]);
+            for (int c = 0; c < C; ++c) acc[r][c] = fmaf(av, b[c], acc[r][c]);
+          }
         }
       }
-    }
+    });
   }
   __syncthreads();  // every warp is done with Bs/As (and with A) before they are reused
 }
@@ -192,9 +215,47 @@ struct Smem {
   static constexpr int H1 = 0, H2 = H1 + kRows * ld1, H3 = H2 + kRows * ld2;
   static constexpr int As = H2;  // the AEV stage of L1 lives where H2/H3 go later
   static constexpr int Bs = H3 + kRows * ld3;
-  static constexpr int floats = Bs + 2 * KS * cmax(cmax(N1, N2), cmax(N3, kOutChunk));
+  static constexpr int Dot = Bs + 2 * KS * cmax(cmax(N1, N2), cmax(N3, kOutChunk));  // [2][32]
+  static constexpr int floats = Dot + 2 * kRows;
   static_assert(2 * kRows * (KS + 4) <= kRows * (ld2 + ld3), "A stage overlay");
 };
+
+// L1/L2 epilogue: H[row][col] = CELU(acc + b[col]) for this warp's half
+template <int N, class Acc>
+__device__ __forceinline__ void store_celu(Acc& acc, const float* bias, float* H, int ld, int h,
+                                           int rg, int lane, float alpha, float inv_alpha) {
+  on_half<N>(h, [&](auto nw, int col0) {
+    constexpr int NW = decltype(nw)::value;
+    constexpr int CM = Halves<N>::C;
+    float b[CM];
+    Cols<NW>::load(b, bias + col0, lane);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+#pragma unroll
+      for (int c = 0; c < NW / 32; ++c) acc[r][c] = celu_f(acc[r][c] + b[c], alpha, inv_alpha);
+      Cols<NW>::store(acc[r], H + (rg * 8 + r) * ld + col0, lane);
+    }
+  });
+}
+
+// B3/B2 epilogue: H[row][col] = acc * CELU'(z) rebuilt from the stored H
+template <int N, class Acc>
+__device__ __forceinline__ void store_delta(Acc& acc, float* H, int ld, int h, int rg, int lane,
+                                            float inv_alpha) {
+  on_half<N>(h, [&](auto nw, int col0) {
+    constexpr int NW = decltype(nw)::value;
+    constexpr int CM = Halves<N>::C;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      float* row = H + (rg * 8 + r) * ld + col0;
+      float hv[CM];
+      Cols<NW>::load(hv, row, lane);
+#pragma unroll
+      for (int c = 0; c < NW / 32; ++c) acc[r][c] *= celu_d_of_h(hv[c], inv_alpha);
+      Cols<NW>::store(acc[r], row, lane);
+    }
+  });
+}
 
 template <int N1, int N2, int N3, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_mlp_fused(FusedArgs a) {
@@ -212,57 +273,49 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mlp_fused(FusedArgs a) {
   float* H3 = smf + L::H3;  // [32][ld3]
   float* As = smf + L::As;  // [2][32][KS+4], during L1 only
   float* Bs = smf + L::Bs;  // [2][KS][N]
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* dot_sh = smf + L::Dot;  // [2 halves][32 rows]
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, rg = w & 3, h = w >> 2;
   const float alpha = a.alpha, inv_alpha = 1.f / a.alpha;
 
   // ---- L1
   {
-    constexpr int C = N1 / 32;
-    float acc[8][C], bias[C];
+    float acc[8][Halves<N1>::C];
     block_gemm<N1, true>(acc, nullptr, 0, a.G + (size_t)m0 * Dp, Dp, As, Dp,
                          a.W1T + s * a.sW1T, N1, 0, N1, Bs);
-    Cols<N1>::load(bias, a.b1 + s * a.sb1, lane);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) acc[r][c] = celu_f(acc[r][c] + bias[c], alpha, inv_alpha);
-      Cols<N1>::store(acc[r], H1 + (w * 8 + r) * L::ld1, lane);
-    }
+    store_celu<N1>(acc, a.b1 + s * a.sb1, H1, L::ld1, h, rg, lane, alpha, inv_alpha);
   }
   __syncthreads();
   // ---- L2
   {
-    constexpr int C = N2 / 32;
-    float acc[8][C], bias[C];
+    float acc[8][Halves<N2>::C];
     block_gemm<N2, false>(acc, H1, L::ld1, nullptr, 0, nullptr, N1, a.W2T + s * a.sW2, N2, 0, N2, Bs);
-    Cols<N2>::load(bias, a.b2 + s * a.sb2, lane);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) acc[r][c] = celu_f(acc[r][c] + bias[c], alpha, inv_alpha);
-      Cols<N2>::store(acc[r], H2 + (w * 8 + r) * L::ld2, lane);
-    }
+    store_celu<N2>(acc, a.b2 + s * a.sb2, H2, L::ld2, h, rg, lane, alpha, inv_alpha);
   }
   __syncthreads();
   // ---- L3 and the output layer: e = H3 . w4, D3 = w4 * CELU'(Z3)
   {
-    constexpr int C = N3 / 32;
-    float acc[8][C], bias[C], w4[C];
+    constexpr int CM = Halves<N3>::C;
+    float acc[8][CM];
     block_gemm<N3, false>(acc, H2, L::ld2, nullptr, 0, nullptr, N2, a.W3T + s * a.sW3, N3, 0, N3, Bs);
-    Cols<N3>::load(bias, a.b3 + s * a.sb3, lane);
-    Cols<N3>::load(w4, a.w4 + s * a.sw4, lane);
     float dot[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      dot[r] = 0.f;
+    for (int r = 0; r < 8; ++r) dot[r] = 0.f;
+    on_half<N3>(h, [&](auto nw, int col0) {
+      constexpr int NW = decltype(nw)::value;
+      float b[CM], w4[CM];
+      Cols<NW>::load(b, a.b3 + s * a.sb3 + col0, lane);
+      Cols<NW>::load(w4, a.w4 + s * a.sw4 + col0, lane);
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const float z = acc[r][c] + bias[c];
-        dot[r] = fmaf(celu_f(z, alpha, inv_alpha), w4[c], dot[r]);
-        acc[r][c] = w4[c] * (z > 0.f ? 1.f : __expf(z * inv_alpha));
+      for (int r = 0; r < 8; ++r) {
+#pragma unroll
+        for (int c = 0; c < NW / 32; ++c) {
+          const float z = acc[r][c] + b[c];
+          dot[r] = fmaf(celu_f(z, alpha, inv_alpha), w4[c], dot[r]);
+          acc[r][c] = w4[c] * (z > 0.f ? 1.f : __expf(z * inv_alpha));
+        }
+        Cols<NW>::store(acc[r], H3 + (rg * 8 + r) * L::ld3 + col0, lane);
       }
-      Cols<N3>::store(acc[r], H3 + (w * 8 + r) * L::ld3, lane);
-    }
+    });
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -271,49 +324,39 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mlp_fused(FusedArgs a) {
       float v = dot[0];
 #pragma unroll
       for (int r = 1; r < 8; ++r) v = lane == r ? dot[r] : v;
-      a.e_row[m0 + w * 8 + lane] = v;
+      dot_sh[h * kRows + rg * 8 + lane] = v;
     }
+    __syncthreads();
+    // the two halves' partial dot products, added in a fixed order
+    if (threadIdx.x < kRows) a.e_row[m0 + threadIdx.x] = dot_sh[threadIdx.x] + dot_sh[kRows + threadIdx.x];
   }
   if (a.energy_only) return;
   __syncthreads();
   // ---- B3: delta2 = (D3 W3) * CELU'(Z2), over H2
   {
-    constexpr int C = N2 / 32;
-    float acc[8][C], h[C];
+    float acc[8][Halves<N2>::C];
     block_gemm<N2, false>(acc, H3, L::ld3, nullptr, 0, nullptr, N3, a.W3 + s * a.sW3, N2, 0, N2, Bs);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      float* row = H2 + (w * 8 + r) * L::ld2;
-      Cols<N2>::load(h, row, lane);
-#pragma unroll
-      for (int c = 0; c < C; ++c) acc[r][c] *= celu_d_of_h(h[c], inv_alpha);
-      Cols<N2>::store(acc[r], row, lane);
-    }
+    store_delta<N2>(acc, H2, L::ld2, h, rg, lane, inv_alpha);
   }
   __syncthreads();
   // ---- B2: delta1 = (delta2 W2) * CELU'(Z1), over H1
   {
-    constexpr int C = N1 / 32;
-    float acc[8][C], h[C];
+    float acc[8][Halves<N1>::C];
     block_gemm<N1, false>(acc, H2, L::ld2, nullptr, 0, nullptr, N2, a.W2 + s * a.sW2, N1, 0, N1, Bs);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      float* row = H1 + (w * 8 + r) * L::ld1;
-      Cols<N1>::load(h, row, lane);
-#pragma unroll
-      for (int c = 0; c < C; ++c) acc[r][c] *= celu_d_of_h(h[c], inv_alpha);
-      Cols<N1>::store(acc[r], row, lane);
-    }
+    store_delta<N1>(acc, H1, L::ld1, h, rg, lane, inv_alpha);
   }
   __syncthreads();
   // ---- B1: dE/dG = delta1 W1, 128 columns per pass (Dp a multiple of 128)
   const float* W1 = a.W1 + s * a.sW1;
   for (int n0 = 0; n0 < Dp; n0 += kOutChunk) {
-    float acc[8][kOutChunk / 32];
+    float acc[8][Halves<kOutChunk>::C];
     block_gemm<kOutChunk, false>(acc, H1, L::ld1, nullptr, 0, nullptr, N1, W1, Dp, n0, Dp, Bs);
+    on_half<kOutChunk>(h, [&](auto nw, int col0) {
+      constexpr int NW = decltype(nw)::value;
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
-      Cols<kOutChunk>::store(acc[r], a.dEdG + (size_t)(m0 + w * 8 + r) * Dp + n0, lane);
+      for (int r = 0; r < 8; ++r)
+        Cols<NW>::store(acc[r], a.dEdG + (size_t)(m0 + rg * 8 + r) * Dp + n0 + col0, lane);
+    });
   }
 }
 
@@ -323,10 +366,10 @@ struct Variant {
   size_t smem;
 };
 const Variant kVariants[] = {
-    // 160-128-96 (4-species model), three CTAs per SM
-    {160, 128, 96, k_mlp_fused<160, 128, 96, 3>, Smem<160, 128, 96>::floats * sizeof(float)},
+    // 160-128-96 (4-species model), two CTAs per SM
+    {160, 128, 96, k_mlp_fused<160, 128, 96, 2>, Smem<160, 128, 96>::floats * sizeof(float)},
     // 256-192-160 (7-species model)
-    {256, 192, 160, k_mlp_fused<256, 192, 160, 2>, Smem<256, 192, 160>::floats * sizeof(float)},
+    {256, 192, 160, k_mlp_fused<256, 192, 160, 1>, Smem<256, 192, 160>::floats * sizeof(float)},
 };
 
 const Variant* find_variant(const MlpDims& md) {
