@@ -451,6 +451,10 @@ void split_box(double L, float* hi, float* lo) {
   *lo = (float)(L - (double)*hi);
 }
 
+// batches up to this many atoms (in one descriptor chunk) run the front end of
+// the chain in one CTA
+constexpr int kFrontMaxAtoms = 2048;
+
 // the kernel chain of one batch on stream st (no host synchronisation)
 int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::vector<BatchParams>& chunks,
                   int n_in, bool any_virial, cudaStream_t st, int* n_launch) {
@@ -486,20 +490,30 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
       }
     if ((rc = chk("displacement check"))) return rc;
   }
-  for (const auto& bp : chunks) { launch_init_chunk(ws, bp, st); ++launches; }
-  for (const auto& bp : chunks) {
-    int n_chunk = 0;
-    for (int k = 0; k < bp.n_sys; ++k) n_chunk += bp.sys[k].n_in;
-    if (n_chunk > 0) { launch_prep_atoms(ws, bp, n_chunk, m.ac.S, st); ++launches; }
+  // small one-chunk batches: the whole front end in one single-CTA launch
+  const bool one_cta_front = chunks.size() == 1 && n_in > 0 && n_in <= kFrontMaxAtoms &&
+                             !ws.skin_state;
+  if (one_cta_front) {
+    StageTimer t(h, st, 0);
+    launch_front(ws, chunks[0], ac, n_in, st);
+    ++launches;
+  } else {
+    for (const auto& bp : chunks) { launch_init_chunk(ws, bp, st); ++launches; }
+    for (const auto& bp : chunks) {
+      int n_chunk = 0;
+      for (int k = 0; k < bp.n_sys; ++k) n_chunk += bp.sys[k].n_in;
+      if (n_chunk > 0) { launch_prep_atoms(ws, bp, n_chunk, m.ac.S, st); ++launches; }
+    }
   }
   if ((rc = chk("init/prep"))) return rc;
   if (n_in > 0) {
-    {
+    if (!one_cta_front) {
       StageTimer t(h, st, 0);
       launch_setup(ws, ac, st);
       launch_bin(ws, n_in, st);
       launch_scan(ws, st);
       launch_scatter(ws, n_in, st);
+      launches += 4;
     }
     if ((rc = chk("cell lists"))) return rc;
     { StageTimer t(h, st, 1); launch_neighbors(ws, n_in, ac, st); }
@@ -507,7 +521,7 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     if (ws.skin_state) ++launches;   // the list refresh
     { StageTimer t(h, st, 2); launch_aev_fwd(ws, n_in, ac, st); }
     if ((rc = chk("aev_fwd"))) return rc;
-    launches += 6;
+    launches += 2;
     // energy only when no system asks for forces or a virial
     bool energy_only = true;
     for (int b = 0; b < n_sys; ++b) energy_only &= (sy[b].forces == nullptr && sy[b].virial == nullptr);

@@ -21,9 +21,10 @@
 // per 128-wide group (then 2 of a 64-wide and 1 of a 32-wide remainder), so a
 // K-slice row of the weights is read with 16-byte loads, and the activation
 // operand is a broadcast 16-byte load of 4 consecutive k of one row.  Weight
-// K-slices (k-major, from the transposed or plain layout as the phase needs) are
-// double-buffered in shared memory with cp.async; they come from L2, which holds
-// every network's weights.
+// K-slices (k-major, from the transposed or plain layout as the phase needs)
+// stream through a 4-stage cp.async ring in shared memory, three slices ahead of
+// the one in use: a tile's phases are a chain of ~90 short slices, and one L2
+// round trip per slice would otherwise set the kernel's duration.
 #include <type_traits>
 
 #include "mlp.cuh"
@@ -35,6 +36,7 @@ namespace {
 constexpr int kRows = 32;       // rows per CTA
 constexpr int kThreads = 256;   // 8 warps: 4 row groups x 2 column halves
 constexpr int KS = 16;          // K-slice of one pipeline stage
+constexpr int NS = 4;           // stages of the cp.async ring (NS - 1 slices in flight)
 constexpr int kOutChunk = 128;  // B1 output columns per pass
 
 struct FusedArgs {
@@ -68,8 +70,10 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+// wait until at most N of this thread's most recent cp.async groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ float comp(const float4& v, int q) {
@@ -171,13 +175,21 @@ __device__ __forceinline__ void block_gemm(float (&acc)[8][Halves<N>::C], const 
     }
     cp_async_commit();
   };
+  // NS-stage ring: slice sl lives in buffer sl % NS; NS - 1 slices are issued
+  // ahead, and every iteration commits one group (empty past the end) so that
+  // "at most NS - 2 groups pending" always means "slice sl has landed"
   const int n_slices = K / KS;
-  issue(0, 0);
+#pragma unroll
+  for (int i = 0; i < NS - 1; ++i) {
+    if (i < n_slices) issue(i * KS, i);
+    else cp_async_commit();
+  }
   for (int sl = 0; sl < n_slices; ++sl) {
-    const int buf = sl & 1;
-    cp_async_wait_all();
-    __syncthreads();
-    if (sl + 1 < n_slices) issue((sl + 1) * KS, buf ^ 1);
+    const int buf = sl % NS;
+    cp_async_wait<NS - 2>();
+    __syncthreads();   // slice sl visible to all; every warp is done with slice sl - 1
+    if (sl + NS - 1 < n_slices) issue((sl + NS - 1) * KS, (sl + NS - 1) % NS);
+    else cp_async_commit();
     const float* bs = Bs + buf * KS * N;
     const float* arow = AG ? As + buf * kRows * (KS + 4) + (rg * 8) * (KS + 4)
                            : A + (size_t)(rg * 8) * lda + sl * KS;
@@ -204,6 +216,7 @@ __device__ __forceinline__ void block_gemm(float (&acc)[8][Halves<N>::C], const 
       }
     });
   }
+  cp_async_wait<0>();   // only empty groups remain; none may straddle the next phase
   __syncthreads();  // every warp is done with Bs/As (and with A) before they are reused
 }
 
@@ -215,9 +228,9 @@ struct Smem {
   static constexpr int H1 = 0, H2 = H1 + kRows * ld1, H3 = H2 + kRows * ld2;
   static constexpr int As = H2;  // the AEV stage of L1 lives where H2/H3 go later
   static constexpr int Bs = H3 + kRows * ld3;
-  static constexpr int Dot = Bs + 2 * KS * cmax(cmax(N1, N2), cmax(N3, kOutChunk));  // [2][32]
+  static constexpr int Dot = Bs + NS * KS * cmax(cmax(N1, N2), cmax(N3, kOutChunk));  // [2][32]
   static constexpr int floats = Dot + 2 * kRows;
-  static_assert(2 * kRows * (KS + 4) <= kRows * (ld2 + ld3), "A stage overlay");
+  static_assert(NS * kRows * (KS + 4) <= kRows * (ld2 + ld3), "A stage overlay");
 };
 
 // L1/L2 epilogue: H[row][col] = CELU(acc + b[col]) for this warp's half
@@ -271,8 +284,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mlp_fused(FusedArgs a) {
   float* H1 = smf + L::H1;  // [32][ld1]
   float* H2 = smf + L::H2;  // [32][ld2]
   float* H3 = smf + L::H3;  // [32][ld3]
-  float* As = smf + L::As;  // [2][32][KS+4], during L1 only
-  float* Bs = smf + L::Bs;  // [2][KS][N]
+  float* As = smf + L::As;  // [NS][32][KS+4], during L1 only
+  float* Bs = smf + L::Bs;  // [NS][KS][N]
   float* dot_sh = smf + L::Dot;  // [2 halves][32 rows]
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, rg = w & 3, h = w >> 2;
   const float alpha = a.alpha, inv_alpha = 1.f / a.alpha;

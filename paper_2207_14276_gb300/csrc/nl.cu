@@ -37,9 +37,8 @@ __device__ __forceinline__ int find_sys(const BatchParams& bp, int idx) {
   return lo;
 }
 
-__global__ void k_init(Ws ws, BatchParams bp, int zero_all, int n_in) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int stride = gridDim.x * blockDim.x;
+__device__ __forceinline__ void init_body(const Ws& ws, const BatchParams& bp, int zero_all,
+                                          int n_in, int tid, int stride) {
   const bool rebuild = lists_rebuild(ws);
   if (!rebuild) {
     // persistent lists: the grids and counts of the last build stay; only this
@@ -75,8 +74,13 @@ __global__ void k_init(Ws ws, BatchParams bp, int zero_all, int n_in) {
   for (int i = tid; i < n_in; i += stride) ws.f_pos[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__global__ void k_prep(Ws ws, BatchParams bp, int n_chunk, int S) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_init(Ws ws, BatchParams bp, int zero_all, int n_in) {
+  init_body(ws, bp, zero_all, n_in, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// one input atom of a chunk (all 32 lanes of a warp call it together)
+__device__ __forceinline__ void prep_body(const Ws& ws, const BatchParams& bp, int t, int n_chunk,
+                                          int S) {
   const unsigned lane = threadIdx.x & 31;
   const bool live = t < n_chunk;
   int k = 0, local = 0, gi = 0, s = -1, b = -1;
@@ -146,10 +150,14 @@ __global__ void k_prep(Ws ws, BatchParams bp, int n_chunk, int S) {
   }
 }
 
-// block-wide exclusive scan helper (blockDim.x == 256)
+__global__ void k_prep(Ws ws, BatchParams bp, int n_chunk, int S) {
+  prep_body(ws, bp, blockIdx.x * blockDim.x + threadIdx.x, n_chunk, S);
+}
+
+// block-wide exclusive scan helper (blockDim.x a multiple of 32, at most 1024)
 __device__ int block_exclusive_scan(int v, int* total) {
-  __shared__ int warp_sums[8];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ int warp_sums[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int incl = v;
   for (int o = 1; o < 32; o <<= 1) {
     int u = __shfl_up_sync(0xffffffffu, incl, o);
@@ -158,21 +166,21 @@ __device__ int block_exclusive_scan(int v, int* total) {
   if (lane == 31) warp_sums[w] = incl;
   __syncthreads();
   if (w == 0) {
-    int ws_ = lane < 8 ? warp_sums[lane] : 0;
-    for (int o = 1; o < 8; o <<= 1) {
+    int ws_ = lane < nw ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
       int u = __shfl_up_sync(0xffffffffu, ws_, o);
       if (lane >= o) ws_ += u;
     }
-    if (lane < 8) warp_sums[lane] = ws_;
+    if (lane < nw) warp_sums[lane] = ws_;
   }
   __syncthreads();
   const int before = (w > 0 ? warp_sums[w - 1] : 0) + incl - v;
-  *total = warp_sums[7];
+  *total = warp_sums[nw - 1];
   __syncthreads();
   return before;
 }
 
-__global__ void k_setup(Ws ws, AevConst ac) {
+__device__ __forceinline__ void setup_body(const Ws& ws, const AevConst& ac) {
   if (!lists_rebuild(ws)) return;
   const float rc = fmaxf(ac.rc_r, ac.rc_a) + ac.skin;
   int run_atoms = 0, run_cells = 0;
@@ -235,6 +243,8 @@ __global__ void k_setup(Ws ws, AevConst ac) {
   }
 }
 
+__global__ void k_setup(Ws ws, AevConst ac) { setup_body(ws, ac); }
+
 // periodic systems: the coordinate wrapped into [0, L] (the value the cell index
 // is taken from and the one stored for the kernels); else the coordinate itself
 __device__ __forceinline__ float wrap_coord(float x, const SysDev& d, int c) {
@@ -249,9 +259,8 @@ __device__ __forceinline__ int cell_coord(float x, const SysDev& d, int c) {
   return min(max(k, 0), d.nc[c] - 1);
 }
 
-__global__ void k_bin(Ws ws, int n_in) {
-  if (!lists_rebuild(ws)) return;
-  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+// one input atom (all 32 lanes of a warp call it together)
+__device__ __forceinline__ void bin_body(const Ws& ws, int gi, int n_in) {
   const unsigned lane = threadIdx.x & 31;
   int b = -1;
   if (gi < n_in) b = ws.in_sys[gi];
@@ -278,10 +287,14 @@ __global__ void k_bin(Ws ws, int n_in) {
   ws.in_slot[gi] = slot;
 }
 
-// single-block exclusive scan of the cell counts (1024 threads)
-__global__ void k_scan(Ws ws) {
-  __shared__ int warp_sums[32];
+__global__ void k_bin(Ws ws, int n_in) {
   if (!lists_rebuild(ws)) return;
+  bin_body(ws, blockIdx.x * blockDim.x + threadIdx.x, n_in);
+}
+
+// single-block exclusive scan of the cell counts (1024 threads)
+__device__ __forceinline__ void scan_body(const Ws& ws) {
+  __shared__ int warp_sums[32];
   const int T = ws.totals[1];
   const int nt = blockDim.x;
   const int per = (T + nt - 1) / nt;
@@ -313,8 +326,12 @@ __global__ void k_scan(Ws ws) {
   if (threadIdx.x == nt - 1) ws.cell_start[T] = warp_sums[31];
 }
 
-__global__ void k_scatter(Ws ws, int n_in) {
-  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_scan(Ws ws) {
+  if (!lists_rebuild(ws)) return;
+  scan_body(ws);
+}
+
+__device__ __forceinline__ void scatter_body(const Ws& ws, int gi, int n_in) {
   if (gi >= n_in) return;
   if (!lists_rebuild(ws)) {
     // persistent lists: new coordinates into the packed order of the last build
@@ -348,6 +365,32 @@ __global__ void k_scatter(Ws ws, int n_in) {
     ws.ref[gi] = make_float4(d.in.coords[3 * local + 0], d.in.coords[3 * local + 1],
                              d.in.coords[3 * local + 2], 0.f);
   }
+}
+
+__global__ void k_scatter(Ws ws, int n_in) {
+  scatter_body(ws, blockIdx.x * blockDim.x + threadIdx.x, n_in);
+}
+
+// The whole front end (init, prep, setup, bin, scan, scatter) of a one-chunk
+// batch in a single CTA: one launch instead of six for small batches, with
+// __syncthreads between the phases (their global writes are visible to the
+// whole CTA after the barrier).
+constexpr int kFrontThreads = 1024;
+__global__ void __launch_bounds__(kFrontThreads) k_front(Ws ws, BatchParams bp, AevConst ac,
+                                                          int n_in) {
+  const int tid = threadIdx.x;
+  init_body(ws, bp, 1, n_in, tid, kFrontThreads);
+  __syncthreads();
+  const int n_up = (n_in + 31) & ~31;   // whole warps, for the warp-collective parts
+  for (int t = tid; t < n_up; t += kFrontThreads) prep_body(ws, bp, t, n_in, ac.S);
+  __syncthreads();
+  setup_body(ws, ac);
+  __syncthreads();
+  for (int t = tid; t < n_up; t += kFrontThreads) bin_body(ws, t, n_in);
+  __syncthreads();
+  scan_body(ws);
+  __syncthreads();
+  for (int t = tid; t < n_in; t += kFrontThreads) scatter_body(ws, t, n_in);
 }
 
 // Largest displacement of an atom of the last build's lists since that build
@@ -820,6 +863,11 @@ void launch_scan(const Ws& ws, cudaStream_t st) { k_scan<<<1, 1024, 0, st>>>(ws)
 void launch_scatter(const Ws& ws, int n_in, cudaStream_t st) {
   if (n_in <= 0) return;
   k_scatter<<<(n_in + 255) / 256, 256, 0, st>>>(ws, n_in);
+}
+
+void launch_front(const Ws& ws, const BatchParams& bp, const AevConst& ac, int n_in,
+                  cudaStream_t st) {
+  k_front<<<1, kFrontThreads, 0, st>>>(ws, bp, ac, n_in);
 }
 
 void launch_skin_check(const Ws& ws, const BatchParams& bp, int n_in_chunk, cudaStream_t st) {

@@ -142,6 +142,9 @@ void launch_scan(const Ws& ws, cudaStream_t st);
 void launch_scatter(const Ws& ws, int n_in, cudaStream_t st);
 void launch_neighbors(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st);
 void launch_skin_check(const Ws& ws, const BatchParams& bp, int n_in_chunk, cudaStream_t st);
+// init + prep + setup + bin + scan + scatter of a one-chunk batch in one CTA
+void launch_front(const Ws& ws, const BatchParams& bp, const AevConst& ac, int n_in,
+                  cudaStream_t st);
 // ---- aev.cu
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st);
 void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
