@@ -294,7 +294,6 @@ size_t carve(nnp_handle* h, char* base) {
   ws.pos_slot = c.take<int>(n);
   ws.pos_sys = c.take<int>(n);
   ws.pos_cell = c.take<int>(n);
-  ws.slot_pos = c.take<int>(rows);
   ws.nb_cnt = c.take<uint16_t>(n * 16);
   ws.nb_r = c.take<int>(n * h->cap_r);
   ws.nb_a = c.take<int>(n * h->cap_a);
@@ -1278,7 +1277,6 @@ size_t noalloc_carve(const Model& m, int n_atoms, char* base, Ws* ws, MlpBufs* m
   ws->pos_slot = c.take<int>(n);
   ws->pos_sys = c.take<int>(n);
   ws->pos_cell = c.take<int>(n);
-  ws->slot_pos = c.take<int>(rows);
   ws->nb_cnt = c.take<uint16_t>(n * 16);
   ws->nb_r = c.take<int>(n * kNoAllocCapR);
   ws->nb_a = c.take<int>(n * kNoAllocCapA);

@@ -69,8 +69,9 @@ __device__ __forceinline__ void init_body(const Ws& ws, const BatchParams& bp, i
     ws.species_fill[tid] = 0;
   }
   if (tid < 4) ws.totals[tid] = 0;
-  for (int i = tid; i < ws.cell_cap; i += stride) ws.cell_count[i] = 0;
-  for (int i = tid; i < ws.row_cap; i += stride) ws.slot_pos[i] = -1;
+  // the batch's cell grids hold at most 2 n + 27 cells per system (k_setup)
+  const int cells = min(ws.cell_cap, 2 * n_in + 27 * ws.n_sys);
+  for (int i = tid; i < cells; i += stride) ws.cell_count[i] = 0;
   for (int i = tid; i < n_in; i += stride) ws.f_pos[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
@@ -359,7 +360,6 @@ __device__ __forceinline__ void scatter_body(const Ws& ws, int gi, int n_in) {
   ws.pos_slot[pos] = slot;
   ws.pos_sys[pos] = b;
   ws.pos_cell[pos] = gcell - d.cell_base;
-  ws.slot_pos[slot] = pos;
   if (ws.in_pos) {   // the reference the displacement check of later calls compares with
     ws.in_pos[gi] = pos;
     ws.ref[gi] = make_float4(d.in.coords[3 * local + 0], d.in.coords[3 * local + 1],
@@ -837,7 +837,8 @@ __global__ void __launch_bounds__(256) k_list_refresh(Ws ws, AevConst ac) {
 void launch_init_chunk(const Ws& ws, const BatchParams& bp, cudaStream_t st) {
   // the first chunk of a batch also zeroes the shared counters
   const int zero_all = (bp.sys_base == 0);
-  const int work = zero_all ? max(max(ws.cell_cap, ws.row_cap), max(ws.n_in, bp.n_sys)) : bp.n_sys;
+  const int cells = min(ws.cell_cap, 2 * ws.n_in + 27 * ws.n_sys);
+  const int work = zero_all ? max(cells, max(ws.n_in, bp.n_sys)) : bp.n_sys;
   int blocks = (work + 255) / 256;
   blocks = max(1, min(blocks, 1184));
   k_init<<<blocks, 256, 0, st>>>(ws, bp, zero_all, ws.n_in);

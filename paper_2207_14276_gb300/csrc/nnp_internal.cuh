@@ -104,7 +104,6 @@ struct Ws {
   int* pos_slot;        // AEV row
   int* pos_sys;
   int* pos_cell;        // local cell index within the system grid
-  int* slot_pos;        // [row_cap] packed position of a row, -1 for padding
   // neighbour lists
   uint16_t* nb_cnt;     // [n_in][16]: radial count per species [0..7], angular [8..15]
   int* nb_r;            // [n_in][cap_r] packed positions, species-sorted
