@@ -45,7 +45,7 @@ constexpr int kMaxStages = 4;
 constexpr unsigned kWaitLimit = 1u << 24;
 // dynamic shared memory limit: the 227 KB per block minus the kernel's static
 // shared memory (barriers, bias and w4 staging) and some headroom
-constexpr int kMaxDynSmem = 232448 - 8192;
+constexpr int kMaxDynSmem = 232448 - 16384;
 
 struct TcArgs {
   int N, K, n_tile, n_k, tmem_cols, stages, nets;
@@ -190,15 +190,6 @@ __device__ __forceinline__ void load_bf16x16(const __nv_bfloat16* src, float (&v
   }
 }
 
-__device__ __forceinline__ void load_f32x16(const float* src, float (&v)[16]) {
-  const float4* s = reinterpret_cast<const float4*>(src);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const float4 t = __ldg(s + q);
-    v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
-  }
-}
-
 struct Tile {
   int m0, n0, e, s;
 };
@@ -223,6 +214,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], done_bar;
   __shared__ uint32_t tmem_base_sh;
+  // per epilogue warp: the bias and output-layer weights of its columns of a tile
+  __shared__ __align__(16) float epi_sh[kEpiWarps][2][128];
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kStages = g.stages;
@@ -340,7 +333,29 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           }
         }
       }
+      // the bias (and output-layer weights) of this warp's columns, also fetched
+      // before the wait: lane l holds entries l + 32 i of the warp's 16-column chunks
+      float bpre[4] = {0.f, 0.f, 0.f, 0.f}, wpre[4] = {0.f, 0.f, 0.f, 0.f};
+      if (EPI == kEpiCelu || EPI == kEpiCeluDot) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int jj = lane + 32 * i, c0 = half * 16 + 32 * (jj >> 4), n = tl.n0 + c0 + (jj & 15);
+          if (c0 < g.n_tile && n < g.N) {
+            bpre[i] = __ldg(g.bias + tl.e * g.bias_e + tl.s * g.bias_s + n);
+            if (EPI == kEpiCeluDot) wpre[i] = __ldg(g.w4 + tl.e * g.w4_e + tl.s * g.w4_s + n);
+          }
+        }
+      }
       if (!mbar_wait(&tfull_bar[ab], (j >> 1) & 1, abort_flag)) break;
+      if (EPI == kEpiCelu || EPI == kEpiCeluDot) {
+        __syncwarp();   // the previous tile's reads of epi_sh are done
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          epi_sh[warp][0][lane + 32 * i] = bpre[i];
+          epi_sh[warp][1][lane + 32 * i] = wpre[i];
+        }
+        __syncwarp();
+      }
       tc_fence_after();
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * g.tmem_cols);
       float dot = 0.f;
@@ -354,9 +369,19 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
         if (n >= g.N) continue;
         if (EPI == kEpiCelu || EPI == kEpiCeluDot) {
           float b[16];
-          load_f32x16(g.bias + tl.e * g.bias_e + tl.s * g.bias_s + n, b);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 t4 = *reinterpret_cast<const float4*>(&epi_sh[warp][0][ci * 16 + 4 * k]);
+            b[4 * k] = t4.x; b[4 * k + 1] = t4.y; b[4 * k + 2] = t4.z; b[4 * k + 3] = t4.w;
+          }
           float w4[16];
-          if (EPI == kEpiCeluDot) load_f32x16(g.w4 + tl.e * g.w4_e + tl.s * g.w4_s + n, w4);
+          if (EPI == kEpiCeluDot) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float4 t4 = *reinterpret_cast<const float4*>(&epi_sh[warp][1][ci * 16 + 4 * k]);
+              w4[4 * k] = t4.x; w4[4 * k + 1] = t4.y; w4[4 * k + 2] = t4.z; w4[4 * k + 3] = t4.w;
+            }
+          }
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const float z = v[i] + b[i];

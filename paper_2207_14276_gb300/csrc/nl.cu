@@ -815,21 +815,34 @@ __global__ void __launch_bounds__(256) k_list_refresh(Ws ws, AevConst ac) {
       }
       const unsigned br = __ballot_sync(0xffffffffu, keep);
       const unsigned ba = __ballot_sync(0xffffffffu, ang);
-      if (keep) out_r[wr_r + cr + __popc(br & lanemask_lt())] = j;
-      if (ang) out_a[wr_a + ca + __popc(ba & lanemask_lt())] = j;
+      if (keep) {
+        const int at = wr_r + cr + __popc(br & lanemask_lt());
+        if (at < ws.cap_r) out_r[at] = j;
+      }
+      if (ang) {
+        const int at = wr_a + ca + __popc(ba & lanemask_lt());
+        if (at < ws.cap_a) out_a[at] = j;
+      }
       cr += __popc(br);
       ca += __popc(ba);
     }
+    // counts clamped so that the lists stay inside their capacity
     if (lane == 0) {
-      hdr[s] = (uint16_t)cr;
-      hdr[8 + s] = (uint16_t)ca;
+      hdr[s] = (uint16_t)max(0, min(cr, ws.cap_r - wr_r));
+      hdr[8 + s] = (uint16_t)max(0, min(ca, ws.cap_a - wr_a));
     }
     wr_r += cr;
     wr_a += ca;
     off = end;
   }
-  if (lane == 0)
+  if (lane == 0) {
     for (int s = ac.S; s < 8; ++s) { hdr[s] = 0; hdr[8 + s] = 0; }
+    if (wr_r > ws.cap_r || wr_a > ws.cap_a) {   // the call reports it; the retry grows the lists
+      atomicOr(ws.status, kStCapacity);
+      atomicMax(ws.status + 1, wr_r);
+      atomicMax(ws.status + 2, wr_a);
+    }
+  }
 }
 
 }  // namespace

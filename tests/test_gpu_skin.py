@@ -161,3 +161,17 @@ def test_force_vjp_between_skin_calls(torch_cuda):
     torch.cuda.synchronize()
     _same(fresh.energy_forces(d["coords"], d["species"]),
           kept.energy_forces(d["coords"], d["species"]))
+
+
+def test_dense_box_capacity_growth_with_skin(torch_cuda):
+    # three times liquid density: ~90 angular and ~300 radial neighbours, far
+    # above the initial list capacities; the first call overflows, reports it,
+    # and the repeated call (with grown lists) matches fresh lists
+    fresh, kept, _ = _pair(skin=0.5)
+    s = synth.water_box(1000, 18.0, 10, seed=36)
+    d = to_cuda(s)
+    _same(fresh.energy_forces(d["coords"], d["species"], d["box"]),
+          kept.energy_forces(d["coords"], d["species"], d["box"]), f_atol=1e-3)
+    x = d["coords"] + 0.01
+    _same(fresh.energy_forces(x, d["species"], d["box"]),
+          kept.energy_forces(x, d["species"], d["box"]), f_atol=1e-3)
