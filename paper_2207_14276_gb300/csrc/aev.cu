@@ -364,7 +364,14 @@ k_aev_bwd(Ws ws, AevConst ac) {
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
   const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
-  for (int f = lane; f < ac.S * kNR; f += 32) grad[f] = g_row[f];
+  // the radial dE/dG (S * 16 <= 128 values) is loaded now and stored after the
+  // neighbour gathers, so that the two latencies overlap
+  float gr[kMaxSpecies * kNR / 32];
+#pragma unroll
+  for (int i = 0; i < kMaxSpecies * kNR / 32; ++i) {
+    const int f = (int)lane + 32 * i;
+    gr[i] = f < ac.S * kNR ? g_row[f] : 0.f;
+  }
   // angular neighbours: unit vector and R, (f_c, f_c', 1/R, packed index)
   stage_list(H.off_a[ac.S], la, xi, d, ws.xyzq, lane,
              [&](int slot, int j, const Geo& g) {
@@ -378,6 +385,11 @@ k_aev_bwd(Ws ws, AevConst ac) {
                accz[slot] = 0.f;
              });
   const int na_tot = H.off_a[ac.S];
+#pragma unroll
+  for (int i = 0; i < kMaxSpecies * kNR / 32; ++i) {
+    const int f = (int)lane + 32 * i;
+    if (f < ac.S * kNR) grad[f] = gr[i];
+  }
   __syncwarp();
   float fi[3] = {0.f, 0.f, 0.f};
   float vir[9];
@@ -440,13 +452,26 @@ k_aev_bwd(Ws ws, AevConst ac) {
     carry += __shfl_sync(kFull, incl, 31);
     if (q0 + 32 >= np && lane == 0) bt_start[np] = carry;
   }
-  // every block's 32 dE/dG values (index 8a + z), transposed to [z][a] so that
-  // an angle section is one 16-byte load
+  __syncwarp();   // the block table is complete
+  // the 32 dE/dG values (index 8a + z) of every block that has triplets,
+  // transposed to [z][a] so that an angle section is one 16-byte load
   {
     const float* ga = g_row + ac.S * kNR;
     float* gf = reinterpret_cast<float*>(gall);
-    for (int f = lane; f < np * 32; f += 32)
-      gf[(f & ~31) + (f & 7) * 4 + ((f >> 3) & 3)] = ga[f];
+    unsigned live0 = __ballot_sync(kFull, (int)lane < np && bt_start[lane + 1] > bt_start[lane]);
+    const int q1 = 32 + (int)lane;
+    unsigned live1 = __ballot_sync(kFull, q1 < np && bt_start[q1 + 1] > bt_start[q1]);
+    const int tpos = (lane & 7) * 4 + (lane >> 3);
+    while (live0) {
+      const int q = __ffs(live0) - 1;
+      live0 &= live0 - 1;
+      gf[q * 32 + tpos] = ga[q * 32 + lane];
+    }
+    while (live1) {
+      const int q = 32 + __ffs(live1) - 1;
+      live1 &= live1 - 1;
+      gf[q * 32 + tpos] = ga[q * 32 + lane];
+    }
   }
   __syncwarp();
   const int T = bt_start[np];
