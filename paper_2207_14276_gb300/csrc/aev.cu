@@ -395,11 +395,15 @@ k_aev_bwd(Ws ws, AevConst ac) {
   float vir[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) vir[k] = 0.f;
-  // ---- radial edges, one lane per neighbour
+  // ---- radial edges, one lane per neighbour, numbered continuously over the
+  // species blocks of the list (a lane finds its neighbour's species block)
   const float cr_ = -ac.eta_r * kLog2e;
-  for (int s = 0; s < ac.S; ++s) {
-    const float* gs = grad + s * kNR;
-    for (int t = H.off_r[s] + lane; t < H.off_r[s + 1]; t += 32) {
+  const int nr_tot = H.off_r[ac.S];
+  int sr = 0;
+  for (int t = lane; t < nr_tot; t += 32) {
+    while (H.off_r[sr + 1] <= t) ++sr;
+    const float* gs = grad + sr * kNR;
+    {
       const int j = lr[t];
       const Geo g = pair_geo(xi, ws.xyzq[j], d);
       float fc, dfc;
