@@ -120,7 +120,11 @@ def stage_work(stage, spec, counts, n_atoms, precision):
 
     counts: mean radial neighbours n_r and angular neighbours n_a per atom.
     Bytes are compulsory DRAM traffic; FLOPs count the arithmetic the equations
-    require ('Roofline accounting')."""
+    require: per radial pair 16 shells x 5 FLOP forward / 8 backward (Gaussian,
+    cutoff and their derivatives), per angular (j, k) pair 200 forward / 330
+    backward (4 Gaussians, 8 factors (1 + cos(theta - theta_z))^32, the 32-term
+    contraction and, backward, the derivatives and two edge gradients), and
+    2 K N per row for a network layer."""
     D = spec.widths[0]
     E = spec.n_ensemble
     h1, h2, h3 = spec.widths[1:4]
