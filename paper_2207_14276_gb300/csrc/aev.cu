@@ -214,10 +214,11 @@ __device__ __forceinline__ void decode_pair_diag(int t, int same, int c, int cu,
   }
 }
 
-// one AEV element: the FP32 row and, for the tensor-core path, its BF16 copy
+// one AEV element: the FP32 row, or on the tensor-core path (Gh != null) only
+// the BF16 row its first layer reads
 __device__ __forceinline__ void put_g(float* G, uint16_t* Gh, int f, float v) {
-  G[f] = v;
   if (Gh) Gh[f] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  else G[f] = v;
 }
 
 // after the call lane l holds the warp sum of v[l]

@@ -1186,12 +1186,14 @@ const char* nnp_profile_stage_name(int i) {
 }
 
 // ---------------------------------------------------------------- diagnostics
-// Rows of the last call in batch input-atom order: which = 0 AEV, 1 dE/dG.
+// Rows of the last call in batch input-atom order: which = 0 AEV (on the BF16
+// path its BF16 copy, widened), 1 dE/dG.
 // out: device float [n_in_total, D]; rows of atoms outside the mask untouched.
 int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream) {
   if (!h || !h->arena || !out) return fail(NNP_ERR_ARG, "bad argument");
   const float* src = which == 0 ? h->ws.aev : h->ws.dEdG;
-  launch_gather_rows(h->ws, h->last_n_in, src, h->model->ac.Dp, h->model->ac.D, out,
+  const uint16_t* src_h = which == 0 ? h->ws.aev_h : nullptr;
+  launch_gather_rows(h->ws, h->last_n_in, src, src_h, h->model->ac.Dp, h->model->ac.D, out,
                      static_cast<cudaStream_t>(stream));
   CU_TRY(cudaGetLastError());
   return NNP_OK;

@@ -154,8 +154,8 @@ size_t aev_bwd_smem(const Ws& ws, int n_pairs = kMaxSpecies * (kMaxSpecies + 1) 
 // ---- finalize.cu
 void launch_finalize_e(const Ws& ws, int n_in, const float* e_row, int E, int e_row_net,
                        const double* ebias, cudaStream_t st);
-void launch_gather_rows(const Ws& ws, int n_in, const float* rows, int ld, int D, float* out,
-                        cudaStream_t st);
+void launch_gather_rows(const Ws& ws, int n_in, const float* rows, const uint16_t* rows_h, int ld,
+                        int D, float* out, cudaStream_t st);
 void launch_gather_nbrs(const Ws& ws, int n_in, int angular, int cap_out, int* out,
                         cudaStream_t st);
 
