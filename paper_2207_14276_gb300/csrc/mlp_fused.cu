@@ -13,20 +13,16 @@
 // CELU'(Z) is rebuilt from the stored activation: 1 for H > 0, else 1 + H/alpha
 // (CELU(z) = alpha (exp(z/alpha) - 1) on the negative branch).
 //
-// Each phase is a 32 x N block product on 8 warps: warp w owns rows
-// 8 (w % 4)..+7 of the tile and one of two column halves (w / 4; the first half
-// is the smallest multiple of 32 that is at least N/2), so every row of the
-// tile is worked on by two warps and a CTA keeps 8 warps busy.  A thread keeps
-// an 8 x C accumulator tile; inside its half a lane owns 4 consecutive columns
-// per 128-wide group (then 2 of a 64-wide and 1 of a 32-wide remainder), so a
-// K-slice row of the weights is read with 16-byte loads, and the activation
-// operand is a broadcast 16-byte load of 4 consecutive k of one row.  Weight
-// K-slices (k-major, from the transposed or plain layout as the phase needs)
-// stream through a 4-stage cp.async ring in shared memory, three slices ahead of
-// the one in use: a tile's phases are a chain of ~90 short slices, and one L2
-// round trip per slice would otherwise set the kernel's duration.
-#include <type_traits>
-
+// Each phase is a 32 x N block product on 8 warps: warp w owns rows 4w..4w+3 of
+// the tile and all N columns, a thread an accumulator tile of 4 rows x N/32
+// columns.  A lane owns 4 consecutive columns per 128-wide group (then 2 of a
+// 64-wide and 1 of a 32-wide remainder), so that a K-slice row of the weights is
+// read with 16-byte loads, and the activation operand is a broadcast 16-byte load
+// of 4 consecutive k of one row.  Weight K-slices (k-major, from the transposed
+// or plain layout as the phase needs) stream through a cp.async ring in shared
+// memory, two slices ahead of the one in use: a tile's phases are a chain of ~45
+// slices, and one L2 round trip per slice would otherwise set the kernel's
+// duration.
 #include "mlp.cuh"
 
 namespace nnp {
@@ -123,40 +119,23 @@ struct Cols {
   }
 };
 
-// the two column halves of an N-wide phase
-template <int N>
-struct Halves {
-  static constexpr int N0 = 32 * ((N + 63) / 64);
-  static constexpr int N1 = N - N0;
-  static constexpr int C = N0 / 32;   // accumulator columns (the wider half)
-};
+constexpr int RPW = 4;   // rows per warp: warp w owns rows 4w..4w+3 of the tile
 
-template <int V>
-using IC = std::integral_constant<int, V>;
-
-// f(IC<width>, first column) for the calling warp's column half
-template <int N, class F>
-__device__ __forceinline__ void on_half(int h, F f) {
-  if (h == 0) f(IC<Halves<N>::N0>{}, 0);
-  else if (Halves<N>::N1 > 0) f(IC<Halves<N>::N1>{}, Halves<N>::N0);
-}
-
-// acc[r][c] = sum_k A[row r][k] * B[k][n0 + half column c] over k < K (K a multiple
-// of KS), rows 8 (w % 4) + r.  A: shared [32][lda] (AG = false) or global rows
-// Ag[row][ldg] starting at the tile (AG = true, staged through As).  B: global
-// [K][ldb]; columns n0 + j >= Nv read as zero.
+// acc[r][c] = sum_k A[row 4w + r][k] * B[k][n0 + col(c)] over k < K (K a multiple
+// of KS).  A: shared [32][lda] (AG = false) or global rows Ag[row][ldg] starting
+// at the tile (AG = true, staged through As).  B: global [K][ldb]; columns
+// n0 + j >= Nv read as zero.
 template <int N, bool AG>
-__device__ __forceinline__ void block_gemm(float (&acc)[8][Halves<N>::C], const float* A, int lda,
+__device__ __forceinline__ void block_gemm(float (&acc)[RPW][N / 32], const float* A, int lda,
                                            const float* Ag, int ldg, float* As, int K,
                                            const float* B, int ldb, int n0, int Nv, float* Bs) {
-  constexpr int CM = Halves<N>::C;
+  constexpr int C = N / 32;
   constexpr int kVec = KS * N / 4;  // float4s per B slice
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int rg = w & 3, h = w >> 2;
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
+  for (int r = 0; r < RPW; ++r)
 #pragma unroll
-    for (int c = 0; c < CM; ++c) acc[r][c] = 0.f;
+    for (int c = 0; c < C; ++c) acc[r][c] = 0.f;
   auto issue = [&](int k0, int buf) {
     float* bs = Bs + buf * KS * N;
 #pragma unroll
@@ -191,30 +170,26 @@ __device__ __forceinline__ void block_gemm(float (&acc)[8][Halves<N>::C], const 
     if (sl + NS - 1 < n_slices) issue((sl + NS - 1) * KS, (sl + NS - 1) % NS);
     else cp_async_commit();
     const float* bs = Bs + buf * KS * N;
-    const float* arow = AG ? As + buf * kRows * (KS + 4) + (rg * 8) * (KS + 4)
-                           : A + (size_t)(rg * 8) * lda + sl * KS;
+    const float* arow = AG ? As + buf * kRows * (KS + 4) + (w * RPW) * (KS + 4)
+                           : A + (size_t)(w * RPW) * lda + sl * KS;
     const int lds = AG ? KS + 4 : lda;
-    on_half<N>(h, [&](auto nw, int col0) {
-      constexpr int NW = decltype(nw)::value;
-      constexpr int C = NW / 32;
 #pragma unroll
-      for (int kk = 0; kk < KS; kk += 4) {
-        float4 a[8];
+    for (int kk = 0; kk < KS; kk += 4) {
+      float4 a[RPW];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) a[r] = *reinterpret_cast<const float4*>(arow + r * lds + kk);
+      for (int r = 0; r < RPW; ++r) a[r] = *reinterpret_cast<const float4*>(arow + r * lds + kk);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float b[CM];
-          Cols<NW>::load(b, bs + (kk + q) * N + col0, lane);
+      for (int q = 0; q < 4; ++q) {
+        float b[C];
+        Cols<N>::load(b, bs + (kk + q) * N, lane);
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const float av = comp(a[r], q);
+        for (int r = 0; r < RPW; ++r) {
+          const float av = comp(a[r], q);
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[r][c] = fmaf(av, b[c], acc[r][c]);
-          }
+          for (int c = 0; c < C; ++c) acc[r][c] = fmaf(av, b[c], acc[r][c]);
         }
       }
-    });
+    }
   }
   cp_async_wait<0>();   // only empty groups remain; none may straddle the next phase
   __syncthreads();  // every warp is done with Bs/As (and with A) before they are reused
@@ -228,46 +203,39 @@ struct Smem {
   static constexpr int H1 = 0, H2 = H1 + kRows * ld1, H3 = H2 + kRows * ld2;
   static constexpr int As = H2;  // the AEV stage of L1 lives where H2/H3 go later
   static constexpr int Bs = H3 + kRows * ld3;
-  static constexpr int Dot = Bs + NS * KS * cmax(cmax(N1, N2), cmax(N3, kOutChunk));  // [2][32]
-  static constexpr int floats = Dot + 2 * kRows;
+  static constexpr int floats = Bs + NS * KS * cmax(cmax(N1, N2), cmax(N3, kOutChunk));
   static_assert(NS * kRows * (KS + 4) <= kRows * (ld2 + ld3), "A stage overlay");
 };
 
-// L1/L2 epilogue: H[row][col] = CELU(acc + b[col]) for this warp's half
-template <int N, class Acc>
-__device__ __forceinline__ void store_celu(Acc& acc, const float* bias, float* H, int ld, int h,
-                                           int rg, int lane, float alpha, float inv_alpha) {
-  on_half<N>(h, [&](auto nw, int col0) {
-    constexpr int NW = decltype(nw)::value;
-    constexpr int CM = Halves<N>::C;
-    float b[CM];
-    Cols<NW>::load(b, bias + col0, lane);
+// L1/L2 epilogue: H[row][col] = CELU(acc + b[col])
+template <int N>
+__device__ __forceinline__ void store_celu(float (&acc)[RPW][N / 32], const float* bias, float* H,
+                                           int ld, int w, int lane, float alpha, float inv_alpha) {
+  constexpr int C = N / 32;
+  float b[C];
+  Cols<N>::load(b, bias, lane);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+  for (int r = 0; r < RPW; ++r) {
 #pragma unroll
-      for (int c = 0; c < NW / 32; ++c) acc[r][c] = celu_f(acc[r][c] + b[c], alpha, inv_alpha);
-      Cols<NW>::store(acc[r], H + (rg * 8 + r) * ld + col0, lane);
-    }
-  });
+    for (int c = 0; c < C; ++c) acc[r][c] = celu_f(acc[r][c] + b[c], alpha, inv_alpha);
+    Cols<N>::store(acc[r], H + (w * RPW + r) * ld, lane);
+  }
 }
 
 // B3/B2 epilogue: H[row][col] = acc * CELU'(z) rebuilt from the stored H
-template <int N, class Acc>
-__device__ __forceinline__ void store_delta(Acc& acc, float* H, int ld, int h, int rg, int lane,
-                                            float inv_alpha) {
-  on_half<N>(h, [&](auto nw, int col0) {
-    constexpr int NW = decltype(nw)::value;
-    constexpr int CM = Halves<N>::C;
+template <int N>
+__device__ __forceinline__ void store_delta(float (&acc)[RPW][N / 32], float* H, int ld, int w,
+                                            int lane, float inv_alpha) {
+  constexpr int C = N / 32;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      float* row = H + (rg * 8 + r) * ld + col0;
-      float hv[CM];
-      Cols<NW>::load(hv, row, lane);
+  for (int r = 0; r < RPW; ++r) {
+    float* row = H + (w * RPW + r) * ld;
+    float hv[C];
+    Cols<N>::load(hv, row, lane);
 #pragma unroll
-      for (int c = 0; c < NW / 32; ++c) acc[r][c] *= celu_d_of_h(hv[c], inv_alpha);
-      Cols<NW>::store(acc[r], row, lane);
-    }
-  });
+    for (int c = 0; c < C; ++c) acc[r][c] *= celu_d_of_h(hv[c], inv_alpha);
+    Cols<N>::store(acc[r], row, lane);
+  }
 }
 
 template <int N1, int N2, int N3, int MINB>
@@ -286,90 +254,78 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mlp_fused(FusedArgs a) {
   float* H3 = smf + L::H3;  // [32][ld3]
   float* As = smf + L::As;  // [NS][32][KS+4], during L1 only
   float* Bs = smf + L::Bs;  // [NS][KS][N]
-  float* dot_sh = smf + L::Dot;  // [2 halves][32 rows]
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, rg = w & 3, h = w >> 2;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float alpha = a.alpha, inv_alpha = 1.f / a.alpha;
 
   // ---- L1
   {
-    float acc[8][Halves<N1>::C];
+    float acc[RPW][N1 / 32];
     block_gemm<N1, true>(acc, nullptr, 0, a.G + (size_t)m0 * Dp, Dp, As, Dp,
                          a.W1T + s * a.sW1T, N1, 0, N1, Bs);
-    store_celu<N1>(acc, a.b1 + s * a.sb1, H1, L::ld1, h, rg, lane, alpha, inv_alpha);
+    store_celu<N1>(acc, a.b1 + s * a.sb1, H1, L::ld1, w, lane, alpha, inv_alpha);
   }
   __syncthreads();
   // ---- L2
   {
-    float acc[8][Halves<N2>::C];
+    float acc[RPW][N2 / 32];
     block_gemm<N2, false>(acc, H1, L::ld1, nullptr, 0, nullptr, N1, a.W2T + s * a.sW2, N2, 0, N2, Bs);
-    store_celu<N2>(acc, a.b2 + s * a.sb2, H2, L::ld2, h, rg, lane, alpha, inv_alpha);
+    store_celu<N2>(acc, a.b2 + s * a.sb2, H2, L::ld2, w, lane, alpha, inv_alpha);
   }
   __syncthreads();
   // ---- L3 and the output layer: e = H3 . w4, D3 = w4 * CELU'(Z3)
   {
-    constexpr int CM = Halves<N3>::C;
-    float acc[8][CM];
+    constexpr int C = N3 / 32;
+    float acc[RPW][C];
     block_gemm<N3, false>(acc, H2, L::ld2, nullptr, 0, nullptr, N2, a.W3T + s * a.sW3, N3, 0, N3, Bs);
-    float dot[8];
+    float b[C], w4[C], dot[RPW];
+    Cols<N3>::load(b, a.b3 + s * a.sb3, lane);
+    Cols<N3>::load(w4, a.w4 + s * a.sw4, lane);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) dot[r] = 0.f;
-    on_half<N3>(h, [&](auto nw, int col0) {
-      constexpr int NW = decltype(nw)::value;
-      float b[CM], w4[CM];
-      Cols<NW>::load(b, a.b3 + s * a.sb3 + col0, lane);
-      Cols<NW>::load(w4, a.w4 + s * a.sw4 + col0, lane);
+    for (int r = 0; r < RPW; ++r) {
+      dot[r] = 0.f;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-#pragma unroll
-        for (int c = 0; c < NW / 32; ++c) {
-          const float z = acc[r][c] + b[c];
-          dot[r] = fmaf(celu_f(z, alpha, inv_alpha), w4[c], dot[r]);
-          acc[r][c] = w4[c] * (z > 0.f ? 1.f : __expf(z * inv_alpha));
-        }
-        Cols<NW>::store(acc[r], H3 + (rg * 8 + r) * L::ld3 + col0, lane);
+      for (int c = 0; c < C; ++c) {
+        const float z = acc[r][c] + b[c];
+        dot[r] = fmaf(celu_f(z, alpha, inv_alpha), w4[c], dot[r]);
+        acc[r][c] = w4[c] * (z > 0.f ? 1.f : __expf(z * inv_alpha));
       }
-    });
+      Cols<N3>::store(acc[r], H3 + (w * RPW + r) * L::ld3, lane);
+    }
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < RPW; ++r)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) dot[r] += __shfl_xor_sync(0xffffffffu, dot[r], o);
-    if (lane < 8) {
+    if (lane < RPW) {
       float v = dot[0];
 #pragma unroll
-      for (int r = 1; r < 8; ++r) v = lane == r ? dot[r] : v;
-      dot_sh[h * kRows + rg * 8 + lane] = v;
+      for (int r = 1; r < RPW; ++r) v = lane == r ? dot[r] : v;
+      a.e_row[m0 + w * RPW + lane] = v;
     }
-    __syncthreads();
-    // the two halves' partial dot products, added in a fixed order
-    if (threadIdx.x < kRows) a.e_row[m0 + threadIdx.x] = dot_sh[threadIdx.x] + dot_sh[kRows + threadIdx.x];
   }
   if (a.energy_only) return;
   __syncthreads();
   // ---- B3: delta2 = (D3 W3) * CELU'(Z2), over H2
   {
-    float acc[8][Halves<N2>::C];
+    float acc[RPW][N2 / 32];
     block_gemm<N2, false>(acc, H3, L::ld3, nullptr, 0, nullptr, N3, a.W3 + s * a.sW3, N2, 0, N2, Bs);
-    store_delta<N2>(acc, H2, L::ld2, h, rg, lane, inv_alpha);
+    store_delta<N2>(acc, H2, L::ld2, w, lane, inv_alpha);
   }
   __syncthreads();
   // ---- B2: delta1 = (delta2 W2) * CELU'(Z1), over H1
   {
-    float acc[8][Halves<N1>::C];
+    float acc[RPW][N1 / 32];
     block_gemm<N1, false>(acc, H2, L::ld2, nullptr, 0, nullptr, N2, a.W2 + s * a.sW2, N1, 0, N1, Bs);
-    store_delta<N1>(acc, H1, L::ld1, h, rg, lane, inv_alpha);
+    store_delta<N1>(acc, H1, L::ld1, w, lane, inv_alpha);
   }
   __syncthreads();
   // ---- B1: dE/dG = delta1 W1, 128 columns per pass (Dp a multiple of 128)
   const float* W1 = a.W1 + s * a.sW1;
   for (int n0 = 0; n0 < Dp; n0 += kOutChunk) {
-    float acc[8][Halves<kOutChunk>::C];
+    float acc[RPW][kOutChunk / 32];
     block_gemm<kOutChunk, false>(acc, H1, L::ld1, nullptr, 0, nullptr, N1, W1, Dp, n0, Dp, Bs);
-    on_half<kOutChunk>(h, [&](auto nw, int col0) {
-      constexpr int NW = decltype(nw)::value;
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-        Cols<NW>::store(acc[r], a.dEdG + (size_t)(m0 + rg * 8 + r) * Dp + n0 + col0, lane);
-    });
+    for (int r = 0; r < RPW; ++r)
+      Cols<kOutChunk>::store(acc[r], a.dEdG + (size_t)(m0 + w * RPW + r) * Dp + n0, lane);
   }
 }
 
