@@ -309,3 +309,22 @@ def test_energy_only_matches_full_evaluation(torch_cuda, precision):
         e0, e1 = float(a["energy"].cpu()[0]), float(b["energy"].cpu()[0])
         assert e1 == pytest.approx(e0, rel=1e-6, abs=1e-6)
         assert "forces" not in b
+
+
+def test_golden_closed_form_aev_values(torch_cuda):
+    # the kernels' AEV (FP32) against the hand-derived values of Eqs. 3-5 in
+    # tests/golden/aev_closed_forms.txt, not only against the oracle
+    torch = torch_cuda
+    from paper_2207_14276_gb300 import Potential
+    from tests._golden import closed_form_cases
+    for c in closed_form_cases():
+        pot = Potential(c["spec"], synth.make_weights(c["spec"], 7))
+        x = torch.tensor(c["coords"], dtype=torch.float32, device="cuda")
+        sp = torch.tensor(c["species"], device="cuda")
+        pot.energy_forces(x, sp)
+        G = pot.debug_rows(0, len(c["species"])).cpu().numpy().astype(np.float64)
+        for i, f, v in c["expect"]:
+            assert abs(G[i, f] - v) <= 2e-5 * abs(v) + 1e-6, (c["name"], i, f, G[i, f], v)
+        for i, a, b in c["zero"]:
+            assert np.all(np.abs(G[i, a:b + 1]) <= 1e-6), (c["name"], i, a, b)
+        pot.close()

@@ -409,3 +409,32 @@ def test_sample_matches_full_evaluation():
     np.testing.assert_allclose(smp["atom_energies"], full["atom_energies"][idx], rtol=1e-12)
     np.testing.assert_allclose(smp["forces"], full["forces"][idx], atol=1e-13)
     np.testing.assert_allclose(smp["aev"], full["aev"][idx], atol=1e-13)
+
+
+# ------------------------------------------------------------------ golden fixtures
+def test_golden_closed_form_aev_values():
+    # hand-derived values of Eqs. 3-5 at special geometries (tests/golden/aev_closed_forms.txt)
+    from tests._golden import closed_form_cases
+    cases = closed_form_cases()
+    assert len(cases) == 4
+    for c in cases:
+        m = oracle.Model(c["spec"], synth.make_weights(c["spec"], 7))
+        G = m.energy_forces(c["coords"], c["species"], want_aev=True)["aev"]
+        for i, f, v in c["expect"]:
+            assert G[i, f] == pytest.approx(v, rel=1e-12, abs=1e-15), (c["name"], i, f)
+        for i, a, b in c["zero"]:
+            assert np.all(np.abs(G[i, a:b + 1]) <= 1e-15), (c["name"], i, a, b)
+
+
+def test_golden_paper_constants():
+    # the cutoff radius and the sub-AEV counts the paper prints (tests/golden/paper_constants.txt)
+    from tests._golden import paper_constants
+    k = paper_constants()
+    (rc,), = k["rc_r"]
+    for kind in ("ani4", "ani7", "ani7x8"):
+        assert synth.model_spec(kind).aev.rc_r == rc
+    for N, n_rad, n_ang in k["sub_aevs"]:
+        spec, m = small_model("ani4" if N == 4 else "ani7")
+        p = spec.aev
+        assert p.n_species == N
+        assert m.D == n_rad * len(p.shf_r) + n_ang * len(p.shf_a) * len(p.shf_z)
