@@ -80,7 +80,8 @@ struct nnp_handle {
   bool dirty = true;  // capacities changed: re-carve before the next call
   Ws ws{};
   MlpBufs mb{};
-  int* status_host = nullptr;  // pinned [4]
+  int* status_host = nullptr;  // pinned: [4] status words, then out_host
+  double* out_host = nullptr;  // pinned [10]: energy and virial of a host-buffer call
   int last_launches = 0;
   int last_n_in = 0;
   void* tc_state = nullptr;
@@ -695,6 +696,16 @@ extern "C" {
 
 const char* nnp_last_error(void) { return g_err.c_str(); }
 
+namespace {
+bool alloc_host_words(nnp_handle* h) {
+  void* p = nullptr;
+  if (cudaMallocHost(&p, 16 + 10 * sizeof(double)) != cudaSuccess) return false;
+  h->status_host = static_cast<int*>(p);
+  h->out_host = reinterpret_cast<double*>(static_cast<char*>(p) + 16);
+  return true;
+}
+}  // namespace
+
 int nnp_create(const nnp_species_t* species, const nnp_aev_params_t* aev,
                const nnp_weights_t* weights, int precision, size_t hbm_budget_bytes,
                nnp_handle** out) {
@@ -707,7 +718,7 @@ int nnp_create(const nnp_species_t* species, const nnp_aev_params_t* aev,
   nnp_handle* h = new nnp_handle;
   h->model = m.release();
   h->budget = hbm_budget_bytes;
-  if (cudaMallocHost(&h->status_host, 4 * sizeof(int)) != cudaSuccess) {
+  if (!alloc_host_words(h)) {
     nnp_destroy(h);
     return fail(NNP_ERR_CUDA, "cudaMallocHost failed");
   }
@@ -723,7 +734,7 @@ int nnp_clone(const nnp_handle* src, nnp_handle** out) {
   h->budget = src->budget;
   h->cap_r = src->cap_r;
   h->cap_a = src->cap_a;
-  if (cudaMallocHost(&h->status_host, 4 * sizeof(int)) != cudaSuccess) {
+  if (!alloc_host_words(h)) {
     nnp_destroy(h);
     return fail(NNP_ERR_CUDA, "cudaMallocHost failed");
   }
@@ -790,14 +801,18 @@ int nnp_energy_forces_batch(nnp_handle* h, int n_sys, const nnp_system_t* system
   return run_batch(h, n_sys, systems, static_cast<cudaStream_t>(stream));
 }
 
-int nnp_sync_status(nnp_handle* h, void* stream) {
-  g_err.clear();
-  if (!h) return fail(NNP_ERR_ARG, "null handle");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  CU_TRY(cudaStreamSynchronize(st));
-  if (!h->arena) return NNP_OK;
-  CU_TRY(cudaMemcpy(h->status_host, h->ws.status, 4 * sizeof(int), cudaMemcpyDeviceToHost));
-  CU_TRY(cudaMemset(h->ws.status, 0, 4 * sizeof(int)));
+namespace {
+
+// enqueue the read-back and reset of the device status word on st
+cudaError_t enqueue_status_read(nnp_handle* h, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(h->status_host, h->ws.status, 4 * sizeof(int),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws.status, 0, 4 * sizeof(int), st);
+  return e;
+}
+
+// the outcome of the status word read back by enqueue_status_read (after a sync)
+int status_result(nnp_handle* h) {
   const int f = h->status_host[0];
   if (f & kStSpecies) return fail(NNP_ERR_SPECIES, "species index out of range");
   if (f & kStNonFinite) return fail(NNP_ERR_NONFINITE, "non-finite coordinate in the ML region");
@@ -816,6 +831,17 @@ int nnp_sync_status(nnp_handle* h, void* stream) {
                                       "); repeat the call");
   }
   return NNP_OK;
+}
+
+}  // namespace
+
+int nnp_sync_status(nnp_handle* h, void* stream) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (h->arena) CU_TRY(enqueue_status_read(h, st));
+  CU_TRY(cudaStreamSynchronize(st));
+  return h->arena ? status_result(h) : NNP_OK;
 }
 
 int nnp_energy_forces_host(nnp_handle* h, int64_t n, const float* coords_h,
@@ -849,10 +875,17 @@ int nnp_energy_forces_host(nnp_handle* h, int64_t n, const float* coords_h,
     int rc = nnp_energy_forces(h, n, d_xyz, d_sp, box_host, mask_h ? d_mask : nullptr, d_e, d_f,
                                virial_h ? d_v : nullptr, st);
     if (rc) return rc;
-    CU_TRY(cudaMemcpyAsync(energy_h, d_e, sizeof(double), cudaMemcpyDeviceToHost, st));
+    // energy and virial land in pinned words and the status read joins the same
+    // stream, so that the call synchronises once
+    CU_TRY(cudaMemcpyAsync(h->out_host, d_e, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (n > 0) CU_TRY(cudaMemcpyAsync(forces_h, d_f, (size_t)n * 12, cudaMemcpyDeviceToHost, st));
-    if (virial_h) CU_TRY(cudaMemcpyAsync(virial_h, d_v, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (virial_h)
+      CU_TRY(cudaMemcpyAsync(h->out_host + 1, d_v, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
     rc = nnp_sync_status(h, st);
+    if (rc == NNP_OK) {
+      *energy_h = h->out_host[0];
+      if (virial_h) std::memcpy(virial_h, h->out_host + 1, 9 * sizeof(double));
+    }
     if (rc != NNP_ERR_CAPACITY) return rc;
   }
   return fail(NNP_ERR_CAPACITY, "neighbour list over capacity after one retry");

@@ -250,11 +250,28 @@ def test_capacity_overflow_grows_and_retries(torch_cuda):
 
 def test_host_entry_point(torch_cuda):
     pot, orc = make("ani4")
+    # lists too small for liquid water: the first call overflows and the entry
+    # point repeats it with grown lists before it returns
+    pot.reserve(400, 1, 32, 32)
     s = synth.water_box(300, 20.5, 7, seed=14)
     E, F = pot.energy_forces_host(s.coords, s.species, s.box)
     ref = orc.energy_forces(s.coords, s.species, s.box)
     assert abs(E - ref["energy"]) <= E_TOL
-    assert force_errors(F, ref["forces"])[0] <= 1e-4 * np.sqrt(np.mean(ref["forces"] ** 2))
+    f_rms = np.sqrt(np.mean(ref["forces"] ** 2))
+    assert force_errors(F, ref["forces"])[0] <= 1e-4 * f_rms
+    # repeated calls (the second one a graph replay), with the virial
+    for _ in range(3):
+        E2, F2, V2 = pot.energy_forces_host(s.coords, s.species, s.box, virial=True)
+        assert abs(E2 - ref["energy"]) <= E_TOL
+        assert force_errors(F2, ref["forces"])[0] <= 1e-4 * f_rms
+        np.testing.assert_allclose(V2, ref["virial"], atol=1e-4 * np.abs(ref["virial"]).max() + 1e-6)
+    # an out-of-range species is reported, and the handle keeps working
+    bad = s.species.copy()
+    bad[5] = 9
+    with pytest.raises(RuntimeError):
+        pot.energy_forces_host(s.coords, bad, s.box)
+    E3, _ = pot.energy_forces_host(s.coords, s.species, s.box)
+    assert abs(E3 - ref["energy"]) <= E_TOL
 
 
 def test_solvated100k_sampled(torch_cuda):
