@@ -354,11 +354,8 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
     carve(h, static_cast<char*>(h->arena));
     return fail(NNP_ERR_OOM, "work arena of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
   }
-  int* saved_status = nullptr;
   if (h->arena) {
     CU_TRY(cudaDeviceSynchronize());
-    saved_status = h->ws.status;
-    (void)saved_status;
     if (h->tc_state) { mlp_tc_release(h->tc_state); h->tc_state = nullptr; }
     cudaFree(h->arena);
     h->arena = nullptr;
