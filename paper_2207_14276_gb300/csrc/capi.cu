@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -620,7 +621,9 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
     const int skin_mode = ws.skin_state ? (h->lists_valid ? 1 : 2) : 0;
     put(&skin_mode, sizeof(skin_mode));
     put(&h->skin, sizeof(h->skin));
-    for (const auto& bp : chunks) put(&bp, sizeof(BatchParams));
+    // the kernels read only the first n_sys descriptors of a chunk
+    for (const auto& bp : chunks)
+      put(&bp, offsetof(BatchParams, sys) + (size_t)bp.n_sys * sizeof(SysIn));
     if (h->gexec && sig == h->gsig) {
       CU_TRY(cudaGraphLaunch(h->gexec, st));
       h->last_launches = h->last_launches_graph;

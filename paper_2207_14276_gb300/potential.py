@@ -201,7 +201,7 @@ class Potential:
         F = out_forces if out_forces is not None else np.empty((n, 3), dtype=np.float32)
         V = np.zeros(9, dtype=np.float64) if virial else None
         box_arr = None if box is None else (ctypes.c_double * 3)(*[float(b) for b in box])
-        vp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+        vp = lambda a: None if a is None else a.ctypes.data   # plain address
         check(lib().nnp_energy_forces_host(self._h, n, vp(x), vp(sp), box_arr, vp(m), vp(E),
                                            vp(F), vp(V)))
         return (E[0], F, V.reshape(3, 3)) if virial else (E[0], F)
