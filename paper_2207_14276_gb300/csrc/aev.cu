@@ -28,6 +28,8 @@
 //   one warp-reduced atomic.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "nnp_internal.cuh"
 
 namespace nnp {
@@ -135,11 +137,25 @@ __device__ __forceinline__ float sin_theta(const float4& a, const float4& b, flo
   return sqrt_approx(fmaf(1.f - k * k, chat * chat, s2));
 }
 
-// float4s of shared memory per warp of the backward kernel: neighbour geometry,
-// cutoffs and accumulators (3 cap_a), radial dE/dG (32), the angular blocks'
-// dE/dG (8 per block) and the block table (5 ints per block + 1)
-__host__ __device__ constexpr int aev_bwd_warp_f4(int cap_a, int n_pairs) {
-  return 3 * cap_a + 32 + 8 * n_pairs + (5 * n_pairs + 1 + 3) / 4;
+// float4s of shared memory per warp of the backward kernel: neighbour geometry
+// and cutoffs (2 cap_a), `copies` copies of the x/y/z accumulators (3 cap_a
+// copies floats), radial dE/dG (32), the angular blocks' dE/dG (8 per block)
+// and the block table (5 ints per block + 1)
+__host__ __device__ constexpr int aev_bwd_warp_f4(int cap_a, int n_pairs, int copies) {
+  return 2 * cap_a + (3 * cap_a * copies + 3) / 4 + 32 + 8 * n_pairs + (5 * n_pairs + 1 + 3) / 4;
+}
+
+// Copies of the per-neighbour angular accumulators.  The lanes of one 32-triplet
+// window often add into the same neighbour (a block with few neighbours of a
+// species repeats them across the window), and shared-memory float atomics on
+// one address serialise; with R copies lane l adds into copy l mod R, so only
+// lanes equal mod R can collide.  R = 4, 2 or 1: the largest that keeps the
+// CTA within the shared memory of four CTAs per SM.
+constexpr int kBwdCtaSmem = 56 * 1024;
+int aev_bwd_copies(int cap_a, int n_pairs) {
+  for (int r = 4; r > 1; r >>= 1)
+    if ((size_t)kWarps * aev_bwd_warp_f4(cap_a, n_pairs, r) * sizeof(float4) <= kBwdCtaSmem) return r;
+  return 1;
 }
 
 // per-warp header: species offsets/counts of the radial and angular lists
@@ -336,7 +352,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
 
 template <int ZETA, bool VIR>
 __global__ void __launch_bounds__(kWarps * 32, 4)
-k_aev_bwd(Ws ws, AevConst ac) {
+k_aev_bwd(Ws ws, AevConst ac, int log_r) {
   constexpr bool want_virial = VIR;
   extern __shared__ float4 sm4[];
   __shared__ ListHdr hdrs[kWarps];
@@ -344,16 +360,18 @@ k_aev_bwd(Ws ws, AevConst ac) {
   const unsigned lane = threadIdx.x & 31;
   const int p = blockIdx.x * kWarps + w;
   if (p >= ws.totals[0]) return;
-  float4* angv = sm4 + (size_t)w * aev_bwd_warp_f4(ws.cap_a, ac.n_pairs);
+  const int n_copy = 1 << log_r;
+  float4* angv = sm4 + (size_t)w * aev_bwd_warp_f4(ws.cap_a, ac.n_pairs, n_copy);
   float4* angf = angv + ws.cap_a;          // fc, dfc
-  // dE/du per angular neighbour as three arrays (x, y, z): lanes adding into
-  // consecutive neighbours hit consecutive banks
+  // dE/du per angular neighbour as three arrays (x, y, z), each [neighbour][copy]:
+  // lane l adds into copy l mod n_copy, and lanes adding into consecutive
+  // neighbours hit consecutive banks
   float* accx = reinterpret_cast<float*>(angf + ws.cap_a);
-  float* accy = accx + ws.cap_a;
-  float* accz = accy + ws.cap_a;
-  float4* acc3 = angf + ws.cap_a;          // the region of the three arrays
-  float* grad = reinterpret_cast<float*>(acc3 + ws.cap_a);  // S*16 radial dE/dG
-  float4* gall = acc3 + ws.cap_a + 32;     // every angular block's dE/dG, [block][z][a]
+  float* accy = accx + ws.cap_a * n_copy;
+  float* accz = accy + ws.cap_a * n_copy;
+  float4* past_acc = angf + ws.cap_a + (3 * ws.cap_a * n_copy + 3) / 4;
+  float* grad = reinterpret_cast<float*>(past_acc);  // S*16 radial dE/dG
+  float4* gall = past_acc + 32;            // every angular block's dE/dG, [block][z][a]
   int4* bt_geo = reinterpret_cast<int4*>(gall + 8 * ac.n_pairs);     // [n_pairs]
   int* bt_start = reinterpret_cast<int*>(bt_geo + ac.n_pairs);       // [n_pairs + 1]
   ListHdr& H = hdrs[w];
@@ -381,11 +399,13 @@ k_aev_bwd(Ws ws, AevConst ac) {
                float fc, dfc;
                fcut_both(g.r, ac.rc_a, inv_rc_a, &fc, &dfc);
                angf[slot] = make_float4(fc, dfc, inv, __int_as_float(j));
-               accx[slot] = 0.f;
-               accy[slot] = 0.f;
-               accz[slot] = 0.f;
              });
   const int na_tot = H.off_a[ac.S];
+  for (int i = lane; i < (na_tot << log_r); i += 32) {
+    accx[i] = 0.f;
+    accy[i] = 0.f;
+    accz[i] = 0.f;
+  }
 #pragma unroll
   for (int i = 0; i < kMaxSpecies * kNR / 32; ++i) {
     const int f = (int)lane + 32 * i;
@@ -545,17 +565,25 @@ k_aev_bwd(Ws ws, AevConst ac) {
         const float sj = dEdchat * fj4.z, sk = dEdchat * fk4.z;
         const float rj = 0.5f * tR + tf * fj4.y * fk4.x;
         const float rk = 0.5f * tR + tf * fj4.x * fk4.y;
-        atomicAdd(accx + tj, sj * (vk.x - chat * vj.x) + rj * vj.x);
-        atomicAdd(accy + tj, sj * (vk.y - chat * vj.y) + rj * vj.y);
-        atomicAdd(accz + tj, sj * (vk.z - chat * vj.z) + rj * vj.z);
-        atomicAdd(accx + tk, sk * (vj.x - chat * vk.x) + rk * vk.x);
-        atomicAdd(accy + tk, sk * (vj.y - chat * vk.y) + rk * vk.y);
-        atomicAdd(accz + tk, sk * (vj.z - chat * vk.z) + rk * vk.z);
+        const int cp = (int)lane & (n_copy - 1);
+        const int aj = (tj << log_r) | cp, ak = (tk << log_r) | cp;
+        atomicAdd(accx + aj, sj * (vk.x - chat * vj.x) + rj * vj.x);
+        atomicAdd(accy + aj, sj * (vk.y - chat * vj.y) + rj * vj.y);
+        atomicAdd(accz + aj, sj * (vk.z - chat * vj.z) + rj * vj.z);
+        atomicAdd(accx + ak, sk * (vj.x - chat * vk.x) + rk * vk.x);
+        atomicAdd(accy + ak, sk * (vj.y - chat * vk.y) + rk * vk.y);
+        atomicAdd(accz + ak, sk * (vj.z - chat * vk.z) + rk * vk.z);
     }
   }
   __syncwarp();
   for (int t = lane; t < na_tot; t += 32) {
-    const float4 a = make_float4(accx[t], accy[t], accz[t], 0.f);
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < n_copy; ++c) {
+      const int i = (t << log_r) + c;
+      a.x += accx[i];
+      a.y += accy[i];
+      a.z += accz[i];
+    }
     const float4 v = angv[t];
     atomicAdd(&ws.f_pos[__float_as_int(angf[t].w)], make_float4(-a.x, -a.y, -a.z, 0.f));
     fi[0] += a.x; fi[1] += a.y; fi[2] += a.z;
@@ -589,7 +617,8 @@ size_t aev_fwd_smem(const Ws& ws) {
   return (size_t)kWarps * (ws.cap_a + ws.cap_a / 4 + ws.cap_r / 2 + 2) * sizeof(float4);
 }
 size_t aev_bwd_smem(const Ws& ws, int n_pairs) {
-  return (size_t)kWarps * aev_bwd_warp_f4(ws.cap_a, n_pairs) * sizeof(float4);
+  return (size_t)kWarps * aev_bwd_warp_f4(ws.cap_a, n_pairs, aev_bwd_copies(ws.cap_a, n_pairs)) *
+         sizeof(float4);
 }
 
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st) {
@@ -604,20 +633,27 @@ void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
                     cudaStream_t st) {
   if (n_in <= 0) return;
   const size_t sm = aev_bwd_smem(ws, ac.n_pairs);
+  const int copies = aev_bwd_copies(ws.cap_a, ac.n_pairs);
+  const int log_r = copies == 4 ? 2 : copies == 2 ? 1 : 0;
   const int grid = (n_in + kWarps - 1) / kWarps;
   if (ac.zeta == 32) {
-    if (want_virial) k_aev_bwd<32, true><<<grid, kWarps * 32, sm, st>>>(ws, ac);
-    else k_aev_bwd<32, false><<<grid, kWarps * 32, sm, st>>>(ws, ac);
+    if (want_virial) k_aev_bwd<32, true><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r);
+    else k_aev_bwd<32, false><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r);
   } else {
-    if (want_virial) k_aev_bwd<0, true><<<grid, kWarps * 32, sm, st>>>(ws, ac);
-    else k_aev_bwd<0, false><<<grid, kWarps * 32, sm, st>>>(ws, ac);
+    if (want_virial) k_aev_bwd<0, true><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r);
+    else k_aev_bwd<0, false><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r);
   }
 }
 
 // raise (never lower) the dynamic shared-memory limit of the AEV kernels to what
 // a launch over `ws` needs
 cudaError_t aev_ensure_smem(const Ws& ws) {
-  const int need_f = (int)aev_fwd_smem(ws), need_b = (int)aev_bwd_smem(ws);
+  // the backward kernel's size depends on the species-pair count through the
+  // number of accumulator copies: take the largest over every model size
+  int need_b = 0;
+  for (int np = 1; np <= kMaxSpecies * (kMaxSpecies + 1) / 2; ++np)
+    need_b = std::max(need_b, (int)aev_bwd_smem(ws, np));
+  const int need_f = (int)aev_fwd_smem(ws);
   const void* fwd[2] = {(const void*)k_aev_fwd<32>, (const void*)k_aev_fwd<0>};
   const void* bwd[4] = {(const void*)k_aev_bwd<32, false>, (const void*)k_aev_bwd<32, true>,
                         (const void*)k_aev_bwd<0, false>, (const void*)k_aev_bwd<0, true>};
