@@ -101,12 +101,18 @@ __device__ __forceinline__ Geo pair_geo(const float4& xi, const float4& xj, cons
 }
 
 // One lane per entry of a neighbour list: visit(slot, j, geometry) stages entry j.
+// A lane takes two entries per pass and issues both gathers before either is used.
 template <class Visit>
 __device__ __forceinline__ void stage_list(int n, const int* lst, const float4& xi, const SysDev& d,
                                            const float4* xyzq, unsigned lane, Visit visit) {
-  for (int t = (int)lane; t < n; t += 32) {
-    const int j = lst[t];
-    visit(t, j, pair_geo(xi, xyzq[j], d));
+  for (int t0 = 0; t0 < n; t0 += 64) {
+    const int ta = t0 + (int)lane, tb = ta + 32;
+    const int ja = ta < n ? lst[ta] : -1;
+    const int jb = tb < n ? lst[tb] : -1;
+    const float4 xa = ja >= 0 ? xyzq[ja] : xi;
+    const float4 xb = jb >= 0 ? xyzq[jb] : xi;
+    if (ja >= 0) visit(ta, ja, pair_geo(xi, xa, d));
+    if (jb >= 0) visit(tb, jb, pair_geo(xi, xb, d));
   }
 }
 
