@@ -30,7 +30,7 @@ namespace nnp {
 namespace {
 
 constexpr int kRows = 32;       // rows per CTA
-constexpr int kThreads = 256;   // 8 warps: 4 row groups x 2 column halves
+constexpr int kThreads = 256;   // 8 warps, 4 rows of the tile each
 constexpr int KS = 32;          // K-slice of one pipeline stage
 constexpr int NS = 3;           // stages of the cp.async ring (NS - 1 slices in flight)
 constexpr int kOutChunk = 128;  // B1 output columns per pass
