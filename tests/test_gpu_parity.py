@@ -345,3 +345,15 @@ def test_golden_closed_form_aev_values(torch_cuda):
         for i, a, b in c["zero"]:
             assert np.all(np.abs(G[i, a:b + 1]) <= 1e-6), (c["name"], i, a, b)
         pot.close()
+
+
+@pytest.mark.parametrize("kind,max_na", [("ani4", 32), ("ani4", 64), ("ani4", 128),
+                                         ("ani7", 32), ("ani7", 64)])
+def test_angular_accumulator_copies(torch_cuda, kind, max_na):
+    # the force kernel keeps 4, 2 or 1 copies of its angular accumulators,
+    # depending on the angular list capacity and the species-pair count; every
+    # choice must give the oracle's forces
+    pot, orc = make(kind)
+    pot.reserve(1000, 1, 128, max_na)
+    s = synth.water_box(300, 20.5, 7, seed=41)
+    check_system(pot, orc, s, aev=False)
