@@ -181,8 +181,11 @@ int nnp_energy_forces_batch(nnp_handle* h, int n_sys, const nnp_system_t* system
 /* End-to-end convenience for host callers: host buffers in and out, copies to
  * and from the device inside, synchronous.  coords_h [n,3] float32, species_h
  * [n] uint8, mask_h [n] or NULL, box_host double[3] or NULL; energy_h double[1],
- * forces_h float32 [n,3], virial_h double[9] or NULL.  Retries once after a
- * capacity overflow. */
+ * forces_h float32 [n,3], virial_h double[9] or NULL.  Copies, evaluation and
+ * the status read run on the legacy default stream with one synchronisation;
+ * page-locked buffers keep the copies asynchronous.  energy_h and virial_h are
+ * written only when the call returns NNP_OK; forces_h may hold partial results
+ * after an error.  Retries once after a capacity overflow. */
 int nnp_energy_forces_host(nnp_handle* h, int64_t n_atoms, const float* coords_h,
                            const uint8_t* species_h, const double* box_host,
                            const uint8_t* mask_h, double* energy_h, float* forces_h,
