@@ -143,31 +143,40 @@ __device__ __forceinline__ float sin_theta(const float4& a, const float4& b, flo
   return sqrt_approx(fmaf(1.f - k * k, chat * chat, s2));
 }
 
+// per-warp header: species offsets/counts of the radial and angular lists
+struct ListHdr {
+  int off_r[kMaxSpecies + 1], off_a[kMaxSpecies + 1];
+  unsigned live[2];   // backward kernel: angular blocks with triplets (bit q = block q)
+};
+
+// dE/dG blocks of a centre held in shared memory at a time by the backward
+// kernel (the blocks with triplets, in block order; a centre with more passes
+// over them in groups of this many)
+constexpr int kGallBlocks = 16;
+
 // float4s of shared memory per warp of the backward kernel: neighbour geometry
 // and cutoffs (2 cap_a), `copies` copies of the x/y/z accumulators (3 cap_a
-// copies floats), radial dE/dG (32), the angular blocks' dE/dG (8 per block)
-// and the block table (5 ints per block + 1)
+// copies floats), radial dE/dG (32), up to kGallBlocks angular blocks' dE/dG
+// (8 per block) and the block table (5 ints per block + 1)
 __host__ __device__ constexpr int aev_bwd_warp_f4(int cap_a, int n_pairs, int copies) {
-  return 2 * cap_a + (3 * cap_a * copies + 3) / 4 + 32 + 8 * n_pairs + (5 * n_pairs + 1 + 3) / 4;
+  return 2 * cap_a + (3 * cap_a * copies + 3) / 4 + 32 +
+         8 * (n_pairs < kGallBlocks ? n_pairs : kGallBlocks) + (5 * n_pairs + 1 + 3) / 4;
 }
 
 // Copies of the per-neighbour angular accumulators.  The lanes of one 32-triplet
 // window often add into the same neighbour (a block with few neighbours of a
 // species repeats them across the window), and shared-memory float atomics on
 // one address serialise; with R copies lane l adds into copy l mod R, so only
-// lanes equal mod R can collide.  R = 4, 2 or 1: the largest that keeps the
-// CTA within the shared memory of four CTAs per SM.
-constexpr int kBwdCtaSmem = 56 * 1024;
+// lanes equal mod R can collide.  R = 4, 2 or 1: the largest that keeps four
+// CTAs on an SM (228 KiB of shared memory per SM, 1 KiB reserved per CTA, plus
+// the static list headers).
+constexpr int kBwdCtaSmem = 228 * 1024 / 4 - 1024 - kWarps * (int)sizeof(ListHdr);
 int aev_bwd_copies(int cap_a, int n_pairs) {
   for (int r = 4; r > 1; r >>= 1)
-    if ((size_t)kWarps * aev_bwd_warp_f4(cap_a, n_pairs, r) * sizeof(float4) <= kBwdCtaSmem) return r;
+    if ((size_t)kWarps * aev_bwd_warp_f4(cap_a, n_pairs, r) * sizeof(float4) <= (size_t)kBwdCtaSmem)
+      return r;
   return 1;
 }
-
-// per-warp header: species offsets/counts of the radial and angular lists
-struct ListHdr {
-  int off_r[kMaxSpecies + 1], off_a[kMaxSpecies + 1];
-};
 
 __device__ __forceinline__ void load_hdr(const uint16_t* hdr, int S, unsigned lane, ListHdr* h) {
   int cr = (lane < (unsigned)S) ? hdr[lane] : 0;
@@ -377,8 +386,10 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
   float* accz = accy + ws.cap_a * n_copy;
   float4* past_acc = angf + ws.cap_a + (3 * ws.cap_a * n_copy + 3) / 4;
   float* grad = reinterpret_cast<float*>(past_acc);  // S*16 radial dE/dG
-  float4* gall = past_acc + 32;            // every angular block's dE/dG, [block][z][a]
-  int4* bt_geo = reinterpret_cast<int4*>(gall + 8 * ac.n_pairs);     // [n_pairs]
+  // dE/dG of up to kGallBlocks angular blocks with triplets, [slot][z][a]
+  const int n_gall = min(ac.n_pairs, kGallBlocks);
+  float4* gall = past_acc + 32;
+  int4* bt_geo = reinterpret_cast<int4*>(gall + 8 * n_gall);         // [n_pairs]
   int* bt_start = reinterpret_cast<int*>(bt_geo + ac.n_pairs);       // [n_pairs + 1]
   ListHdr& H = hdrs[w];
 
@@ -484,102 +495,119 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
     if (q0 + 32 >= np && lane == 0) bt_start[np] = carry;
   }
   __syncwarp();   // the block table is complete
-  // the 32 dE/dG values (index 8a + z) of every block that has triplets,
-  // transposed to [z][a] so that an angle section is one 16-byte load
+  // the dE/dG blocks with triplets, in block order; a group of up to n_gall of
+  // them at a time is staged (its 32 values, index 8a + z, transposed to [z][a]
+  // so that an angle section is one 16-byte load) and its triplets processed
+  const float* ga = g_row + ac.S * kNR;
+  float* gf = reinterpret_cast<float*>(gall);
   {
-    const float* ga = g_row + ac.S * kNR;
-    float* gf = reinterpret_cast<float*>(gall);
-    unsigned live0 = __ballot_sync(kFull, (int)lane < np && bt_start[lane + 1] > bt_start[lane]);
+    const unsigned l0 = __ballot_sync(kFull, (int)lane < np && bt_start[lane + 1] > bt_start[lane]);
     const int q1 = 32 + (int)lane;
-    unsigned live1 = __ballot_sync(kFull, q1 < np && bt_start[q1 + 1] > bt_start[q1]);
-    const int tpos = (lane & 7) * 4 + (lane >> 3);
-    while (live0) {
-      const int q = __ffs(live0) - 1;
-      live0 &= live0 - 1;
-      gf[q * 32 + tpos] = ga[q * 32 + lane];
-    }
-    while (live1) {
-      const int q = 32 + __ffs(live1) - 1;
-      live1 &= live1 - 1;
-      gf[q * 32 + tpos] = ga[q * 32 + lane];
-    }
+    const unsigned l1 = __ballot_sync(kFull, q1 < np && bt_start[q1 + 1] > bt_start[q1]);
+    if (lane == 0) { H.live[0] = l0; H.live[1] = l1; }
   }
   __syncwarp();
-  const int T = bt_start[np];
+  const int n_live = __popc(H.live[0]) + __popc(H.live[1]);
+  const int tpos = (lane & 7) * 4 + (lane >> 3);
   int bl = 0, cur = -1;
   int os = 0, cs = 0, ou = 0, cu = 0, same = 0;
   float inv_cs = 0.f, inv_cu = 0.f;
-  for (int t = lane; t < T; t += 32) {
-    while (bt_start[bl + 1] <= t) ++bl;
-    if (bl != cur) {
-      cur = bl;
-      const int4 g4 = bt_geo[bl];
-      os = g4.x; cs = g4.y; ou = g4.z; cu = g4.w & 0xffff; same = g4.w >> 16;
-      inv_cs = 1.f / (float)max(cs, 1);
-      inv_cu = 1.f / (float)max(cu, 1);
-    }
-    int j, k;
-    decode_pair_diag(t - bt_start[bl], same, cs, cu, inv_cs, inv_cu, &j, &k);
-    const float4* gblk = gall + bl * 8;
+  const float4* gblk = gall;
+  for (int first = 0; first < n_live; first += n_gall) {
+    // live blocks first .. first + n_gall - 1 into slots 0 .. (the slot also goes
+    // to bits 17.. of the block's table entry); block ids b_lo .. b_hi
+    int b_lo = -1, b_hi = -1;
     {
-        const int tj = os + j, tk = ou + k;
-        const float4 vj = angv[tj], vk = angv[tk];
-        const float4 fj4 = angf[tj], fk4 = angf[tk];
-        const float chat = vj.x * vk.x + vj.y * vk.y + vj.z * vk.z;
-        const float c = ac.cos_scale * chat;
-        const float sn = fmaxf(sin_theta(vj, vk, chat, ac.cos_scale), 1e-6f);
-        const float c_over_s = c * rcp_approx(sn);
-        const float rb = 0.5f * (vj.w + vk.w);
-        // contract the block's dE/dG over the 8 angle sections first:
-        //   F_a = sum_z g[a][z] B_z,  dF_a = sum_z g[a][z] dB_z/dc
-        float F[kNA] = {0.f, 0.f, 0.f, 0.f}, dF[kNA] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int z = 0; z < kNZ; ++z) {
-          const float base = fmaf(sn, ac.sin_z[z], fmaf(c, ac.cos_z[z], 1.f));
-          float B, B1;
-          if constexpr (ZETA == 32) {
-            // base >= 1 + cos(15 pi / 16) > 0: base^31 = base^32 / base
-            const float p2 = base * base, p4 = p2 * p2, p8 = p4 * p4, p16 = p8 * p8;
-            B = p16 * p16;
-            B1 = B * rcp_approx(base);
-          } else {
-            B1 = ipow<0>(base, ac.zeta - 1);
-            B = B1 * base;
-          }
-          const float dB = B1 * fmaf(-ac.sin_z[z], c_over_s, ac.cos_z[z]);
-          const float4 gz = gblk[z];
-          F[0] = fmaf(gz.x, B, F[0]); F[1] = fmaf(gz.y, B, F[1]);
-          F[2] = fmaf(gz.z, B, F[2]); F[3] = fmaf(gz.w, B, F[3]);
-          dF[0] = fmaf(gz.x, dB, dF[0]); dF[1] = fmaf(gz.y, dB, dF[1]);
-          dF[2] = fmaf(gz.z, dB, dF[2]); dF[3] = fmaf(gz.w, dB, dF[3]);
+      unsigned m0 = H.live[0], m1 = H.live[1];
+      for (int idx = 0; idx < first + n_gall && (m0 | m1); ++idx) {
+        int q;
+        if (m0) { q = __ffs(m0) - 1; m0 &= m0 - 1; }
+        else { q = 32 + __ffs(m1) - 1; m1 &= m1 - 1; }
+        if (idx >= first) {
+          gf[(idx - first) * 32 + tpos] = ga[q * 32 + lane];
+          if (lane == 0) bt_geo[q].w = (bt_geo[q].w & 0x1ffff) | ((idx - first) << 17);
+          if (b_lo < 0) b_lo = q;
+          b_hi = q;
         }
-        float tc = 0.f, tR = 0.f, tf = 0.f;
-#pragma unroll
-        for (int a = 0; a < kNA; ++a) {
-          const float x = rb - ac.shf_a[a];
-          const float A = fast_exp2(ca_ * x * x);
-          const float AF = A * F[a];
-          tf += AF;
-          tR = fmaf(m2eta * x, AF, tR);
-          tc = fmaf(A, dF[a], tc);
-        }
-        const float fjk = fj4.x * fk4.x;
-        tc *= ac.ang_pre * (float)ac.zeta * fjk;  // dE/dc, c = cos_scale * cos_hat
-        tR *= ac.ang_pre * fjk;                    // dE/dRbar
-        tf *= ac.ang_pre;                          // dE/d(f_j f_k)
-        const float dEdchat = ac.cos_scale * tc;
-        const float sj = dEdchat * fj4.z, sk = dEdchat * fk4.z;
-        const float rj = 0.5f * tR + tf * fj4.y * fk4.x;
-        const float rk = 0.5f * tR + tf * fj4.x * fk4.y;
-        const int cp = (int)lane & (n_copy - 1);
-        const int aj = (tj << log_r) | cp, ak = (tk << log_r) | cp;
-        atomicAdd(accx + aj, sj * (vk.x - chat * vj.x) + rj * vj.x);
-        atomicAdd(accy + aj, sj * (vk.y - chat * vj.y) + rj * vj.y);
-        atomicAdd(accz + aj, sj * (vk.z - chat * vj.z) + rj * vj.z);
-        atomicAdd(accx + ak, sk * (vj.x - chat * vk.x) + rk * vk.x);
-        atomicAdd(accy + ak, sk * (vj.y - chat * vk.y) + rk * vk.y);
-        atomicAdd(accz + ak, sk * (vj.z - chat * vk.z) + rk * vk.z);
+      }
     }
+    __syncwarp();
+    const int t_end = bt_start[b_hi + 1];
+    bl = b_lo;
+    cur = -1;
+    for (int t = bt_start[b_lo] + (int)lane; t < t_end; t += 32) {
+      while (bt_start[bl + 1] <= t) ++bl;
+      if (bl != cur) {
+        cur = bl;
+        const int4 g4 = bt_geo[bl];
+        os = g4.x; cs = g4.y; ou = g4.z; cu = g4.w & 0xffff; same = (g4.w >> 16) & 1;
+        inv_cs = 1.f / (float)max(cs, 1);
+        inv_cu = 1.f / (float)max(cu, 1);
+        gblk = gall + (g4.w >> 17) * 8;
+      }
+      int j, k;
+      decode_pair_diag(t - bt_start[bl], same, cs, cu, inv_cs, inv_cu, &j, &k);
+      {
+          const int tj = os + j, tk = ou + k;
+          const float4 vj = angv[tj], vk = angv[tk];
+          const float4 fj4 = angf[tj], fk4 = angf[tk];
+          const float chat = vj.x * vk.x + vj.y * vk.y + vj.z * vk.z;
+          const float c = ac.cos_scale * chat;
+          const float sn = fmaxf(sin_theta(vj, vk, chat, ac.cos_scale), 1e-6f);
+          const float c_over_s = c * rcp_approx(sn);
+          const float rb = 0.5f * (vj.w + vk.w);
+          // contract the block's dE/dG over the 8 angle sections first:
+          //   F_a = sum_z g[a][z] B_z,  dF_a = sum_z g[a][z] dB_z/dc
+          float F[kNA] = {0.f, 0.f, 0.f, 0.f}, dF[kNA] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int z = 0; z < kNZ; ++z) {
+            const float base = fmaf(sn, ac.sin_z[z], fmaf(c, ac.cos_z[z], 1.f));
+            float B, B1;
+            if constexpr (ZETA == 32) {
+              // base >= 1 + cos(15 pi / 16) > 0: base^31 = base^32 / base
+              const float p2 = base * base, p4 = p2 * p2, p8 = p4 * p4, p16 = p8 * p8;
+              B = p16 * p16;
+              B1 = B * rcp_approx(base);
+            } else {
+              B1 = ipow<0>(base, ac.zeta - 1);
+              B = B1 * base;
+            }
+            const float dB = B1 * fmaf(-ac.sin_z[z], c_over_s, ac.cos_z[z]);
+            const float4 gz = gblk[z];
+            F[0] = fmaf(gz.x, B, F[0]); F[1] = fmaf(gz.y, B, F[1]);
+            F[2] = fmaf(gz.z, B, F[2]); F[3] = fmaf(gz.w, B, F[3]);
+            dF[0] = fmaf(gz.x, dB, dF[0]); dF[1] = fmaf(gz.y, dB, dF[1]);
+            dF[2] = fmaf(gz.z, dB, dF[2]); dF[3] = fmaf(gz.w, dB, dF[3]);
+          }
+          float tc = 0.f, tR = 0.f, tf = 0.f;
+#pragma unroll
+          for (int a = 0; a < kNA; ++a) {
+            const float x = rb - ac.shf_a[a];
+            const float A = fast_exp2(ca_ * x * x);
+            const float AF = A * F[a];
+            tf += AF;
+            tR = fmaf(m2eta * x, AF, tR);
+            tc = fmaf(A, dF[a], tc);
+          }
+          const float fjk = fj4.x * fk4.x;
+          tc *= ac.ang_pre * (float)ac.zeta * fjk;  // dE/dc, c = cos_scale * cos_hat
+          tR *= ac.ang_pre * fjk;                    // dE/dRbar
+          tf *= ac.ang_pre;                          // dE/d(f_j f_k)
+          const float dEdchat = ac.cos_scale * tc;
+          const float sj = dEdchat * fj4.z, sk = dEdchat * fk4.z;
+          const float rj = 0.5f * tR + tf * fj4.y * fk4.x;
+          const float rk = 0.5f * tR + tf * fj4.x * fk4.y;
+          const int cp = (int)lane & (n_copy - 1);
+          const int aj = (tj << log_r) | cp, ak = (tk << log_r) | cp;
+          atomicAdd(accx + aj, sj * (vk.x - chat * vj.x) + rj * vj.x);
+          atomicAdd(accy + aj, sj * (vk.y - chat * vj.y) + rj * vj.y);
+          atomicAdd(accz + aj, sj * (vk.z - chat * vj.z) + rj * vj.z);
+          atomicAdd(accx + ak, sk * (vj.x - chat * vk.x) + rk * vk.x);
+          atomicAdd(accy + ak, sk * (vj.y - chat * vk.y) + rk * vk.y);
+          atomicAdd(accz + ak, sk * (vj.z - chat * vk.z) + rk * vk.z);
+      }
+    }
+    __syncwarp();   // the group's slots are refilled by the next group
   }
   __syncwarp();
   for (int t = lane; t < na_tot; t += 32) {

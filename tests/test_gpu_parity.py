@@ -357,3 +357,25 @@ def test_angular_accumulator_copies(torch_cuda, kind, max_na):
     pot.reserve(1000, 1, 128, max_na)
     s = synth.water_box(300, 20.5, 7, seed=41)
     check_system(pot, orc, s, aev=False)
+
+
+def test_centres_with_more_live_blocks_than_staged(torch_cuda):
+    # a dense 7-species cluster: most centres see neighbours of every species, so
+    # more than 16 of the 28 angular blocks have triplets and the force kernel
+    # stages their dE/dG in two groups
+    pot, orc = make("ani7")
+    rng = np.random.Generator(np.random.PCG64(43))
+    sp = (np.arange(120) % 7).astype(np.uint8)
+    rng.shuffle(sp)
+    s = synth.gas_molecule(rng, 120, sp, density=0.15)
+    d = s.coords.astype(np.float64)
+    r = np.linalg.norm(d[:, None, :] - d[None, :, :], axis=-1)
+    live = []
+    for i in range(s.n_atoms):
+        nb = np.nonzero((r[i] <= 3.5) & (np.arange(s.n_atoms) != i))[0]
+        present = np.bincount(sp[nb], minlength=7) > 0
+        k = int(present.sum())
+        pairs = k * (k - 1) // 2 + int(sum(np.bincount(sp[nb], minlength=7) >= 2))
+        live.append(pairs)
+    assert max(live) > 16
+    check_system(pot, orc, s)
