@@ -32,6 +32,12 @@
 // Forces are the analytic chain rule F = -dE/dr written out by hand.  The
 // force-matching gradient uses a forward-mode dual number along the
 // coordinate direction v = dL/dF, run through the same templated code.
+// Pins (CPU tests): hand-derived AEV values at special geometries (the golden
+// fixture of Eqs. 3-5), the networks against a numpy chain, invariants
+// (translation, rotation, permutation, zero net force and torque, extensivity,
+// the mask), and finite differences of the energy and of the force-matching
+// loss.  Parity unpinned: the absolute energies of the synthetic models (the
+// paper prints no worked example with its weights).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
