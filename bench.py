@@ -669,13 +669,17 @@ def run_ours(args):
         return 0
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        n_c, times = oracle_sample_rate(args.workload, 1000, 4, seed=1)
+        # about 10 s of single-thread oracle work: a 100-centre probe sizes the sample
+        n_p, t_p = oracle_sample_rate(args.workload, 100, 1, seed=2)
+        n_s = int(min(20000, max(200, n_p / t_p[0] * 10.0 / 4)))
+        n_c, times = oracle_sample_rate(args.workload, n_s, 4, seed=1)
         cpu = {"value": n_c * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{len(times)} x {n_c} random centres of {args.workload} "
-                         f"(energy + forces of their terms), FP64, single thread"}
-        rate, cores = oracle_all_cores(args.workload, 1000)
+                         f"(energy + forces of their terms), FP64, single thread, "
+                         f"{sum(times):.1f} s"}
+        rate, cores = oracle_all_cores(args.workload, n_c)
         cpu["all_cores"] = {"value": rate, "unit": UNIT, "cores": cores,
-                            "sample": f"{cores} processes x 1000 random centres of {args.workload}, "
+                            "sample": f"{cores} processes x {n_c} random centres of {args.workload}, "
                                       "one process per host core"}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
