@@ -125,3 +125,12 @@ def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     # a changed kernel source invalidates the record
     src.write_text("kernel v2\n")
     assert bench.recorded_traffic("mlp", "water9000") is None
+
+
+def test_oracle_baselines_run_on_the_host():
+    # the bench's CPU baseline legs: the single-thread sample and one spawned
+    # oracle process per host core
+    n, times = bench.oracle_sample_rate("gas24", 10, 2, seed=3)
+    assert n == 10 and len(times) == 2 and all(t > 0 for t in times)
+    rate, cores = bench.oracle_all_cores("gas24", 5)
+    assert cores >= 1 and rate > 0
