@@ -21,11 +21,14 @@
 //
 // Backward (F = -dE/dr)
 //   radial edges: lane-per-neighbour, 16 shells each.
-//   angular: lane-per-triplet with the block's 32 dE/dG values in registers;
-//   each lane contracts them to dE/dcos, dE/dRbar and dE/d(f_j f_k), forms
-//   dE/du_j and dE/du_k and adds them to per-neighbour accumulators in shared
-//   memory; afterwards each neighbour receives one vector atomic and the centre
-//   one warp-reduced atomic.
+//   angular: lane-per-triplet, the triplets numbered continuously over the
+//   species-pair blocks that have any.  The dE/dG of those blocks is staged in
+//   shared memory ([z][a], up to 16 blocks at a time).  Each lane contracts its
+//   block's 32 values to dE/dcos, dE/dRbar and dE/d(f_j f_k), forms dE/du_j
+//   and dE/du_k and adds them to per-neighbour accumulators in shared memory.
+//   The accumulators come in up to four lane-indexed copies, so that lanes of
+//   one window rarely add into the same address.  Afterwards each neighbour
+//   receives one vector atomic and the centre one warp-reduced atomic.
 #include <cuda_bf16.h>
 
 #include <algorithm>
