@@ -10,8 +10,16 @@
 //   k_bin      per atom: cell index, rank inside the cell, AEV row (slot)
 //   k_scan     exclusive scan of the cell counts
 //   k_scatter  packed (cell-ordered) float4 coordinates and index maps
-//   k_neighbors one warp per centre: scan the 27 neighbour cells, keep pairs
-//              with R <= rc_r, mark R <= rc_a, write species-sorted lists
+//   k_neighbors one CTA per home cell: the atoms of the 27 neighbour cells are
+//              staged in shared memory, sorted by species; one warp per centre
+//              keeps pairs with R <= rc_r, marks R <= rc_a and writes
+//              species-sorted lists (per-centre search from global memory when
+//              a neighbourhood does not fit the stage)
+// A one-chunk batch of at most 2048 atoms runs init .. scatter as one CTA
+// (k_front).  With a Verlet skin, k_skin_check measures the displacement since
+// the last build, the front-end kernels and k_neighbors return at once when no
+// rebuild is due, and k_list_refresh cuts the lists at Rc + skin down to the
+// cutoffs on every call.
 #include <algorithm>
 
 #include "nnp_internal.cuh"
