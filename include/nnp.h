@@ -363,11 +363,13 @@ const char* nnp_last_error(void);
  * device current); make that first call before any stream capture.
  *
  * Limits: one system, FP32 handles only (NNP_ERR_UNSUPPORTED otherwise); the
- * atoms in the mask, their neighbour lists (at most 256 radial and 96 angular
- * neighbours per atom) and the network activations must fit in the array --
- * about 4000 atoms for the 4-species 384-160-128-96-1 network, fewer for wider
- * or ensemble networks.  A larger request returns NNP_ERR_ARG with a message
- * giving the bytes needed and the limit, before any work is enqueued.
+ * input atoms, their neighbour lists (at most 256 radial and 96 angular
+ * neighbours per atom), AEV rows and network buffers must fit in the array:
+ * about 6,900 atoms for the 4-species 384-160-128-96-1 network (one-network models
+ * keep their activations on chip), fewer for the 7-species model and far fewer
+ * for ensembles; nnp_noalloc_max_atoms returns the exact limit of a handle.
+ * A larger request returns NNP_ERR_ARG with a message giving the bytes needed
+ * and the limit, before any work is enqueued.
  *
  * Every call reuses the same array and overwrites what the previous call left
  * there (the call clears its counters and accumulators itself).  Calls whose
@@ -383,6 +385,9 @@ int nnp_energy_forces_noalloc(nnp_handle* h, int64_t n_atoms, const float* coord
                               const uint8_t* species, const double* box_host,
                               const uint8_t* mask, double* energy, float* forces,
                               double* virial, void* stream);
+/* The largest n_atoms nnp_energy_forces_noalloc accepts for this handle's model
+ * (0 for a BF16 handle).  Host computation only. */
+int nnp_noalloc_max_atoms(const nnp_handle* h, int64_t* max_atoms);
 
 /* ---------------------------------------------------------------- diagnostics
  * Read back intermediate results of the LAST compute call on this handle (for
@@ -405,6 +410,16 @@ int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream);
  * nnp_sync_status); the context stays usable. */
 int nnp_debug_wait_probe(nnp_handle* h, unsigned limit, void* stream);
 int nnp_debug_neighbors(nnp_handle* h, int angular, int cap, int* out, void* stream);
+/* The cell grid the neighbour search (Sec. "Massive Parallelism within
+ * Tinker-HP": linked cells of edge >= the cutoff) builds for one system whose
+ * ML region spans len[3] A (the box edges if periodic), with list cutoff rc A
+ * and n_atoms input atoms: nc_out[3] cells per dimension, each cell at least rc
+ * wide, and the total (returned in *cells_out) at most 2 n_atoms + 27, the cell
+ * capacity the work arena holds per system.  Host computation only (no device
+ * call); the kernels use the same function.  NNP_ERR_ARG on null pointers or
+ * rc <= 0. */
+int nnp_debug_cell_grid(const float* len, float rc, int64_t n_atoms, int* nc_out,
+                        int64_t* cells_out);
 
 #ifdef __cplusplus
 }

@@ -41,7 +41,7 @@ EXPORTS = (
     "nnp_server_create", "nnp_server_destroy", "nnp_server_register", "nnp_server_submit",
     "nnp_server_poll", "nnp_server_stats", "nnp_force_vjp_batch", "nnp_force_vjp",
     "nnp_n_weights", "nnp_debug_wait_probe", "nnp_set_skin", "nnp_list_stats",
-    "nnp_integrate",
+    "nnp_integrate", "nnp_noalloc_max_atoms", "nnp_debug_cell_grid",
 )
 
 
@@ -119,6 +119,8 @@ def lib():
     L.nnp_debug_rows.argtypes = [P, i, P, P]
     L.nnp_debug_neighbors.argtypes = [P, i, i, P, P]
     L.nnp_energy_forces_noalloc.argtypes = [P, i64, P, P, P, P, P, P, P, P]
+    L.nnp_noalloc_max_atoms.argtypes = [P, ctypes.POINTER(i64)]
+    L.nnp_debug_cell_grid.argtypes = [P, ctypes.c_float, i64, P, ctypes.POINTER(i64)]
     L.nnp_server_create.argtypes = [P, i, i64, i, ctypes.POINTER(P)]
     L.nnp_server_destroy.argtypes = [P]
     L.nnp_server_destroy.restype = None

@@ -1235,6 +1235,16 @@ int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream) {
 // Neighbour lists of the last call in input-atom order: out[i][t] = input index
 // of the t-th neighbour of atom i (radial list, or angular if angular != 0),
 // -1 past the end.  out: device int32 [n_in_total, cap].
+int nnp_debug_cell_grid(const float* len, float rc, int64_t n_atoms, int* nc_out,
+                        int64_t* cells_out) {
+  g_err.clear();
+  if (!len || !nc_out || !cells_out || !(rc > 0.f) || n_atoms < 0)
+    return fail(NNP_ERR_ARG, "bad argument");
+  const float l[3] = {len[0], len[1], len[2]};
+  *cells_out = cell_grid(l, rc, 2 * (long long)n_atoms + 27, nc_out);
+  return NNP_OK;
+}
+
 int nnp_debug_neighbors(nnp_handle* h, int angular, int cap, int* out, void* stream) {
   if (!h || !h->arena || !out || cap <= 0) return fail(NNP_ERR_ARG, "bad argument");
   launch_gather_nbrs(h->ws, h->last_n_in, angular, cap, out, static_cast<cudaStream_t>(stream));
@@ -1428,9 +1438,34 @@ extern "C" int nnp_energy_forces_noalloc(nnp_handle* h, int64_t n_atoms, const f
   CU_TRY(cudaStreamSynchronize(st));
   if (status[0] & kStSpecies) return fail(NNP_ERR_SPECIES, "species index out of range");
   if (status[0] & kStNonFinite) return fail(NNP_ERR_NONFINITE, "non-finite coordinate in the ML region");
-  if (status[0] & (kStCapacity | kStCells))
+  if (status[0] & kStCells)
+    return fail(NNP_ERR_CAPACITY, "the cell grid needs more than the " +
+                                      std::to_string(2 * (long long)n_atoms + 27) +
+                                      " cells (2 n + 27) the scratch array holds");
+  if (status[0] & kStCapacity)
     return fail(NNP_ERR_CAPACITY, "an atom has more than " + std::to_string(kNoAllocCapR) +
                                       " radial or " + std::to_string(kNoAllocCapA) +
                                       " angular neighbours (fixed lists of the allocation-free entry point)");
+  return NNP_OK;
+}
+
+extern "C" int nnp_noalloc_max_atoms(const nnp_handle* h, int64_t* max_atoms) {
+  g_err.clear();
+  if (!h || !max_atoms) return fail(NNP_ERR_ARG, "null argument");
+  const Model& m = *h->model;
+  if (m.precision != NNP_FP32) {
+    *max_atoms = 0;
+    return NNP_OK;
+  }
+  // the work space grows with the atom count: the largest count whose carve fits
+  Ws ws{};
+  MlpBufs mb{};
+  long long lo = 0, hi = 1 << 24;
+  while (lo < hi) {
+    const long long mid = (lo + hi + 1) / 2;
+    if (noalloc_carve(m, (int)mid, nullptr, &ws, &mb) <= kNoAllocBytes) lo = mid;
+    else hi = mid - 1;
+  }
+  *max_atoms = lo;
   return NNP_OK;
 }

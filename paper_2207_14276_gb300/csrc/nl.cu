@@ -200,7 +200,7 @@ __device__ __forceinline__ void setup_body(const Ws& ws, const AevConst& ac) {
     if (b < ws.n_sys) {
       d = ws.sys[b];
       n_ml = d.n_ml;
-      const int cap = 2 * d.in.n_in + 27;
+      const long long cap = 2LL * d.in.n_in + 27;
       int nc[3];
       float len[3], org[3];
       for (int c = 0; c < 3; ++c) {
@@ -215,12 +215,8 @@ __device__ __forceinline__ void setup_body(const Ws& ws, const AevConst& ac) {
           len[c] = 1.f;
           org[c] = 0.f;
         }
-        nc[c] = max(1, (int)floorf(len[c] / rc));
       }
-      while ((long long)nc[0] * nc[1] * nc[2] > cap) {
-        int c = (nc[0] >= nc[1] && nc[0] >= nc[2]) ? 0 : (nc[1] >= nc[2] ? 1 : 2);
-        nc[c] = max(1, nc[c] - 1);
-      }
+      cell_grid(len, rc, cap, nc);
       for (int c = 0; c < 3; ++c) {
         d.nc[c] = nc[c];
         d.origin[c] = org[c];
@@ -240,16 +236,26 @@ __device__ __forceinline__ void setup_body(const Ws& ws, const AevConst& ac) {
     run_cells += tot_c;
   }
   if (threadIdx.x == 0) {
-    ws.totals[0] = run_atoms;
-    ws.totals[1] = run_cells;
-    if (run_cells > ws.cell_cap) atomicOr(ws.status, kStCells);
+    // more cells than the arena holds (impossible while the arena is sized for
+    // 2 n + 27 cells per system, as every grid is): the call reports it, and the
+    // batch becomes empty for every later kernel (no atoms, cells or AEV rows),
+    // so that no kernel indexes past the cell arrays
+    const bool over = run_cells > ws.cell_cap;
+    if (over) atomicOr(ws.status, kStCells);
+    ws.totals[0] = over ? 0 : run_atoms;
+    ws.totals[1] = over ? 0 : run_cells;
     int acc = 0;
     for (int s = 0; s < ac.S; ++s) {
       ws.seg_start[s] = acc;
-      acc += (ws.species_count[s] + kRowTile - 1) / kRowTile * kRowTile;
+      if (!over) acc += (ws.species_count[s] + kRowTile - 1) / kRowTile * kRowTile;
     }
     for (int s = ac.S; s <= kMaxSpecies; ++s) ws.seg_start[s] = acc;
   }
+}
+
+// the cell grids of this batch fit the arena (k_setup clears the batch otherwise)
+__device__ __forceinline__ bool cells_fit(const Ws& ws) {
+  return (*(volatile const int*)ws.status & kStCells) == 0;
 }
 
 __global__ void k_setup(Ws ws, AevConst ac) { setup_body(ws, ac); }
@@ -270,6 +276,7 @@ __device__ __forceinline__ int cell_coord(float x, const SysDev& d, int c) {
 
 // one input atom (all 32 lanes of a warp call it together)
 __device__ __forceinline__ void bin_body(const Ws& ws, int gi, int n_in) {
+  if (!cells_fit(ws)) return;   // uniform: the flag is set before this kernel (or phase)
   const unsigned lane = threadIdx.x & 31;
   int b = -1;
   if (gi < n_in) b = ws.in_sys[gi];
@@ -354,7 +361,7 @@ __device__ __forceinline__ void scatter_body(const Ws& ws, int gi, int n_in) {
     return;
   }
   const int b = ws.in_sys[gi];
-  if (b < 0) return;
+  if (b < 0 || !cells_fit(ws)) return;
   const SysDev& d = ws.sys[b];
   const int local = gi - d.in.in_base;
   const int gcell = ws.in_cell[gi];

@@ -159,6 +159,29 @@ void launch_gather_rows(const Ws& ws, int n_in, const float* rows, const uint16_
 void launch_gather_nbrs(const Ws& ws, int n_in, int angular, int cap_out, int* out,
                         cudaStream_t st);
 
+// Cells per dimension of one system's grid: edge >= rc (nc[c] <= len[c] / rc)
+// and nc[0] nc[1] nc[2] <= cap.  Each count starts at floor(len / rc), clamped to
+// [1, 2^20] (a non-finite or huge extent cannot overflow the product, which
+// stays below 2^60); while the product exceeds cap the largest count is cut to
+// cap / (product of the other two), at least 1, so the loop ends within three
+// passes.  Returns the product.
+__host__ __device__ inline long long cell_grid(const float len[3], float rc, long long cap,
+                                               int nc[3]) {
+  for (int c = 0; c < 3; ++c) {
+    const float q = len[c] / rc;
+    nc[c] = (q >= 1048576.f) ? 1048576 : (q >= 1.f ? (int)q : 1);   // NaN -> 1
+  }
+  long long prod = (long long)nc[0] * nc[1] * nc[2];
+  while (prod > cap) {
+    const int c = (nc[0] >= nc[1] && nc[0] >= nc[2]) ? 0 : (nc[1] >= nc[2] ? 1 : 2);
+    const long long rest = prod / nc[c];
+    const long long want = cap / rest;
+    nc[c] = (int)(want < 1 ? 1 : want);
+    prod = (long long)nc[0] * nc[1] * nc[2];
+  }
+  return prod;
+}
+
 // order-preserving float <-> uint key (for atomicMin/atomicMax on floats)
 __host__ __device__ inline unsigned float_key(float f) {
   unsigned u;

@@ -134,3 +134,40 @@ def test_oracle_baselines_run_on_the_host():
     assert n == 10 and len(times) == 2 and all(t > 0 for t in times)
     rate, cores = bench.oracle_all_cores("gas24", 5)
     assert cores >= 1 and rate > 0
+
+
+def test_cell_grid_never_exceeds_the_arena_capacity():
+    """The cell grid of one system (linked cells of edge >= the cutoff) holds at
+    most 2 n + 27 cells, the per-system capacity the work arena is sized for, and
+    every cell is at least the cutoff wide -- also for extents that would
+    overflow a plain product of the per-dimension counts (huge, non-finite or
+    degenerate bounding boxes).  Host computation of the same function the
+    kernels use, through the C ABI (no device call)."""
+    import ctypes
+    from paper_2207_14276_gb300 import _lib
+    L = _lib.lib()
+    rng = np.random.Generator(np.random.PCG64(7))
+    cases = [((99.9, 99.9, 99.9), 100000), ((44.77,) * 3, 9000), ((10.0, 10.0, 10.0), 24),
+             ((1e30, 1e30, 1e30), 10), ((3e38, 1.0, 5e9), 2), ((float("inf"), 1.0, 1.0), 5),
+             ((float("nan"), 30.0, 30.0), 50), ((1e-3, 1e-3, 1e-3), 1), ((1e7, 1e7, 1e7), 0),
+             ((2.1e9, 2.1e9, 2.1e9), 1 << 30)]
+    for _ in range(300):
+        n = int(rng.integers(0, 200000))
+        cases.append((tuple(float(10.0 ** rng.uniform(-3, 12)) for _ in range(3)), n))
+    nc = (ctypes.c_int * 3)()
+    cells = ctypes.c_int64()
+    for ln, n in cases:
+        arr = (ctypes.c_float * 3)(*ln)
+        assert L.nnp_debug_cell_grid(arr, ctypes.c_float(5.2), n, nc, ctypes.byref(cells)) == 0
+        cap = 2 * n + 27
+        got = [nc[0], nc[1], nc[2]]
+        assert all(c >= 1 for c in got)
+        assert cells.value == got[0] * got[1] * got[2] <= cap, (ln, n, got)
+        for c, l in zip(got, np.float32(ln)):
+            if c > 1:   # every cell at least the cutoff wide
+                assert np.float32(l) / np.float32(c) >= np.float32(5.2) * (1 - 1e-6), (ln, got)
+    # a grid that fits is not reshaped: floor(L / rc) cells per dimension
+    arr = (ctypes.c_float * 3)(99.9, 99.9, 99.9)
+    L.nnp_debug_cell_grid(arr, ctypes.c_float(5.2), 100000, nc, ctypes.byref(cells))
+    assert [nc[0], nc[1], nc[2]] == [19, 19, 19]
+    assert L.nnp_debug_cell_grid(arr, ctypes.c_float(0.0), 10, nc, ctypes.byref(cells)) != 0
