@@ -3,11 +3,14 @@
 
 One step = one energy+force evaluation of the whole workload through the C ABI
 (cell list -> AEVs -> per-species networks -> analytic forces), inputs resident
-in HBM.  Default workload: 'water9000' (3000 rigid waters, 9000 atoms, periodic
-44.77 A box, 4-species 384-dim AEV, networks 384-160-128-96-1, FP32 path).
+in HBM.  Default workload: 'solvated100k' (a 1000-atom solute in 33,000 waters,
+100,000 atoms, periodic 99.9 A box, 7-species 1008-dim AEV, an ensemble of 8
+networks 1008-256-192-160-1) at FP32 accuracy, the largest single-GPU
+configuration; the BF16-network path on the same workload is measured beside
+it, and both are compared with the FP64 oracle on a seeded sample of atoms.
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload water9000]
-                  [--precision fp32|bf16] [--impl ours|reference]
+  python bench.py [--gpus N --steps K --warmup W] [--workload solvated100k]
+                  [--precision fp32|fp32_split|fp32_simt|bf16] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank evaluates its own replica of the workload on
 its own GPU (independent replicas, no data-path collective); the time is the
@@ -59,8 +62,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="water9000")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--workload", default="solvated100k")
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "fp32_split", "fp32_simt", "bf16"])
+    ap.add_argument("--no-bf16-beside", action="store_true",
+                    help="skip the BF16-network measurement beside an FP32 headline")
+    ap.add_argument("--oracle-atoms", type=int, default=24,
+                    help="seeded sample of atoms whose energies and forces are compared "
+                         "with the FP64 oracle (0 to skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--serving-rates", default="",
@@ -117,7 +126,7 @@ def recorded_traffic(stage, workload):
     return None
 
 
-def stage_work(stage, spec, counts, n_atoms, precision):
+def stage_work(stage, spec, counts, n_atoms, path):
     """Algorithmic work of one launch of a stage: (amount, unit, bound).
 
     counts: mean radial neighbours n_r and angular neighbours n_a per atom.
@@ -126,7 +135,9 @@ def stage_work(stage, spec, counts, n_atoms, precision):
     cutoff and their derivatives), per angular (j, k) pair 200 forward / 330
     backward (4 Gaussians, 8 factors (1 + cos(theta - theta_z))^32, the 32-term
     contraction and, backward, the derivatives and two edge gradients), and
-    2 K N per row for a network layer."""
+    2 K N per row for a network layer.  path: the network path of the handle
+    ('fp32_simt', 'fp32_split' or 'bf16'); a split-path layer issues three BF16
+    tensor products per term of its 2 K N, so its bound is the BF16 peak / 3."""
     D = spec.widths[0]
     E = spec.n_ensemble
     h1, h2, h3 = spec.widths[1:4]
@@ -148,8 +159,62 @@ def stage_work(stage, spec, counts, n_atoms, precision):
             "mlp_b3": (h3, h2 * E), "mlp_b2": (h2, h1 * E), "mlp_b1": (E * h1, D)}
     if stage in gemm:
         k, n = gemm[stage]
-        return 2.0 * n_atoms * k * n, "FLOP", ("tensor" if precision == "bf16" else "alu")
+        bound = {"bf16": "tensor", "fp32_split": "tensor_split"}.get(path, "alu")
+        return 2.0 * n_atoms * k * n, "FLOP", bound
     return None
+
+
+def roofline(stages, spec, counts, n_eval, path, peaks, peak_src, workload):
+    """Roofline entry of the dominant stage (largest time over the profiled pass)."""
+    live = [k for k in stages if stages[k][1] > 0]
+    if not live:
+        return None
+    dom = max(live, key=lambda k: stages[k][0])
+    dom_ms = stages[dom][0] / stages[dom][1]
+    work = stage_work(dom, spec, counts, n_eval, path)
+    if work is None:
+        return None
+    amount, unit, bound = work
+    if unit == "B":
+        achieved = amount / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]),
+                "unit": "GB/s", "peak_source": f"{peak_src} (hbm_gbs)"}
+    elif bound in ("tensor", "tensor_split"):
+        achieved = amount / (dom_ms / 1e3) / 1e12
+        peak = float(peaks["bf16_tflops"])
+        src = f"{peak_src} (bf16_tflops, burst)"
+        if bound == "tensor_split":
+            # three BF16 products per FP32-accurate term: the rate this algorithm
+            # can reach is a third of the BF16 peak
+            peak /= 3.0
+            src += " / 3: split operands, three BF16 tensor products per term"
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": src}
+    else:
+        achieved = amount / (dom_ms / 1e3) / 1e12
+        peak = fp32_alu_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock "
+                               "(the measured-peaks file has no FP32 figure)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = recorded_traffic(dom, workload)
+    roof.update({"kernel": dom, "launch_ms": dom_ms, "work_per_launch": amount,
+                 "work_unit": unit, "network_path": path,
+                 "timing": "CUDA events around the kernel on its launching stream, "
+                           "second pass of the same K steps"})
+    return roof
+
+
+def oracle_errors(outs, ref, idx):
+    """Errors of one evaluation against the FP64 oracle on the sampled atoms idx."""
+    ae = outs["atom_energies"].double().cpu().numpy()[idx]
+    F = outs["forces"].double().cpu().numpy()[idx]
+    dF = F - ref["forces"]
+    return {"atom_energy_abs_err_max_kcal_mol": float(np.abs(ae - ref["atom_energies"]).max()),
+            "atom_energy_sum_abs_err_kcal_mol": float(abs(ae.sum() - ref["atom_energies"].sum())),
+            "force_err_rms_kcal_mol_A": float(np.sqrt(np.mean(dF * dF))),
+            "force_err_max_kcal_mol_A": float(np.abs(dF).max()),
+            "force_rms_kcal_mol_A": float(np.sqrt(np.mean(ref["forces"] ** 2)))}
 
 
 # ------------------------------------------------------------------ clocks
@@ -489,11 +554,11 @@ def run_ours(args):
     clocks = ClockSampler(uuid, local)
     clocks.start()
     time.sleep(0.3)
-    def timed_steps(profile):
+    def timed_steps(profile, p=pot):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        pot.profile_read(reset=True)
-        pot.profile(profile)
+        p.profile_read(reset=True)
+        p.profile(profile)
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
@@ -501,14 +566,14 @@ def run_ours(args):
         for k in range(args.steps):
             flush.fill_(k & 0xff)        # evict the previous step's data from L2
             starts[k].record(stream)
-            pot.energy_forces_into(x, sp, box, mask, E, F)
+            p.energy_forces_into(x, sp, box, mask, E, F)
             ends[k].record(stream)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         t_b = time.time()
-        pot.profile(False)
-        rc = pot.sync_status()
+        p.profile(False)
+        rc = p.sync_status()
         if rc != 0:
             raise RuntimeError(f"device status {rc} after the timed region")
         return [a.elapsed_time(b) for a, b in zip(starts, ends)], t_a, t_b
@@ -526,32 +591,8 @@ def run_ours(args):
     # roofline of the dominant kernel (largest stage time over the timed region)
     peaks, peak_src = measured_peaks()
     clk = clocks.summary(t0, t1)
-    dom = max((k for k in stages if stages[k][1] > 0), key=lambda k: stages[k][0])
-    dom_ms = stages[dom][0] / stages[dom][1]
-    work = stage_work(dom, spec, counts, n_eval, args.precision)
-    roof = None
-    if work is not None:
-        amount, unit, bound = work
-        if unit == "B":
-            achieved = amount / (dom_ms / 1e3) / 1e9
-            peak = float(peaks["hbm_gbs"])
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None}
-        elif bound == "tensor":
-            achieved = amount / (dom_ms / 1e3) / 1e12
-            peak = float(peaks["bf16_tflops"])
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None}
-        else:
-            achieved = amount / (dom_ms / 1e3) / 1e12
-            peak = fp32_alu_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None}
-        roof["traffic"] = recorded_traffic(dom, args.workload)
-        roof.update({"kernel": dom, "launch_ms": dom_ms, "peak_source": peak_src,
-                     "work_per_launch": amount, "work_unit": unit,
-                     "timing": "CUDA events around the kernel on its launching stream, "
-                               "second pass of the same K steps"})
+    path = pot.network_path()
+    roof = roofline(stages, spec, counts, n_eval, path, peaks, peak_src, args.workload)
 
     # end to end through the host entry point (pinned host buffers, copies inside)
     e2e = None
@@ -575,6 +616,50 @@ def run_ours(args):
         if dist is not None:
             # whole-job e2e rate: every rank's replica, limited by the slowest rank
             e2e["value"] = world * n_eval / max_over_ranks(n_eval / e2e["value"], dist, dev)
+
+    # accuracy against the FP64 oracle on a seeded sample of (ML-region) atoms
+    errors = None
+    idx = None
+    if args.oracle_atoms > 0 and rank == 0:
+        import oracle
+        rng = np.random.Generator(np.random.PCG64(11))
+        ml = np.nonzero(s.mask)[0] if s.mask is not None else np.arange(s.n_atoms)
+        idx = np.sort(rng.choice(ml, size=min(args.oracle_atoms, ml.size), replace=False))
+        t_o = time.perf_counter()
+        ref = oracle.Model(spec, w).sample(s.coords, s.species, idx, s.box, s.mask)
+        t_o = time.perf_counter() - t_o
+        d = {"coords": x, "species": sp, "box": box, "mask": mask}
+        errors = {"sample": f"{idx.size} atoms of {args.workload} drawn with PCG64(11) among "
+                            f"the ML-region atoms; oracle time {t_o:.1f} s",
+                  path: oracle_errors(pot.energy_forces_batch([d], atom_energies=True)[0],
+                                      ref, idx)}
+
+    # the BF16-network path on the same workload, beside an FP32 headline
+    beside = None
+    if args.precision != "bf16" and not args.no_bf16_beside:
+        pb = Potential(spec, w, precision="bf16")
+        pb.energy_forces(x, sp, box, mask)
+        for _ in range(args.warmup):
+            pb.energy_forces_into(x, sp, box, mask, E, F)
+        assert pb.sync_status() == 0
+        b_ms, _, _ = timed_steps(False, pb)
+        b_value, b_total = whole_job_rate(n_eval, args.steps, sum(b_ms), dist, dev)
+        timed_steps(True, pb)
+        b_stages = pb.profile_read(reset=True)
+        beside = {"precision": "bf16", "value": b_value, "unit": UNIT,
+                  "ms_per_step": b_total / args.steps,
+                  "latency_ms": {"p50": float(np.percentile(b_ms, 50)),
+                                 "p99": float(np.percentile(b_ms, 99))},
+                  "roofline": roofline(b_stages, spec, counts, n_eval, "bf16", peaks, peak_src,
+                                       args.workload),
+                  "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in b_stages.items()
+                                         if v[1]}}
+        if errors is not None:
+            d = {"coords": x, "species": sp, "box": box, "mask": mask}
+            errors["bf16"] = oracle_errors(pb.energy_forces_batch([d], atom_energies=True)[0],
+                                           ref, idx)
+            beside["errors_vs_oracle"] = errors["bf16"]
+        pb.close()
 
     md = None
     if args.md_steps > 0 and rank == 0:
@@ -627,7 +712,7 @@ def run_ours(args):
     # energy-only re-evaluation of a batch of snapshots (reweighting, no forces)
     snap = None
     if args.md_steps > 0 and rank == 0:
-        n_frames = 16
+        n_frames = 16 if s.n_atoms <= 20000 else 4
         gen = torch.Generator(device=dev).manual_seed(12)
         frames = [{"coords": x + 0.05 * torch.randn(x.shape, device=dev, generator=gen),
                    "species": sp, "box": box, "mask": mask} for _ in range(n_frames)]
@@ -697,15 +782,23 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "bf16-mlp/f32",
+        "dtype": "bf16-mlp/f32" if path == "bf16" else "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload),
                    "atoms_per_step": n_eval, "systems_per_step": 1,
                    "parallelism": f"replicas x{world}",
-                   "l2": "flushed between steps (512 MB write)", "precision": args.precision},
+                   "l2": "flushed between steps (512 MB write)", "precision": args.precision,
+                   "network_path": {"fp32_split": "tensor cores, FP32 operands split into "
+                                                  "two BF16 parts, three products per term, "
+                                                  "FP32 accumulation",
+                                    "fp32_simt": "FP32 FMA pipes",
+                                    "bf16": "tensor cores, BF16 operands, FP32 "
+                                            "accumulation"}[path]},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "roofline": roof,
+        "errors_vs_oracle": errors,
+        "bf16_beside": beside,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,

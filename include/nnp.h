@@ -56,11 +56,19 @@ enum {
   NNP_ERR_UNSUPPORTED = 10    /* hyper-parameters outside what the kernels implement   */
 };
 
-/* precision of the per-species networks */
+/* precision of the per-species networks (AEVs, their backward and the forces
+ * are FP32 in every mode; energies and virials are reduced in FP64) */
 enum {
-  NNP_FP32 = 0,      /* FP32 everywhere; FP64 energy / virial reductions               */
-  NNP_BF16_MLP = 1   /* network layers on tcgen05 tensor cores, BF16 operands and
-                        FP32 accumulation; AEVs and their backward stay FP32            */
+  NNP_FP32 = 0,       /* FP32-accurate networks; the library picks the path:
+                         NNP_FP32_SPLIT for ensembles, NNP_FP32_SIMT otherwise     */
+  NNP_BF16_MLP = 1,   /* network layers on tcgen05 tensor cores, BF16 operands and
+                         FP32 accumulation                                         */
+  NNP_FP32_SPLIT = 2, /* network layers on tcgen05 tensor cores with every FP32
+                         operand split into two BF16 parts, x = hi + lo, and the
+                         three products hi*hi + lo*hi + hi*lo accumulated in FP32
+                         (the "bf16x3" scheme of Henry, Tang and Heinecke, ARITH
+                         2019): about 16 significant bits per operand           */
+  NNP_FP32_SIMT = 3   /* network layers in FP32 on the FMA pipes                  */
 };
 
 typedef struct nnp_handle nnp_handle;
@@ -137,7 +145,8 @@ typedef struct {
  * library).  hbm_budget_bytes bounds the work arena (0 = no bound); the arena is
  * grown on demand in proportion to the number of atoms, as in the paper's
  * bounded upfront buffer (Sec. "Massive Parallelism within Tinker-HP").
- * precision: NNP_FP32 or NNP_BF16_MLP.  On success *out holds the handle. */
+ * precision: one of the NNP_FP32* modes or NNP_BF16_MLP (enum above).  On
+ * success *out holds the handle. */
 int nnp_create(const nnp_species_t* species, const nnp_aev_params_t* aev,
                const nnp_weights_t* weights, int precision, size_t hbm_budget_bytes,
                nnp_handle** out);
@@ -286,6 +295,9 @@ int nnp_sync_status(nnp_handle* h, void* stream);
 
 /* Length of the atomic environment vector. */
 int nnp_aev_dim(const nnp_handle* h);
+/* The network path a handle runs: NNP_FP32_SPLIT, NNP_FP32_SIMT or NNP_BF16_MLP
+ * (NNP_FP32 resolves to one of the first two at nnp_create); -1 for a null handle. */
+int nnp_network_path(const nnp_handle* h);
 
 /* Number of kernels the last compute call enqueued (for launch accounting). */
 int nnp_last_launch_count(const nnp_handle* h);

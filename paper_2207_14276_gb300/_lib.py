@@ -25,6 +25,10 @@ NNP_PENDING = 9
 NNP_ERR_UNSUPPORTED = 10
 NNP_FP32 = 0
 NNP_BF16_MLP = 1
+NNP_FP32_SPLIT = 2
+NNP_FP32_SIMT = 3
+PRECISIONS = {"fp32": NNP_FP32, "bf16": NNP_BF16_MLP, "fp32_split": NNP_FP32_SPLIT,
+              "fp32_simt": NNP_FP32_SIMT}
 
 STATUS_NAMES = {
     0: "NNP_OK", 1: "NNP_ERR_ARG", 2: "NNP_ERR_SPECIES", 3: "NNP_ERR_BOX_TOO_SMALL",
@@ -41,7 +45,7 @@ EXPORTS = (
     "nnp_server_create", "nnp_server_destroy", "nnp_server_register", "nnp_server_submit",
     "nnp_server_poll", "nnp_server_stats", "nnp_force_vjp_batch", "nnp_force_vjp",
     "nnp_n_weights", "nnp_debug_wait_probe", "nnp_set_skin", "nnp_list_stats",
-    "nnp_integrate", "nnp_noalloc_max_atoms", "nnp_debug_cell_grid",
+    "nnp_integrate", "nnp_noalloc_max_atoms", "nnp_debug_cell_grid", "nnp_network_path",
 )
 
 
@@ -113,6 +117,7 @@ def lib():
     L.nnp_energy_forces_host.argtypes = [P, i64, P, P, P, P, P, P, P]
     L.nnp_sync_status.argtypes = [P, P]
     L.nnp_aev_dim.argtypes = [P]
+    L.nnp_network_path.argtypes = [P]
     L.nnp_last_launch_count.argtypes = [P]
     L.nnp_last_error.restype = ctypes.c_char_p
     L.nnp_last_error.argtypes = []

@@ -248,11 +248,17 @@ __device__ __forceinline__ void decode_pair_diag(int t, int same, int c, int cu,
   }
 }
 
-// one AEV element: the FP32 row, or on the tensor-core path (Gh != null) only
-// the BF16 row its first layer reads
-__device__ __forceinline__ void put_g(float* G, uint16_t* Gh, int f, float v) {
-  if (Gh) Gh[f] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
-  else G[f] = v;
+// one AEV element: the FP32 row, or on the tensor-core paths (Gh != null) only
+// what their first layer reads: the BF16 row, and on the split path (Gl != null)
+// also the low part bf16(v - bf16(v))
+__device__ __forceinline__ void put_g(float* G, uint16_t* Gh, uint16_t* Gl, int f, float v) {
+  if (Gh) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    Gh[f] = __bfloat16_as_ushort(h);
+    if (Gl) Gl[f] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+  } else {
+    G[f] = v;
+  }
 }
 
 // after the call lane l holds the warp sum of v[l]
@@ -289,6 +295,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
   const size_t row = (size_t)ws.pos_slot[p] * ac.Dp;
   float* G = ws.aev + row;
   uint16_t* Gh = ws.aev_h ? ws.aev_h + row : nullptr;
+  uint16_t* Gl = ws.aev_l ? ws.aev_l + row : nullptr;
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
@@ -317,7 +324,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
       acc = fmaf(fast_exp2(cr_ * x * x), q.y, acc);
     }
     acc += __shfl_xor_sync(kFull, acc, 16);
-    if (lane < 16) put_g(G, Gh, s * kNR + lane, acc);
+    if (lane < 16) put_g(G, Gh, Gl, s * kNR + lane, acc);
   }
   // ---- angular, Eq. 5
   const float ca_ = -ac.eta_a * kLog2e;
@@ -330,7 +337,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
       const int fb = ac.S * kNR + pidx * 32;
       if (n_tri == 0) {
-        put_g(G, Gh, fb + lane, 0.f);
+        put_g(G, Gh, Gl, fb + lane, 0.f);
         continue;
       }
       const float inv_cu = 1.f / (float)max(cu, 1);
@@ -363,9 +370,9 @@ k_aev_fwd(Ws ws, AevConst ac) {
           }
         }
       }
-      put_g(G, Gh, fb + lane, transpose_reduce32(acc, lane));
+      put_g(G, Gh, Gl, fb + lane, transpose_reduce32(acc, lane));
     }
-  for (int f = ac.D + lane; f < ac.Dp; f += 32) put_g(G, Gh, f, 0.f);
+  for (int f = ac.D + lane; f < ac.Dp; f += 32) put_g(G, Gh, Gl, f, 0.f);
 }
 
 template <int ZETA, bool VIR>

@@ -30,7 +30,7 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
                   float alpha, cudaStream_t st, int* n_launch, StageHook* hook, void* state,
                   bool energy_only);
 int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, int row_cap,
-                   const float* aev, float* dEdG, void** state);
+                   const float* aev, float* dEdG, bool split, void** state);
 void mlp_tc_release(void* state);
 void launch_aev_to_bf16(const Ws& ws, int n_in, const AevConst& ac, void* out, cudaStream_t st);
 void launch_wait_probe(int* status, unsigned limit, cudaStream_t st);
@@ -54,10 +54,18 @@ int fail(int code, const std::string& msg) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// how the per-species networks run
+enum NetPath : int {
+  kNetSimt = 0,    // FP32 FMA: the fused kernel (one network) or six SIMT GEMMs
+  kNetBf16 = 1,    // tcgen05 GEMMs on BF16 operands
+  kNetSplit = 2,   // tcgen05 GEMMs on split BF16 operands (hi + lo), FP32-accurate
+};
+
 struct Model {
   std::atomic<int> refs{1};
   int device = 0;
   int precision = NNP_FP32;
+  int net = kNetSimt;
   AevConst ac{};
   MlpDims md{};
   float alpha = 0.1f;
@@ -85,6 +93,7 @@ struct nnp_handle {
   double* out_host = nullptr;  // pinned [10]: energy and virial of a host-buffer call
   int last_launches = 0;
   int last_n_in = 0;
+  bool last_aev_fp32 = true;  // the last call wrote the FP32 AEV rows (else the BF16 planes)
   void* tc_state = nullptr;
   // host-call staging
   void* stage = nullptr;
@@ -132,7 +141,9 @@ int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
   if (!(a->cos_scale > 0) || a->cos_scale > 1) return fail(NNP_ERR_ARG, "cos_scale must be in (0, 1]");
   if (w->n_layers != 4 || !w->widths || !w->params || w->n_ensemble < 1)
     return fail(NNP_ERR_UNSUPPORTED, "networks must have 4 layers");
-  if (precision != NNP_FP32 && precision != NNP_BF16_MLP) return fail(NNP_ERR_ARG, "bad precision");
+  if (precision != NNP_FP32 && precision != NNP_BF16_MLP && precision != NNP_FP32_SPLIT &&
+      precision != NNP_FP32_SIMT)
+    return fail(NNP_ERR_ARG, "bad precision");
   AevConst& ac = m->ac;
   ac.S = S;
   ac.D = S * kNR + S * (S + 1) / 2 * kNA * kNZ;
@@ -159,6 +170,12 @@ int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
   m->alpha = w->celu_alpha;
   if (!(m->alpha > 0)) return fail(NNP_ERR_ARG, "celu_alpha must be positive");
   m->precision = precision;
+  // FP32 accuracy: ensembles on the split tensor-core path (their network FLOPs
+  // dominate), one-network models on the fused FP32 kernel
+  m->net = precision == NNP_BF16_MLP     ? kNetBf16
+           : precision == NNP_FP32_SPLIT ? kNetSplit
+           : precision == NNP_FP32_SIMT  ? kNetSimt
+           : (w->n_ensemble > 1 ? kNetSplit : kNetSimt);
   CU_TRY(cudaGetDevice(&m->device));
 
   // unpack the flat parameter vector into the kernel layouts
@@ -229,27 +246,38 @@ int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
   if ((rc = upf(W2T, &m->mw.W2T))) return rc;
   if ((rc = upf(W1Tcat, &m->mw.W1Tcat))) return rc;
   if ((rc = upload(ebias.data(), S * sizeof(double), reinterpret_cast<void**>(&m->ebias)))) return rc;
-  if (precision == NNP_BF16_MLP) {
-    // BF16 copies of the GEMM operands (round to nearest even)
-    auto to_bf16 = [](const std::vector<float>& v) {
-      std::vector<uint16_t> o(v.size());
+  if (m->net != kNetSimt) {
+    // BF16 copies of the GEMM operands (round to nearest even); the split path
+    // also keeps the rounded remainders w - bf16(w)
+    auto bf16_bits = [](float x) {
+      uint32_t u;
+      std::memcpy(&u, &x, 4);
+      return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+    };
+    auto bf16_value = [](uint16_t b) {
+      const uint32_t u = (uint32_t)b << 16;
+      float x;
+      std::memcpy(&x, &u, 4);
+      return x;
+    };
+    auto upb = [&](const std::vector<float>& v, void** hi, void** lo) {
+      std::vector<uint16_t> h(v.size()), l(lo ? v.size() : 0);
       for (size_t i = 0; i < v.size(); ++i) {
-        uint32_t u;
-        std::memcpy(&u, &v[i], 4);
-        o[i] = (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+        h[i] = bf16_bits(v[i]);
+        if (lo) l[i] = bf16_bits(v[i] - bf16_value(h[i]));
       }
-      return o;
+      int r = upload(h.data(), h.size() * sizeof(uint16_t), hi);
+      if (r == NNP_OK && lo) r = upload(l.data(), l.size() * sizeof(uint16_t), lo);
+      return r;
     };
-    auto upb = [&](const std::vector<float>& v, void** dst) {
-      std::vector<uint16_t> b = to_bf16(v);
-      return upload(b.data(), b.size() * sizeof(uint16_t), dst);
-    };
-    if ((rc = upb(W1cat, &m->mw.W1cat_h))) return rc;
-    if ((rc = upb(W2, &m->mw.W2_h))) return rc;
-    if ((rc = upb(W3, &m->mw.W3_h))) return rc;
-    if ((rc = upb(W3T, &m->mw.W3T_h))) return rc;
-    if ((rc = upb(W2T, &m->mw.W2T_h))) return rc;
-    if ((rc = upb(W1Tcat, &m->mw.W1Tcat_h))) return rc;
+    const bool sp = m->net == kNetSplit;
+    MlpWeights& mw = m->mw;
+    if ((rc = upb(W1cat, &mw.W1cat_h, sp ? &mw.W1cat_l : nullptr))) return rc;
+    if ((rc = upb(W2, &mw.W2_h, sp ? &mw.W2_l : nullptr))) return rc;
+    if ((rc = upb(W3, &mw.W3_h, sp ? &mw.W3_l : nullptr))) return rc;
+    if ((rc = upb(W3T, &mw.W3T_h, sp ? &mw.W3T_l : nullptr))) return rc;
+    if ((rc = upb(W2T, &mw.W2T_h, sp ? &mw.W2T_l : nullptr))) return rc;
+    if ((rc = upb(W1Tcat, &mw.W1Tcat_h, sp ? &mw.W1Tcat_l : nullptr))) return rc;
   }
   return NNP_OK;
 }
@@ -319,24 +347,32 @@ size_t carve(nnp_handle* h, char* base) {
     ws.nbs_a = nullptr;
   }
   ws.half_skin = 0.5f * h->skin;
-  const bool bf16 = (m.precision == NNP_BF16_MLP);
-  const size_t esz = bf16 ? 2 : 4;
+  const bool tc = (m.net != kNetSimt), split = (m.net == kNetSplit);
+  const size_t esz = tc ? 2 : 4;
   MlpBufs& mb = h->mb;
   mb = MlpBufs{};
-  // the fused FP32 kernel keeps its activations on chip; the tensor-core path
-  // rebuilds CELU' from the activations and stores no derivative buffers
-  if (bf16 || !mlp_fused_supported(m.md)) {
+  // the fused FP32 kernel keeps its activations on chip; the tensor-core paths
+  // rebuild CELU' from the activations and store no derivative buffers; the
+  // split path stores every activation as two BF16 planes (high, low)
+  if (tc || !mlp_fused_supported(m.md)) {
     mb.H1 = c.take<char>(rows * E * m.md.h1 * esz);
     mb.H2 = c.take<char>(rows * E * m.md.h2 * esz);
     mb.d3 = c.take<char>(rows * E * m.md.h3 * esz);
-    if (!bf16) {
+    if (!tc) {
       mb.D1 = c.take<char>(rows * E * m.md.h1 * esz);
       mb.D2 = c.take<char>(rows * E * m.md.h2 * esz);
     }
+    if (split) {
+      mb.H1l = c.take<char>(rows * E * m.md.h1 * 2);
+      mb.H2l = c.take<char>(rows * E * m.md.h2 * 2);
+      mb.d3l = c.take<char>(rows * E * m.md.h3 * 2);
+    }
   }
   mb.e_row = c.take<float>((size_t)E * rows);
-  mb.aev_h = bf16 ? c.take<char>(rows * Dp * 2) : nullptr;
+  mb.aev_h = tc ? c.take<char>(rows * Dp * 2) : nullptr;
+  mb.aev_l = split ? c.take<char>(rows * Dp * 2) : nullptr;
   ws.aev_h = static_cast<uint16_t*>(mb.aev_h);
+  ws.aev_l = static_cast<uint16_t*>(mb.aev_l);
   return align_up(c.off, 256);
 }
 
@@ -377,9 +413,9 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
   // raise-only: other handles of the process may need larger limits
   CU_TRY(aev_ensure_smem(h->ws));
   CU_TRY(mlp_fused_ensure_smem(h->model->md));
-  if (h->model->precision == NNP_BF16_MLP) {
+  if (h->model->net != kNetSimt) {
     int rc = mlp_tc_prepare(h->model->md, h->model->mw, h->mb, h->ws.row_cap, h->ws.aev,
-                            h->ws.dEdG, &h->tc_state);
+                            h->ws.dEdG, h->model->net == kNetSplit, &h->tc_state);
     if (rc) return fail(rc, "tensor-core GEMM set-up (tensor maps, launch limits) failed");
   }
   h->dirty = false;
@@ -524,7 +560,7 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     bool energy_only = true;
     for (int b = 0; b < n_sys; ++b) energy_only &= (sy[b].forces == nullptr && sy[b].virial == nullptr);
     StageHook hook{h, st};
-    if (m.precision == NNP_BF16_MLP) {
+    if (m.net != kNetSimt) {
       rc = launch_mlp_tc(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, h->tc_state, energy_only);
       if (rc) return rc;
     } else {
@@ -559,6 +595,7 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
   Ws& ws = h->ws;
   ws.n_sys = n_sys;
   ws.n_in = n_in;
+  h->last_aev_fp32 = (m.net == kNetSimt);
   // per-chunk descriptors as kernel parameters
   std::vector<BatchParams> chunks;
   int in_base = 0;
@@ -1040,7 +1077,7 @@ extern "C" int nnp_force_vjp_batch(nnp_handle* h, int n_sys, const nnp_vjp_syste
   g_err.clear();
   if (!h || n_sys < 1 || !vs || !dL_dweights) return fail(NNP_ERR_ARG, "bad argument");
   const Model& m = *h->model;
-  if (m.precision != NNP_FP32) return fail(NNP_ERR_UNSUPPORTED, "the force VJP runs FP32 handles");
+  if (m.net == kNetBf16) return fail(NNP_ERR_UNSUPPORTED, "the force VJP runs FP32 handles");
   std::vector<nnp_system_t> sy(n_sys);
   long long n_in_ll = 0;
   for (int b = 0; b < n_sys; ++b) {
@@ -1058,9 +1095,14 @@ extern "C" int nnp_force_vjp_batch(nnp_handle* h, int n_sys, const nnp_vjp_syste
   if (rc) return rc;
   if ((rc = ensure_vjp(h))) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ws& ws = h->ws;
-  ws.n_sys = n_sys;
-  ws.n_in = n_in;
+  h->ws.n_sys = n_sys;
+  h->ws.n_in = n_in;
+  // the VJP's FP32 network chain reads the FP32 AEV rows (a split handle's
+  // energy calls write only the two BF16 planes)
+  Ws ws = h->ws;
+  ws.aev_h = nullptr;
+  ws.aev_l = nullptr;
+  h->last_aev_fp32 = true;
   // the force VJP builds its own lists at the cutoffs in the shared buffers:
   // persistent lists of energy calls are rebuilt on the next such call
   struct SkinOff {
@@ -1145,6 +1187,11 @@ extern "C" int64_t nnp_n_weights(const nnp_handle* h) {
 }
 
 int nnp_aev_dim(const nnp_handle* h) { return h ? h->model->ac.D : -1; }
+int nnp_network_path(const nnp_handle* h) {
+  if (!h) return -1;
+  const int net = h->model->net;
+  return net == kNetBf16 ? NNP_BF16_MLP : net == kNetSplit ? NNP_FP32_SPLIT : NNP_FP32_SIMT;
+}
 int nnp_last_launch_count(const nnp_handle* h) { return h ? h->last_launches : -1; }
 
 int nnp_set_skin(nnp_handle* h, float skin) {
@@ -1224,17 +1271,16 @@ const char* nnp_profile_stage_name(int i) {
 // out: device float [n_in_total, D]; rows of atoms outside the mask untouched.
 int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream) {
   if (!h || !h->arena || !out) return fail(NNP_ERR_ARG, "bad argument");
+  const bool planes = which == 0 && !h->last_aev_fp32;
   const float* src = which == 0 ? h->ws.aev : h->ws.dEdG;
-  const uint16_t* src_h = which == 0 ? h->ws.aev_h : nullptr;
-  launch_gather_rows(h->ws, h->last_n_in, src, src_h, h->model->ac.Dp, h->model->ac.D, out,
+  const uint16_t* src_h = planes ? h->ws.aev_h : nullptr;
+  const uint16_t* src_l = planes ? h->ws.aev_l : nullptr;
+  launch_gather_rows(h->ws, h->last_n_in, src, src_h, src_l, h->model->ac.Dp, h->model->ac.D, out,
                      static_cast<cudaStream_t>(stream));
   CU_TRY(cudaGetLastError());
   return NNP_OK;
 }
 
-// Neighbour lists of the last call in input-atom order: out[i][t] = input index
-// of the t-th neighbour of atom i (radial list, or angular if angular != 0),
-// -1 past the end.  out: device int32 [n_in_total, cap].
 int nnp_debug_cell_grid(const float* len, float rc, int64_t n_atoms, int* nc_out,
                         int64_t* cells_out) {
   g_err.clear();
@@ -1245,6 +1291,9 @@ int nnp_debug_cell_grid(const float* len, float rc, int64_t n_atoms, int* nc_out
   return NNP_OK;
 }
 
+// Neighbour lists of the last call in input-atom order: out[i][t] = input index
+// of the t-th neighbour of atom i (radial list, or angular if angular != 0),
+// -1 past the end.  out: device int32 [n_in_total, cap].
 int nnp_debug_neighbors(nnp_handle* h, int angular, int cap, int* out, void* stream) {
   if (!h || !h->arena || !out || cap <= 0) return fail(NNP_ERR_ARG, "bad argument");
   launch_gather_nbrs(h->ws, h->last_n_in, angular, cap, out, static_cast<cudaStream_t>(stream));
@@ -1352,7 +1401,7 @@ extern "C" int nnp_energy_forces_noalloc(nnp_handle* h, int64_t n_atoms, const f
   g_err.clear();
   if (!h) return fail(NNP_ERR_ARG, "null handle");
   const Model& m = *h->model;
-  if (m.precision != NNP_FP32)
+  if (m.net == kNetBf16)
     return fail(NNP_ERR_UNSUPPORTED, "the allocation-free entry point runs FP32 handles only");
   nnp_system_t s{};
   s.n_atoms = n_atoms;
@@ -1453,7 +1502,7 @@ extern "C" int nnp_noalloc_max_atoms(const nnp_handle* h, int64_t* max_atoms) {
   g_err.clear();
   if (!h || !max_atoms) return fail(NNP_ERR_ARG, "null argument");
   const Model& m = *h->model;
-  if (m.precision != NNP_FP32) {
+  if (m.net == kNetBf16) {
     *max_atoms = 0;
     return NNP_OK;
   }

@@ -53,16 +53,25 @@ __global__ void k_finalize(Ws ws, const float* e_row, int E, int e_row_net,
 }
 
 // out[src_atom][f] = rows[slot][f] for f < D (rows of the batch's input atoms)
-// rows: FP32, or (rows_h != null) BF16 bit patterns widened to FP32
-__global__ void k_gather_rows(Ws ws, const float* rows, const uint16_t* rows_h, int ld, int D,
-                              float* out) {
+// rows: FP32, or (rows_h != null) BF16 bit patterns widened to FP32, plus the
+// low BF16 parts rows_l of the split path if given
+__global__ void k_gather_rows(Ws ws, const float* rows, const uint16_t* rows_h,
+                              const uint16_t* rows_l, int ld, int D, float* out) {
   const int p = blockIdx.x;
   if (p >= ws.totals[0]) return;
   const int slot = ws.pos_slot[p];
   const int gi = ws.pos_src[p];
-  for (int f = threadIdx.x; f < D; f += blockDim.x)
-    out[(size_t)gi * D + f] = rows_h ? __uint_as_float((unsigned)rows_h[(size_t)slot * ld + f] << 16)
-                                     : rows[(size_t)slot * ld + f];
+  for (int f = threadIdx.x; f < D; f += blockDim.x) {
+    const size_t i = (size_t)slot * ld + f;
+    float v;
+    if (rows_h) {
+      v = __uint_as_float((unsigned)rows_h[i] << 16);
+      if (rows_l) v += __uint_as_float((unsigned)rows_l[i] << 16);
+    } else {
+      v = rows[i];
+    }
+    out[(size_t)gi * D + f] = v;
+  }
 }
 
 // out[src_atom][t] = input index of neighbour t (species-sorted), -1 past the count
@@ -86,10 +95,10 @@ void launch_finalize_e(const Ws& ws, int n_in, const float* e_row, int E, int e_
   k_finalize<<<(n_in + 255) / 256, 256, 0, st>>>(ws, e_row, E, e_row_net, ebias);
 }
 
-void launch_gather_rows(const Ws& ws, int n_in, const float* rows, const uint16_t* rows_h, int ld,
-                        int D, float* out, cudaStream_t st) {
+void launch_gather_rows(const Ws& ws, int n_in, const float* rows, const uint16_t* rows_h,
+                        const uint16_t* rows_l, int ld, int D, float* out, cudaStream_t st) {
   if (n_in <= 0) return;
-  k_gather_rows<<<n_in, 128, 0, st>>>(ws, rows, rows_h, ld, D, out);
+  k_gather_rows<<<n_in, 128, 0, st>>>(ws, rows, rows_h, rows_l, ld, D, out);
 }
 
 void launch_gather_nbrs(const Ws& ws, int n_in, int angular, int cap_out, int* out,

@@ -49,6 +49,8 @@ struct MlpWeights {
   float* ebias;                  // [S] mean_e b4 + species shift
   // bf16 copies (same layouts), null for the FP32 path
   void* W1cat_h; void* W2_h; void* W3_h; void* W3T_h; void* W2T_h; void* W1Tcat_h;
+  // split path: the low parts w - bf16(w), rounded to bf16 (same layouts)
+  void* W1cat_l; void* W2_l; void* W3_l; void* W3T_l; void* W2T_l; void* W1Tcat_l;
 };
 
 // activation buffers
@@ -60,6 +62,9 @@ struct MlpBufs {
   void* d3;   // [rows][E*h3]
   float* e_row;  // [E][rows]
   void* aev_h;   // bf16 copy of the AEV (tensor-core path)
+  // split path: low bf16 parts of the AEV, H1, H2 and d3 (same layouts as the
+  // high parts, which are aev_h, H1, H2 and d3)
+  void* aev_l; void* H1l; void* H2l; void* d3l;
 };
 
 // optional per-stage timing callback of the runtime (events on the stream)

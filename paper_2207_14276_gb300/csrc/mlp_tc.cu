@@ -56,8 +56,9 @@ struct TcArgs {
   const float* bias; long long bias_s, bias_e;
   const float* w4; long long w4_s, w4_e;
   void* out; int ldo; int out_net;          // bf16 (or fp32 for kEpiStore)
-  void* out2;                               // unused on this path
+  void* out2;                               // split path: low parts of out (same layout)
   const void* aux; int ld_aux; int aux_net; // bf16 stored activation (kEpiMul)
+  const void* aux2;                         // split path: low parts of aux
   float* e_row; int e_row_net;
   float alpha;
   const int* seg_start;
@@ -177,6 +178,26 @@ __device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float (&
   d[1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
+// split path: v = hi + lo with hi = bf16(v) and lo = bf16(v - hi), 16 values
+__device__ __forceinline__ void store_split16(__nv_bfloat16* hi, __nv_bfloat16* lo,
+                                              const float (&v)[16]) {
+  uint32_t wh[8], wl[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    wh[i] = *reinterpret_cast<const uint32_t*>(&h);
+    wl[i] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+  uint4* dh = reinterpret_cast<uint4*>(hi);
+  uint4* dl = reinterpret_cast<uint4*>(lo);
+  dh[0] = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+  dh[1] = make_uint4(wh[4], wh[5], wh[6], wh[7]);
+  dl[0] = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+  dl[1] = make_uint4(wl[4], wl[5], wl[6], wl[7]);
+}
+
 __device__ __forceinline__ void load_bf16x16(const __nv_bfloat16* src, float (&v)[16]) {
   const uint4* s = reinterpret_cast<const uint4*>(src);
   uint4 q[2] = {s[0], s[1]};
@@ -207,9 +228,14 @@ __device__ __forceinline__ Tile tile_of(int t, int n_tiles_n, int row_tiles, int
   return tl;
 }
 
-template <int EPI>
+// SPLIT: every operand comes as a high and a low BF16 part (ta/tb and ta2/tb2);
+// a stage holds A_hi, A_lo, B_hi, B_lo and every 16-wide K step issues the
+// three products A_hi B_hi + A_lo B_hi + A_hi B_lo into the FP32 accumulator.
+template <int EPI, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
-k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, TcArgs g) {
+k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+          const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb2,
+          TcArgs g) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], done_bar;
@@ -221,7 +247,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   const int kStages = g.stages;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int a_bytes = kBM * kBK * 2, b_bytes = g.n_tile * kBK * 2;
-  const int stage_bytes = a_bytes + b_bytes;   // multiple of 1024
+  constexpr int kParts = SPLIT ? 2 : 1;
+  const int stage_bytes = kParts * (a_bytes + b_bytes);   // multiple of 1024
   volatile int* abort_flag = &abort_sh;
 
   if (threadIdx.x == 0) {
@@ -267,10 +294,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           const unsigned round = it / kStages;
           if (it >= kStages && !mbar_wait(&empty_bar[st], (round - 1) & 1, abort_flag)) { ok = false; break; }
           uint8_t* sa = smem + st * stage_bytes;
-          uint8_t* sb = sa + a_bytes;
+          uint8_t* sb = sa + kParts * a_bytes;
           mbar_expect_tx(&full_bar[st], (unsigned)stage_bytes);
           tma_load_3d(sa, &ta, &full_bar[st], kb * kBK, a_c1, tl.m0);
           tma_load_3d(sb, &tb, &full_bar[st], kb * kBK, tl.n0, b_c2);
+          if (SPLIT) {
+            tma_load_3d(sa + a_bytes, &ta2, &full_bar[st], kb * kBK, a_c1, tl.m0);
+            tma_load_3d(sb + b_bytes, &tb2, &full_bar[st], kb * kBK, tl.n0, b_c2);
+          }
         }
       }
       // every issued copy has landed before the CTA may exit
@@ -293,12 +324,18 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           if (!mbar_wait(&full_bar[st], (it / kStages) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + st * stage_bytes);
-          const uint32_t sb = sa + a_bytes;
+          const uint32_t sb = sa + kParts * a_bytes;
           const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sb);
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk)
+          for (int kk = 0; kk < kBK / 16; ++kk) {
             umma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), g.idesc,
                       (kb > 0 || kk > 0) ? 1u : 0u);
+            if (SPLIT) {
+              const uint64_t adl = sw128_desc(sa + a_bytes), bdl = sw128_desc(sb + b_bytes);
+              umma_bf16(d, adl + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), g.idesc, 1u);
+              umma_bf16(d, ad + (uint64_t)(kk * 2), bdl + (uint64_t)(kk * 2), g.idesc, 1u);
+            }
+          }
           umma_commit(&empty_bar[st]);
         }
         if (ok) umma_commit(&tfull_bar[ab]);
@@ -319,8 +356,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       const int m = tl.m0 + q * 32 + lane;
       // the backward's stored activations do not depend on the MMAs: their loads
       // are issued before the wait for the accumulator
-      uint4 pre[EPI == kEpiMul ? kMaxChunks : 1][2];
-      if (EPI == kEpiMul) {
+      constexpr bool kPre = (EPI == kEpiMul) && !SPLIT;
+      uint4 pre[kPre ? kMaxChunks : 1][2];
+      if (kPre) {
         const __nv_bfloat16* arow = static_cast<const __nv_bfloat16*>(g.aux) + (size_t)m * g.ld_aux +
                                     (size_t)tl.e * g.aux_net + tl.n0;
 #pragma unroll
@@ -359,7 +397,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       tc_fence_after();
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * g.tmem_cols);
       float dot = 0.f;
-#pragma unroll(EPI == kEpiMul ? kMaxChunks : 1)
+#pragma unroll(kPre ? kMaxChunks : 1)
       for (int ci = 0; ci < kMaxChunks; ++ci) {
         const int c0 = half * 16 + 32 * ci;
         if (c0 >= g.n_tile) break;
@@ -394,13 +432,26 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
               v[i] = h;   // CELU' is rebuilt from h where it is needed
             }
           }
-          store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)tl.e * g.out_net + n, v);
+          const size_t o = (size_t)m * g.ldo + (size_t)tl.e * g.out_net + n;
+          if (SPLIT)
+            store_split16(static_cast<__nv_bfloat16*>(g.out) + o, static_cast<__nv_bfloat16*>(g.out2) + o, v);
+          else
+            store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + o, v);
         } else if (EPI == kEpiMul) {
           // aux holds the layer's stored activation h = CELU(z): CELU'(z) = 1 for h > 0,
           // 1 + h / alpha otherwise (exp(z/alpha) = 1 + h/alpha on that branch)
           float a[16];
-          {
-            const uint32_t* w = reinterpret_cast<const uint32_t*>(pre[EPI == kEpiMul ? ci : 0]);
+          const size_t o = (size_t)m * g.ldo + (size_t)tl.e * g.out_net + n;
+          if (SPLIT) {
+            // the stored activation h = hi + lo (about 16 significant bits)
+            const size_t oa = (size_t)m * g.ld_aux + (size_t)tl.e * g.aux_net + n;
+            float al[16];
+            load_bf16x16(static_cast<const __nv_bfloat16*>(g.aux) + oa, a);
+            load_bf16x16(static_cast<const __nv_bfloat16*>(g.aux2) + oa, al);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[i] += al[i];
+          } else {
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(pre[kPre ? ci : 0]);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
@@ -410,7 +461,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           }
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] *= (a[i] > 0.f) ? 1.f : fmaf(a[i], inv_alpha, 1.f);
-          store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo + (size_t)tl.e * g.out_net + n, v);
+          if (SPLIT)
+            store_split16(static_cast<__nv_bfloat16*>(g.out) + o, static_cast<__nv_bfloat16*>(g.out2) + o, v);
+          else
+            store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + o, v);
         } else {
           float4* o = reinterpret_cast<float4*>(static_cast<float*>(g.out) + (size_t)m * g.ldo + n);
 #pragma unroll
@@ -479,7 +533,7 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64
 }
 
 struct TcGemmPlan {
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, ta2, tb2;   // ta2 / tb2: low parts (split path; copies of ta / tb otherwise)
   TcArgs a;
   dim3 grid;
   size_t smem;
@@ -492,6 +546,7 @@ struct TcState {
   const float* aev = nullptr;
   float* e_row = nullptr;
   int row_cap = 0, Dp = 0, E = 1;
+  bool split = false;
 };
 
 int pick_n_tile(int N, int tiles_per_col, bool single, int sms) {
@@ -515,11 +570,13 @@ int tmem_cols_for(int n_tile) {
 }  // namespace
 
 int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, int row_cap,
-                   const float* aev, float* dEdG, void** state_out) {
+                   const float* aev, float* dEdG, bool split, void** state_out) {
   *state_out = nullptr;
   if (!encode_fn()) return NNP_ERR_CUDA;
   if (!mw.W1cat_h || !mb.aev_h) return NNP_ERR_ARG;
+  if (split && (!mw.W1cat_l || !mb.aev_l || !mb.H1l || !mb.H2l || !mb.d3l)) return NNP_ERR_ARG;
   TcState* st = new TcState;
+  st->split = split;
   st->aev_h = mb.aev_h;
   st->aev = aev;
   st->e_row = mb.e_row;
@@ -543,32 +600,40 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     const float* bias; long long bias_s, bias_e;
     const float* w4; long long w4_s, w4_e;
     void* out; int ldo, out_net; void* out2; const void* aux; int ld_aux, aux_net;
+    // split path: low parts of A, B, out and aux
+    const void* A2; const void* B2; void* out_lo; const void* aux_lo;
   };
   std::vector<L> layers = {
       // L1: AEV x [W1 of all members]^T
       {3, kEpiCelu, E * h1, Dp, 1, mb.aev_h, (uint64_t)Dp, 1, (uint64_t)Dp, (uint64_t)Dp,
        mw.W1cat_h, (uint64_t)Dp, (uint64_t)E * h1, (uint64_t)S, 0, mw.b1cat, (long long)E * h1, 0,
-       nullptr, 0, 0, mb.H1, E * h1, 0, mb.D1, nullptr, 0, 0},
+       nullptr, 0, 0, mb.H1, E * h1, 0, mb.D1, nullptr, 0, 0,
+       mb.aev_l, mw.W1cat_l, mb.H1l, nullptr},
       // L2 per member
       {4, kEpiCelu, h2, h1, E, mb.H1, (uint64_t)h1, (uint64_t)E, (uint64_t)h1, (uint64_t)E * h1,
        mw.W2_h, (uint64_t)h1, (uint64_t)h2, (uint64_t)E * S, S, mw.b2, h2, (long long)S * h2,
-       nullptr, 0, 0, mb.H2, E * h2, h2, mb.D2, nullptr, 0, 0},
+       nullptr, 0, 0, mb.H2, E * h2, h2, mb.D2, nullptr, 0, 0,
+       mb.H1l, mw.W2_l, mb.H2l, nullptr},
       // L3 + output dot
       {5, kEpiCeluDot, h3, h2, E, mb.H2, (uint64_t)h2, (uint64_t)E, (uint64_t)h2, (uint64_t)E * h2,
        mw.W3_h, (uint64_t)h2, (uint64_t)h3, (uint64_t)E * S, S, mw.b3, h3, (long long)S * h3,
-       mw.w4, h3, (long long)S * h3, mb.d3, E * h3, h3, nullptr, nullptr, 0, 0},
+       mw.w4, h3, (long long)S * h3, mb.d3, E * h3, h3, nullptr, nullptr, 0, 0,
+       mb.H2l, mw.W3_l, mb.d3l, nullptr},
       // B3: delta2 = (delta3 W3) * CELU'(z2) from H2, written over H2
       {6, kEpiMul, h2, h3, E, mb.d3, (uint64_t)h3, (uint64_t)E, (uint64_t)h3, (uint64_t)E * h3,
        mw.W3T_h, (uint64_t)h3, (uint64_t)h2, (uint64_t)E * S, S, nullptr, 0, 0, nullptr, 0, 0,
-       mb.H2, E * h2, h2, nullptr, mb.H2, E * h2, h2},
+       mb.H2, E * h2, h2, nullptr, mb.H2, E * h2, h2,
+       mb.d3l, mw.W3T_l, mb.H2l, mb.H2l},
       // B2: delta1 = (delta2 W2) * CELU'(z1) from H1, written over H1
       {7, kEpiMul, h1, h2, E, mb.H2, (uint64_t)h2, (uint64_t)E, (uint64_t)h2, (uint64_t)E * h2,
        mw.W2T_h, (uint64_t)h2, (uint64_t)h1, (uint64_t)E * S, S, nullptr, 0, 0, nullptr, 0, 0,
-       mb.H1, E * h1, h1, nullptr, mb.H1, E * h1, h1},
+       mb.H1, E * h1, h1, nullptr, mb.H1, E * h1, h1,
+       mb.H2l, mw.W2T_l, mb.H1l, mb.H1l},
       // B1: dE/dG = [delta1_e] [W1_e / E]   (K = E*h1), FP32 output
       {8, kEpiStore, Dp, E * h1, 1, mb.H1, (uint64_t)E * h1, 1, (uint64_t)E * h1, (uint64_t)E * h1,
        mw.W1Tcat_h, (uint64_t)E * h1, (uint64_t)Dp, (uint64_t)S, 0, nullptr, 0, 0, nullptr, 0, 0,
-       dEdG, Dp, 0, nullptr, nullptr, 0, 0},
+       dEdG, Dp, 0, nullptr, nullptr, 0, 0,
+       mb.H1l, mw.W1Tcat_l, nullptr, nullptr},
   };
   for (const L& l : layers) {
     TcGemmPlan p{};
@@ -580,6 +645,16 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
       delete st;
       return NNP_ERR_CUDA;
     }
+    if (split) {
+      if (!make_map(&p.ta2, l.A2, l.a_d0, l.a_d1, R, l.a_st1, l.a_st2, 1, kBM) ||
+          !make_map(&p.tb2, l.B2, l.b_d0, l.b_d1, l.b_d2, l.b_d0, l.b_d0 * l.b_d1, (uint32_t)nt, 1)) {
+        delete st;
+        return NNP_ERR_CUDA;
+      }
+    } else {
+      p.ta2 = p.ta;
+      p.tb2 = p.tb;
+    }
     TcArgs& a = p.a;
     a.N = l.N; a.K = l.K; a.n_tile = nt; a.n_k = (l.K + kBK - 1) / kBK;
     a.tmem_cols = tmem_cols_for(nt);
@@ -590,17 +665,25 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     a.epi = l.epi;
     a.bias = l.bias; a.bias_s = l.bias_s; a.bias_e = l.bias_e;
     a.w4 = l.w4; a.w4_s = l.w4_s; a.w4_e = l.w4_e;
-    a.out = l.out; a.ldo = l.ldo; a.out_net = l.out_net; a.out2 = l.out2;
+    a.out = l.out; a.ldo = l.ldo; a.out_net = l.out_net;
+    a.out2 = split ? l.out_lo : nullptr;
     a.aux = l.aux; a.ld_aux = l.ld_aux; a.aux_net = l.aux_net;
+    a.aux2 = split ? l.aux_lo : nullptr;
     a.e_row = mb.e_row; a.e_row_net = row_cap;
     // CTAs per SM: as many as the 512 tensor-memory columns hold (two accumulators
     // each), at most two; the shared memory is split between them and never so
     // small that more CTAs could share an SM than its tensor memory holds
-    const int ctas = std::min(2, 512 / (2 * a.tmem_cols));
-    const size_t stage_bytes = (size_t)(kBM * kBK * 2 + nt * kBK * 2);
-    const size_t budget = std::min((size_t)kMaxDynSmem, (size_t)232448 / ctas - 2048);
-    int stages = (int)std::min<size_t>(kMaxStages, (budget - 1024) / stage_bytes);
-    stages = std::min(stages, std::max(a.n_k, 1));
+    // (the split path holds both parts of A and B per stage; it takes one CTA per
+    // SM where two would leave each CTA fewer than two stages)
+    const size_t stage_bytes = (size_t)(split ? 2 : 1) * (kBM * kBK * 2 + nt * kBK * 2);
+    auto stages_for = [&](int c) {
+      const size_t budget = std::min((size_t)kMaxDynSmem, (size_t)232448 / c - 2048);
+      const int n = (int)std::min<size_t>(kMaxStages, (budget - 1024) / stage_bytes);
+      return std::min(n, std::max(a.n_k, 1));
+    };
+    int ctas = std::min(2, 512 / (2 * a.tmem_cols));
+    if (split && ctas == 2 && stages_for(2) < std::min(2, a.n_k)) ctas = 1;
+    const int stages = stages_for(ctas);
     if (stages < 1) { delete st; return NNP_ERR_UNSUPPORTED; }
     a.stages = stages;
     size_t sm = (size_t)stages * stage_bytes + 1024;
@@ -612,8 +695,10 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     p.stage_id = l.stage;
     st->plans.push_back(p);
   }
-  const void* fns[4] = {(const void*)k_gemm_tc<kEpiCelu>, (const void*)k_gemm_tc<kEpiCeluDot>,
-                        (const void*)k_gemm_tc<kEpiMul>, (const void*)k_gemm_tc<kEpiStore>};
+  const void* fns[8] = {(const void*)k_gemm_tc<kEpiCelu, false>, (const void*)k_gemm_tc<kEpiCeluDot, false>,
+                        (const void*)k_gemm_tc<kEpiMul, false>, (const void*)k_gemm_tc<kEpiStore, false>,
+                        (const void*)k_gemm_tc<kEpiCelu, true>, (const void*)k_gemm_tc<kEpiCeluDot, true>,
+                        (const void*)k_gemm_tc<kEpiMul, true>, (const void*)k_gemm_tc<kEpiStore, true>};
   for (const void* fn : fns)
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess) {
       delete st;
@@ -644,16 +729,26 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
     a.S = md.S;
     a.status = ws.status;
     if (hook) hook->begin(p.stage_id);
-    switch (a.epi) {
-      case kEpiCelu: k_gemm_tc<kEpiCelu><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a); break;
-      case kEpiCeluDot:
-        // the two epilogue warps of a row add their halves of the dot product
-        cudaMemsetAsync(a.e_row, 0, sizeof(float) * (size_t)md.E * a.e_row_net, st);
-        k_gemm_tc<kEpiCeluDot><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a);
-        break;
-      case kEpiMul: k_gemm_tc<kEpiMul><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a); break;
-      default: k_gemm_tc<kEpiStore><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, a); break;
+    // the two epilogue warps of a row add their halves of the output dot product
+    if (a.epi == kEpiCeluDot) cudaMemsetAsync(a.e_row, 0, sizeof(float) * (size_t)md.E * a.e_row_net, st);
+#define NNP_TC_LAUNCH(EPI_, SPLIT_) \
+  k_gemm_tc<EPI_, SPLIT_><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, p.ta2, p.tb2, a)
+    if (s->split) {
+      switch (a.epi) {
+        case kEpiCelu: NNP_TC_LAUNCH(kEpiCelu, true); break;
+        case kEpiCeluDot: NNP_TC_LAUNCH(kEpiCeluDot, true); break;
+        case kEpiMul: NNP_TC_LAUNCH(kEpiMul, true); break;
+        default: NNP_TC_LAUNCH(kEpiStore, true); break;
+      }
+    } else {
+      switch (a.epi) {
+        case kEpiCelu: NNP_TC_LAUNCH(kEpiCelu, false); break;
+        case kEpiCeluDot: NNP_TC_LAUNCH(kEpiCeluDot, false); break;
+        case kEpiMul: NNP_TC_LAUNCH(kEpiMul, false); break;
+        default: NNP_TC_LAUNCH(kEpiStore, false); break;
+      }
     }
+#undef NNP_TC_LAUNCH
     if (hook) hook->end();
   }
   if (n_launch) *n_launch += (int)n_plans;

@@ -111,6 +111,7 @@ struct Ws {
   // AEV / gradient
   float* aev;           // [row_cap][Dp]
   uint16_t* aev_h;      // [row_cap][Dp] BF16 copy (bit patterns) for the tensor-core path, or null
+  uint16_t* aev_l;      // [row_cap][Dp] split path: bf16(G - bf16(G)), or null
   float* dEdG;          // [row_cap][Dp]
   float* atom_e;        // [row_cap] per-row energy (mean over the ensemble, incl. shift)
   float4* f_pos;        // [n_in] forces on packed atoms
@@ -154,8 +155,8 @@ size_t aev_bwd_smem(const Ws& ws, int n_pairs = kMaxSpecies * (kMaxSpecies + 1) 
 // ---- finalize.cu
 void launch_finalize_e(const Ws& ws, int n_in, const float* e_row, int E, int e_row_net,
                        const double* ebias, cudaStream_t st);
-void launch_gather_rows(const Ws& ws, int n_in, const float* rows, const uint16_t* rows_h, int ld,
-                        int D, float* out, cudaStream_t st);
+void launch_gather_rows(const Ws& ws, int n_in, const float* rows, const uint16_t* rows_h,
+                        const uint16_t* rows_l, int ld, int D, float* out, cudaStream_t st);
 void launch_gather_nbrs(const Ws& ws, int n_in, int angular, int cap_out, int* out,
                         cudaStream_t st);
 

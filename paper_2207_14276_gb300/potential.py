@@ -29,7 +29,9 @@ class Potential:
     spec: an object with ``aev`` (n_species, rc_r, eta_r, shf_r, rc_a, eta_a, zeta,
     shf_a, shf_z, cos_scale), ``widths``, ``n_ensemble``, ``celu_alpha`` and
     ``atomic_numbers``; weights: flat float32 vector (layout of include/nnp.h).
-    precision: "fp32" or "bf16" (tensor-core network layers).
+    precision: "fp32" (FP32-accurate; split-BF16 tensor cores for ensembles, the
+    FP32 FMA kernel otherwise), "fp32_split" / "fp32_simt" (force one of those),
+    or "bf16" (tensor-core network layers on BF16 operands).
     """
 
     def __init__(self, spec, weights, precision="fp32", shift=None, hbm_budget=0, _clone_of=None):
@@ -67,7 +69,9 @@ class Potential:
             wt.species_shift = (None if shift_arr is None
                                 else shift_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
             wt.celu_alpha = spec.celu_alpha
-            prec = _lib.NNP_BF16_MLP if precision == "bf16" else _lib.NNP_FP32
+            if precision not in _lib.PRECISIONS:
+                raise ValueError(f"precision must be one of {sorted(_lib.PRECISIONS)}")
+            prec = _lib.PRECISIONS[precision]
             check(L.nnp_create(ctypes.byref(sp), ctypes.byref(ap), ctypes.byref(wt), prec,
                                hbm_budget, ctypes.byref(h)))
         self._h = h
@@ -95,6 +99,11 @@ class Potential:
 
     def sync_status(self, stream=None):
         return lib().nnp_sync_status(self._h, _stream_ptr(stream))
+
+    def network_path(self):
+        """'fp32_split', 'fp32_simt' or 'bf16': the path this handle's networks run."""
+        code = lib().nnp_network_path(self._h)
+        return {v: k for k, v in _lib.PRECISIONS.items()}[code]
 
     def launch_count(self):
         return lib().nnp_last_launch_count(self._h)

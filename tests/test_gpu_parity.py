@@ -111,8 +111,11 @@ def test_dense_box_neighbourhood_beyond_the_stage(torch_cuda):
     compare_neighbours(pot, s, pot.spec)
 
 
-def test_water9000_fp32(torch_cuda):
-    pot, orc = make("ani4")
+@pytest.mark.parametrize("precision", ["fp32", "fp32_split"])
+def test_water9000_fp32(torch_cuda, precision):
+    # "fp32" runs the fused FP32 kernel for this one-network model; "fp32_split"
+    # the tensor-core layers on split BF16 operands (three products per term)
+    pot, orc = make("ani4", precision=precision)
     systems, _, _ = synth.workload("water9000")
     s = systems[0]
     E, F, ref = check_system(pot, orc, s)
@@ -126,14 +129,17 @@ def test_cos_scale_variant(torch_cuda):
     check_system(pot, orc, s)
 
 
-def test_seven_species_solute(torch_cuda):
-    pot, orc = make("ani7")
+@pytest.mark.parametrize("precision", ["fp32", "fp32_split"])
+def test_seven_species_solute(torch_cuda, precision):
+    pot, orc = make("ani7", precision=precision)
     s = synth.solvated_solute(400, 120, 24.0, seed=5)
     check_system(pot, orc, s)
 
 
-def test_ensemble_of_eight(torch_cuda):
-    pot, orc = make("ani7x8")
+@pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
+def test_ensemble_of_eight(torch_cuda, precision):
+    # "fp32" takes the split tensor-core path for ensembles; "fp32_simt" the FP32 FMA GEMMs
+    pot, orc = make("ani7x8", precision=precision)
     s = synth.solvated_solute(150, 60, 18.0, seed=6)
     check_system(pot, orc, s)
 
@@ -274,12 +280,13 @@ def test_host_entry_point(torch_cuda):
     assert abs(E3 - ref["energy"]) <= E_TOL
 
 
-def test_solvated100k_sampled(torch_cuda):
+@pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
+def test_solvated100k_sampled(torch_cuda, precision):
     """Full-size 100k-atom, 7-species, 8-network system: sampled atoms against the
     oracle (per-atom energies, AEV rows and forces computed one by one), plus
     properties that hold at any size (net force ~ 0)."""
     import torch
-    pot, orc = make("ani7x8")
+    pot, orc = make("ani7x8", precision=precision)
     s = synth.workload("solvated100k")[0][0]
     d = to_cuda(s)
     outs = pot.energy_forces_batch([d], atom_energies=True)
@@ -313,7 +320,7 @@ def test_bounded_wait_times_out_and_context_survives(torch_cuda):
     check_system(pot, orc, s, aev=False)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp32_split"])
 def test_energy_only_matches_full_evaluation(torch_cuda, precision):
     """Energy-only re-evaluation (no forces requested: backward kernels skipped)
     returns the energies of the full evaluation (same forward arithmetic)."""
@@ -326,6 +333,15 @@ def test_energy_only_matches_full_evaluation(torch_cuda, precision):
         e0, e1 = float(a["energy"].cpu()[0]), float(b["energy"].cpu()[0])
         assert e1 == pytest.approx(e0, rel=1e-6, abs=1e-6)
         assert "forces" not in b
+    # and the energy-only energies against the FP64 oracle: the FP32 bar for the
+    # FP32 paths, the BF16 bound of tests/test_gpu_bf16.py for BF16 networks
+    for m, b in zip(list(mols[:20]) + [synth.water_box(200, 18.0, 6, seed=15)], eonly):
+        ref = orc.energy_forces(m.coords, m.species, m.box)
+        e1 = float(b["energy"].cpu()[0])
+        if precision == "bf16":
+            assert abs(e1 - ref["energy"]) <= 2e-3 * np.abs(ref["atom_energies"]).sum() + 1e-4
+        else:
+            assert abs(e1 - ref["energy"]) <= E_TOL, (e1, ref["energy"])
 
 
 def test_golden_closed_form_aev_values(torch_cuda):
@@ -379,3 +395,22 @@ def test_centres_with_more_live_blocks_than_staged(torch_cuda):
         live.append(pairs)
     assert max(live) > 16
     check_system(pot, orc, s)
+
+
+@pytest.mark.parametrize("kind", ["ani4", "ani7x8"])
+def test_split_path_batch_of_small_molecules(torch_cuda, kind):
+    """The split tensor-core path on a batch of 20-60-atom molecules: few 128-row
+    tiles, so the layers take narrow N tiles and two CTAs per SM where the stages
+    allow; every molecule's energy and forces against the oracle."""
+    pot, orc = make(kind, precision="fp32_split")
+    mols, _, _ = synth.workload("molecules64")
+    if kind == "ani7x8":
+        rng = np.random.Generator(np.random.PCG64(5))
+        mols = [synth.gas_molecule(rng, int(n), synth.systems._species_exact(
+            synth.systems.SOLUTE_FRACTIONS, int(n), rng)) for n in rng.integers(20, 61, 12)]
+    outs = pot.energy_forces_batch([to_cuda(m) for m in mols])
+    for m, o in zip(mols, outs):
+        ref = orc.energy_forces(m.coords, m.species)
+        assert abs(float(o["energy"].cpu()[0]) - ref["energy"]) <= E_TOL
+        rms, _ = force_errors(o["forces"].cpu().numpy(), ref["forces"])
+        assert rms <= 1e-4 * np.sqrt(np.mean(ref["forces"] ** 2)) + 1e-7

@@ -35,12 +35,15 @@ def _norm_close(a, b, rel=1e-3):
     np.testing.assert_allclose(a, b, atol=rel * np.abs(b).max() + 1e-12)
 
 
-def test_force_matching_batch_matches_oracle(torch_cuda):
+@pytest.mark.parametrize("precision", ["fp32", "fp32_split"])
+def test_force_matching_batch_matches_oracle(torch_cuda, precision):
+    # a split-path handle runs its energy calls on the tensor cores and the VJP's
+    # networks in FP32; both must give the oracle's gradients
     torch = torch_cuda
     from paper_2207_14276_gb300 import Potential
     from paper_2207_14276_gb300.autograd import NNPBatchFunction
     spec, w = model_for("ani4")
-    pot = Potential(spec, w)
+    pot = Potential(spec, w, precision=precision)
     mols, _, _ = synth.workload("molecules64")
     rng = np.random.Generator(np.random.PCG64(4))
     targets = [rng.normal(0.0, 1.0, size=(m.n_atoms, 3)) for m in mols]

@@ -73,3 +73,82 @@ def test_reference_arm_runs_on_rank_zero_only():
     rank, rc = q.get(timeout=120)
     p.join(timeout=60)
     assert rank == 1 and rc == 0 and p.exitcode == 0
+
+
+def _shard_worker(rank, world, port, q):
+    import numpy as np
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    import synth
+    from paper_2207_14276_gb300.router import serve_sharded
+    reqs, sizes, orc = _requests()
+
+    def evaluate(s):
+        r = orc.energy_forces(s.coords, s.species, s.box, s.mask)
+        return r["energy"], r["forces"]
+    out = serve_sharded(reqs, sizes, evaluate, dist)
+    if rank == 0:
+        q.put([(e, f.tolist()) for e, f in out])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _requests():
+    import numpy as np
+    import oracle
+    import synth
+    spec = synth.model_spec("ani4")
+    orc = oracle.Model(spec, synth.make_weights(spec, 1))
+    mols, _, _ = synth.workload("molecules64")
+    reqs = list(mols[:9]) + [synth.water_box(60, 12.0, 4, seed=2)]
+    sizes = [m.n_ml for m in reqs]
+    return reqs, sizes, orc
+
+
+def test_replicas_behind_a_router_gather_the_single_rank_results():
+    """Two gloo ranks each evaluate the requests the router assigns them (the FP64
+    oracle stands in for each replica's GPU evaluation); the results rank 0
+    gathers, in request order, equal those of one rank evaluating everything."""
+    import numpy as np
+    from paper_2207_14276_gb300.router import serve_sharded, shard
+    reqs, sizes, orc = _requests()
+    owner = shard(sizes, 2)
+    assert set(owner) == {0, 1}                        # both replicas get work
+    load = [sum(n for n, o in zip(sizes, owner) if o == r) for r in (0, 1)]
+    assert abs(load[0] - load[1]) <= max(sizes)        # balanced to one request
+    single = serve_sharded(reqs, sizes,
+                           lambda s: (lambda r: (r["energy"], r["forces"]))(
+                               orc.energy_forces(s.coords, s.species, s.box, s.mask)))
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    got = q.get(timeout=300)
+    for p in ps:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert len(got) == len(single)
+    for (e, f), (e0, f0) in zip(got, single):
+        assert e == e0
+        np.testing.assert_array_equal(np.asarray(f), f0)
+
+
+def test_router_policy():
+    """Resident boxes stay on the replica that holds them; other requests go to
+    the least-loaded replica by outstanding ML atoms, lowest index on ties."""
+    from paper_2207_14276_gb300.router import Router
+    r = Router(3)
+    assert [r.place_resident(b, 20000) for b in (0, 1, 2, 3)] == [0, 1, 2, 0]
+    assert r.place_resident(1, 20000) == 1
+    assert r.assign(40, box_id=3) == 0
+    assert r.assign(100) == 1 and r.assign(50) == 2 and r.assign(10) == 0
+    assert r.load == [50, 100, 50]
+    r.complete(1, 100)
+    assert r.assign(5) == 1
+    with pytest.raises(KeyError):
+        r.assign(10, box_id=9)

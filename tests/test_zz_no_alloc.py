@@ -8,14 +8,18 @@ instead of allocating it.  This test calls that entry point through the C ABI
 twice in a row (a periodic water box, then a small gas-phase molecule, so the
 second call reuses the array the first one filled) and checks each result
 against the ordinary nnp_energy_forces entry point with the tolerances of the
-other parity tests.  It also checks that an oversized request is refused with a
-clear message.  The file is named so that pytest collects it last.
+other parity tests, and against the FP64 oracle.  It also checks the call's
+refusals: a request beyond the array (the limit nnp_noalloc_max_atoms reports is
+accepted, one atom more is not), an atom with more neighbours than the fixed
+lists hold, and a BF16 handle.  The file is named so that pytest collects it
+last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from tests._common import model_for
 
@@ -57,6 +61,7 @@ def test_noalloc_matches_energy_forces_twice_in_a_row(torch_cuda):
     pot = Potential(spec, w)
     water = synth.water_box(300, 20.5, 7, seed=77)
     mol = synth.workload("gas24")[0][0]
+    orc = oracle.Model(spec, w)
     for s in (water, mol):
         x = torch.from_numpy(s.coords).cuda()
         sp = torch.from_numpy(s.species).cuda()
@@ -73,6 +78,11 @@ def test_noalloc_matches_energy_forces_twice_in_a_row(torch_cuda):
         assert rms <= 1e-4 * float(np.sqrt(np.mean(f0 ** 2))) + 1e-7
         v, v0 = V.cpu().numpy(), V0.cpu().numpy().reshape(9)
         np.testing.assert_allclose(v, v0, atol=1e-4 * np.abs(v0).max() + 1e-6)
+        # and against the FP64 oracle (the FP32 bar of the parity tests)
+        ref = orc.energy_forces(s.coords, s.species, s.box)
+        assert abs(float(E.cpu()[0]) - ref["energy"]) <= E_TOL
+        d = f - ref["forces"]
+        assert float(np.sqrt(np.mean(d * d))) <= 1e-4 * float(np.sqrt(np.mean(ref["forces"] ** 2))) + 1e-7
 
 
 def test_noalloc_rejects_oversized_request(torch_cuda):
@@ -89,3 +99,49 @@ def test_noalloc_rejects_oversized_request(torch_cuda):
     rc = _noalloc(pot, x, sp, list(s.box), E, F, None)
     assert rc == NNP_ERR_ARG
     assert "NNP_NOALLOC_SCRATCH_BYTES" in lib().nnp_last_error().decode()
+
+
+def test_noalloc_limit_is_the_reported_one(torch_cuda):
+    """nnp_noalloc_max_atoms gives the largest accepted atom count: a cluster of
+    exactly that many atoms (cut from a water box, non-periodic) runs, one more is
+    refused with NNP_ERR_ARG before any work."""
+    torch = torch_cuda
+    from paper_2207_14276_gb300 import Potential
+    from paper_2207_14276_gb300._lib import NNP_ERR_ARG, lib
+    spec, w = model_for("ani4")
+    pot = Potential(spec, w)
+    lim = ctypes.c_int64()
+    assert lib().nnp_noalloc_max_atoms(pot._h, ctypes.byref(lim)) == 0
+    n = lim.value
+    assert 6000 < n < 8000                 # about 6,900 for this network
+    s = synth.workload("water9000")[0][0]
+    assert n + 1 <= s.n_atoms
+    for k, want in ((n, 0), (n + 1, NNP_ERR_ARG)):
+        x = torch.from_numpy(np.ascontiguousarray(s.coords[:k])).cuda()
+        sp = torch.from_numpy(np.ascontiguousarray(s.species[:k])).cuda()
+        E = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F = torch.zeros((k, 3), dtype=torch.float32, device="cuda")
+        rc = _noalloc(pot, x, sp, None, E, F, None)
+        assert rc == want, (k, rc, lib().nnp_last_error().decode())
+
+
+def test_noalloc_refuses_overfull_lists_and_bf16(torch_cuda):
+    """A box at about eleven times liquid density fits the array but gives atoms
+    more than 96 angular (and 256 radial) neighbours: NNP_ERR_CAPACITY with a
+    message naming the fixed lists.  A BF16 handle: NNP_ERR_UNSUPPORTED."""
+    torch = torch_cuda
+    from paper_2207_14276_gb300 import Potential
+    from paper_2207_14276_gb300._lib import NNP_ERR_CAPACITY, NNP_ERR_UNSUPPORTED, lib
+    spec, w = model_for("ani4")
+    pot = Potential(spec, w)
+    s = synth.water_box(1000, 14.0, 10, seed=23)
+    x = torch.from_numpy(s.coords).cuda()
+    sp = torch.from_numpy(s.species).cuda()
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device="cuda")
+    rc = _noalloc(pot, x, sp, None, E, F, None)
+    assert rc == NNP_ERR_CAPACITY
+    assert "neighbours" in lib().nnp_last_error().decode()
+    pb = Potential(spec, w, precision="bf16")
+    rc = _noalloc(pb, x[:24], sp[:24], None, E, F, None)
+    assert rc == NNP_ERR_UNSUPPORTED
