@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--workload", default="solvated100k")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "fp32_split", "fp32_simt", "bf16"])
+    ap.add_argument("--no-fused-chain", action="store_true",
+                    help="tensor-core paths: run L2, L3, B3, B2 as four layer GEMMs "
+                         "instead of the fused per-network kernel")
     ap.add_argument("--no-bf16-beside", action="store_true",
                     help="skip the BF16-network measurement beside an FP32 headline")
     ap.add_argument("--oracle-atoms", type=int, default=24,
@@ -105,7 +108,7 @@ def fp32_alu_peak_tflops(sm_mhz):
 STAGE_SOURCE = {"mlp": "mlp_fused.cu", "aev_bwd": "aev.cu", "aev_fwd": "aev.cu",
                 "neighbors": "nl.cu", "mlp_l1": "mlp_tc.cu", "mlp_l2": "mlp_tc.cu",
                 "mlp_l3": "mlp_tc.cu", "mlp_b3": "mlp_tc.cu", "mlp_b2": "mlp_tc.cu",
-                "mlp_b1": "mlp_tc.cu"}
+                "mlp_b1": "mlp_tc.cu", "mlp_chain": "mlp_chain.cu"}
 
 
 def recorded_traffic(stage, workload):
@@ -155,6 +158,9 @@ def stage_work(stage, spec, counts, n_atoms, path):
         fwd = D * h1 + h1 * h2 + h2 * h3 + h3
         bwd = h3 * h2 + h2 * h1 + h1 * D
         return 2.0 * n_atoms * E * (fwd + bwd), "FLOP", "alu"
+    if stage == "mlp_chain":   # L2, L3, B3, B2 of every member, one fused kernel
+        bound = {"bf16": "tensor", "fp32_split": "tensor_split"}.get(path, "alu")
+        return 2.0 * n_atoms * E * (2 * h1 * h2 + 2 * h2 * h3), "FLOP", bound
     gemm = {"mlp_l1": (D, E * h1), "mlp_l2": (h1, h2 * E), "mlp_l3": (h2, h3 * E),
             "mlp_b3": (h3, h2 * E), "mlp_b2": (h2, h1 * E), "mlp_b1": (E * h1, D)}
     if stage in gemm:
@@ -525,6 +531,7 @@ def run_ours(args):
     spec = synth.model_spec(kind)
     w = synth.make_weights(spec, wseed)
     pot = Potential(spec, w, precision=args.precision)
+    pot.set_fused_chain(not args.no_fused_chain)
     s = systems[0]
     x = torch.from_numpy(s.coords).to(dev)
     sp = torch.from_numpy(s.species).to(dev)
@@ -638,6 +645,7 @@ def run_ours(args):
     beside = None
     if args.precision != "bf16" and not args.no_bf16_beside:
         pb = Potential(spec, w, precision="bf16")
+        pb.set_fused_chain(not args.no_fused_chain)
         pb.energy_forces(x, sp, box, mask)
         for _ in range(args.warmup):
             pb.energy_forces_into(x, sp, box, mask, E, F)

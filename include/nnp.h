@@ -59,8 +59,8 @@ enum {
 /* precision of the per-species networks (AEVs, their backward and the forces
  * are FP32 in every mode; energies and virials are reduced in FP64) */
 enum {
-  NNP_FP32 = 0,       /* FP32-accurate networks; the library picks the path:
-                         NNP_FP32_SPLIT for ensembles, NNP_FP32_SIMT otherwise     */
+  NNP_FP32 = 0,       /* FP32-accurate networks on the fastest such path, which
+                         on this GPU is NNP_FP32_SPLIT                             */
   NNP_BF16_MLP = 1,   /* network layers on tcgen05 tensor cores, BF16 operands and
                          FP32 accumulation                                         */
   NNP_FP32_SPLIT = 2, /* network layers on tcgen05 tensor cores with every FP32
@@ -295,6 +295,13 @@ int nnp_sync_status(nnp_handle* h, void* stream);
 
 /* Length of the atomic environment vector. */
 int nnp_aev_dim(const nnp_handle* h);
+/* Tensor-core paths (NNP_BF16_MLP, NNP_FP32_SPLIT): enable != 0 (the default)
+ * runs the layers after the first -- L2, L3 with the output layer, and their
+ * backward B3, B2 -- as one fused kernel per 128-row tile with the activations
+ * in shared memory (widths multiples of 16, at most 256); 0 runs them as four
+ * layer GEMMs through HBM.  Both give the same result to rounding order.  No
+ * effect on NNP_FP32_SIMT handles. */
+int nnp_set_fused_chain(nnp_handle* h, int enable);
 /* The network path a handle runs: NNP_FP32_SPLIT, NNP_FP32_SIMT or NNP_BF16_MLP
  * (NNP_FP32 resolves to one of the first two at nnp_create); -1 for a null handle. */
 int nnp_network_path(const nnp_handle* h);

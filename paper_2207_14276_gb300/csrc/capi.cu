@@ -32,6 +32,7 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
 int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, int row_cap,
                    const float* aev, float* dEdG, bool split, void** state);
 void mlp_tc_release(void* state);
+void mlp_tc_use_chain(void* state, bool on);
 void launch_aev_to_bf16(const Ws& ws, int n_in, const AevConst& ac, void* out, cudaStream_t st);
 void launch_wait_probe(int* status, unsigned limit, cudaStream_t st);
 }  // namespace nnp
@@ -109,6 +110,8 @@ struct nnp_handle {
   std::string gsig;       // signature of the captured call
   std::string last_sig;   // signature of the previous eager call
   int last_launches_graph = 0;
+  // tensor-core paths: the layers after the first as one fused kernel
+  bool fused_chain = true;
   // persistent neighbour lists with a Verlet skin (0: rebuilt on every call)
   float skin = 0.f;
   bool lists_valid = false;   // the lists in the arena belong to list_sig's batch layout
@@ -170,12 +173,11 @@ int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
   m->alpha = w->celu_alpha;
   if (!(m->alpha > 0)) return fail(NNP_ERR_ARG, "celu_alpha must be positive");
   m->precision = precision;
-  // FP32 accuracy: ensembles on the split tensor-core path (their network FLOPs
-  // dominate), one-network models on the fused FP32 kernel
-  m->net = precision == NNP_BF16_MLP     ? kNetBf16
-           : precision == NNP_FP32_SPLIT ? kNetSplit
-           : precision == NNP_FP32_SIMT  ? kNetSimt
-           : (w->n_ensemble > 1 ? kNetSplit : kNetSimt);
+  // FP32 accuracy: the split tensor-core path (measured faster than the FP32 FMA
+  // kernels for ensembles and for one-network models alike)
+  m->net = precision == NNP_BF16_MLP    ? kNetBf16
+           : precision == NNP_FP32_SIMT ? kNetSimt
+                                        : kNetSplit;
   CU_TRY(cudaGetDevice(&m->device));
 
   // unpack the flat parameter vector into the kernel layouts
@@ -417,6 +419,7 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
     int rc = mlp_tc_prepare(h->model->md, h->model->mw, h->mb, h->ws.row_cap, h->ws.aev,
                             h->ws.dEdG, h->model->net == kNetSplit, &h->tc_state);
     if (rc) return fail(rc, "tensor-core GEMM set-up (tensor maps, launch limits) failed");
+    mlp_tc_use_chain(h->tc_state, h->fused_chain);
   }
   h->dirty = false;
   return NNP_OK;
@@ -425,8 +428,8 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
 // stage names (index = stage id) reported by nnp_profile_read
 const char* kStageNames[] = {"prep", "neighbors", "aev_fwd", "mlp_l1", "mlp_l2", "mlp_l3",
                              "mlp_b3", "mlp_b2", "mlp_b1", "aev_bwd", "finalize", "mlp_cvt",
-                             "mlp"};
-constexpr int kNumStages = 13;
+                             "mlp", "mlp_chain"};
+constexpr int kNumStages = 14;
 
 cudaEvent_t prof_event(nnp_handle* h) {
   if (!h->prof_pool.empty()) {
@@ -658,6 +661,7 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
     const int skin_mode = ws.skin_state ? (h->lists_valid ? 1 : 2) : 0;
     put(&skin_mode, sizeof(skin_mode));
     put(&h->skin, sizeof(h->skin));
+    put(&h->fused_chain, sizeof(h->fused_chain));
     // the kernels read only the first n_sys descriptors of a chunk
     for (const auto& bp : chunks)
       put(&bp, offsetof(BatchParams, sys) + (size_t)bp.n_sys * sizeof(SysIn));
@@ -1187,6 +1191,14 @@ extern "C" int64_t nnp_n_weights(const nnp_handle* h) {
 }
 
 int nnp_aev_dim(const nnp_handle* h) { return h ? h->model->ac.D : -1; }
+int nnp_set_fused_chain(nnp_handle* h, int enable) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  h->fused_chain = enable != 0;
+  mlp_tc_use_chain(h->tc_state, h->fused_chain);
+  return NNP_OK;
+}
+
 int nnp_network_path(const nnp_handle* h) {
   if (!h) return -1;
   const int net = h->model->net;

@@ -31,10 +31,18 @@
 
 #include "../../include/nnp.h"
 #include "mlp.cuh"
+#include "tc_util.cuh"
 
 namespace nnp {
 
+// the fused per-network chain (mlp_chain.cu)
+void* chain_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, int row_cap, bool split);
+void chain_release(void* plan);
+void launch_chain(void* plan, const Ws& ws, float alpha, bool energy_only, cudaStream_t st);
+
 namespace {
+
+using namespace tcu;
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;           // bf16 elements per K slice (one 128-byte swizzle row)
@@ -42,7 +50,6 @@ constexpr int kEpiWarps = 8;
 constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr int kMaxStages = 4;
-constexpr unsigned kWaitLimit = 1u << 24;
 // dynamic shared memory limit: the 227 KB per block minus the kernel's static
 // shared memory (barriers, bias and w4 staging) and some headroom
 constexpr int kMaxDynSmem = 232448 - 16384;
@@ -66,171 +73,6 @@ struct TcArgs {
   int* status;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait; false if the limit was hit or another role gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
-  for (unsigned it = 0; it < kWaitLimit; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*abort_flag) return false;
-  }
-  *abort_flag = 1;
-  return false;
-}
-
-// bounded wait that ignores the abort flag (used to drain in-flight work)
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < kWaitLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
-                                            int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;               // leading byte offset (unused with this swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
-  d |= (uint64_t)1 << 46;               // descriptor version
-  d |= (uint64_t)2 << 61;               // 128-byte swizzle
-  return d;
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                          uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11,"
-      " %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float (&v)[16]) {
-  uint32_t w[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    w[i] = *reinterpret_cast<uint32_t*>(&h);
-  }
-  uint4* d = reinterpret_cast<uint4*>(dst);
-  d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-  d[1] = make_uint4(w[4], w[5], w[6], w[7]);
-}
-
-// split path: v = hi + lo with hi = bf16(v) and lo = bf16(v - hi), 16 values
-__device__ __forceinline__ void store_split16(__nv_bfloat16* hi, __nv_bfloat16* lo,
-                                              const float (&v)[16]) {
-  uint32_t wh[8], wl[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
-    wh[i] = *reinterpret_cast<const uint32_t*>(&h);
-    wl[i] = *reinterpret_cast<const uint32_t*>(&l);
-  }
-  uint4* dh = reinterpret_cast<uint4*>(hi);
-  uint4* dl = reinterpret_cast<uint4*>(lo);
-  dh[0] = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-  dh[1] = make_uint4(wh[4], wh[5], wh[6], wh[7]);
-  dl[0] = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-  dl[1] = make_uint4(wl[4], wl[5], wl[6], wl[7]);
-}
-
-__device__ __forceinline__ void load_bf16x16(const __nv_bfloat16* src, float (&v)[16]) {
-  const uint4* s = reinterpret_cast<const uint4*>(src);
-  uint4 q[2] = {s[0], s[1]};
-  const uint32_t* w = reinterpret_cast<const uint32_t*>(q);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
-    float2 f = __bfloat1622float2(h);
-    v[2 * i] = f.x;
-    v[2 * i + 1] = f.y;
-  }
-}
-
-struct Tile {
-  int m0, n0, e, s;
-};
-
-__device__ __forceinline__ Tile tile_of(int t, int n_tiles_n, int row_tiles, int n_tile,
-                                        const int* seg_start, int S) {
-  Tile tl;
-  const int ni = t % n_tiles_n, rest = t / n_tiles_n;
-  tl.m0 = (rest % row_tiles) * kBM;
-  tl.e = rest / row_tiles;
-  tl.n0 = ni * n_tile;
-  int s = 0;
-  while (s + 1 < S && tl.m0 >= seg_start[s + 1]) ++s;
-  tl.s = s;
-  return tl;
-}
-
-// SPLIT: every operand comes as a high and a low BF16 part (ta/tb and ta2/tb2);
-// a stage holds A_hi, A_lo, B_hi, B_lo and every 16-wide K step issues the
-// three products A_hi B_hi + A_lo B_hi + A_hi B_lo into the FP32 accumulator.
 template <int EPI, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
@@ -504,34 +346,6 @@ __global__ void k_wait_probe(int* status, unsigned limit) {
 }
 
 // ---------------------------------------------------------------- host side
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-// 3D bf16 map: dims (d0 innermost, d1, d2), strides in elements for d1 and d2, box (64, b1, b2)
-bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t st1,
-              uint64_t st2, uint32_t b1, uint32_t b2) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[3] = {d0, d1, d2};
-  cuuint64_t strides[2] = {st1 * 2, st2 * 2};
-  cuuint32_t box[3] = {(cuuint32_t)kBK, b1, b2};
-  cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 struct TcGemmPlan {
   CUtensorMap ta, tb, ta2, tb2;   // ta2 / tb2: low parts (split path; copies of ta / tb otherwise)
   TcArgs a;
@@ -547,6 +361,11 @@ struct TcState {
   float* e_row = nullptr;
   int row_cap = 0, Dp = 0, E = 1;
   bool split = false;
+  void* chain = nullptr;     // fused L2 -> L3 -> B3 -> B2 (null: the four layer GEMMs)
+  bool use_chain = true;
+  ~TcState() {
+    if (chain) chain_release(chain);
+  }
 };
 
 int pick_n_tile(int N, int tiles_per_col, bool single, int sms) {
@@ -704,11 +523,17 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
       delete st;
       return NNP_ERR_CUDA;
     }
+  st->chain = chain_prepare(md, mw, mb, row_cap, split);
   *state_out = st;
   return NNP_OK;
 }
 
 void mlp_tc_release(void* state) { delete static_cast<TcState*>(state); }
+
+// whether the layers after the first run as the fused chain (where it is set up)
+void mlp_tc_use_chain(void* state, bool on) {
+  if (state) static_cast<TcState*>(state)->use_chain = on;
+}
 
 void launch_wait_probe(int* status, unsigned limit, cudaStream_t st) {
   k_wait_probe<<<1, 32, 0, st>>>(status, limit);
@@ -719,9 +544,19 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
   (void)mw; (void)mb;
   TcState* s = static_cast<TcState*>(state);
   if (!s) return NNP_ERR_ARG;
-  // plans 0-2 are the forward layers, 3-5 the backward to the input
+  // plans 0-2 are the forward layers, 3-5 the backward to the input; with the
+  // fused chain: plan 0 (L1), the chain (L2, L3, B3, B2), plan 5 (B1)
+  const bool chain = s->chain && s->use_chain;
   const size_t n_plans = energy_only ? 3 : s->plans.size();
   for (size_t i = 0; i < n_plans; ++i) {
+    if (chain && i >= 1 && i <= 4) {
+      if (i == 1) {
+        if (hook) hook->begin(13);
+        launch_chain(s->chain, ws, alpha, energy_only, st);
+        if (hook) hook->end();
+      }
+      continue;
+    }
     auto& p = s->plans[i];
     TcArgs a = p.a;
     a.alpha = alpha;
@@ -751,7 +586,7 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
 #undef NNP_TC_LAUNCH
     if (hook) hook->end();
   }
-  if (n_launch) *n_launch += (int)n_plans;
+  if (n_launch) *n_launch += chain ? (energy_only ? 2 : 3) : (int)n_plans;
   return NNP_OK;
 }
 

@@ -29,9 +29,9 @@ class Potential:
     spec: an object with ``aev`` (n_species, rc_r, eta_r, shf_r, rc_a, eta_a, zeta,
     shf_a, shf_z, cos_scale), ``widths``, ``n_ensemble``, ``celu_alpha`` and
     ``atomic_numbers``; weights: flat float32 vector (layout of include/nnp.h).
-    precision: "fp32" (FP32-accurate; split-BF16 tensor cores for ensembles, the
-    FP32 FMA kernel otherwise), "fp32_split" / "fp32_simt" (force one of those),
-    or "bf16" (tensor-core network layers on BF16 operands).
+    precision: "fp32" (FP32-accurate: network layers on the tensor cores with
+    split BF16 operands, the same as "fp32_split"), "fp32_simt" (network layers
+    on the FP32 FMA pipes), or "bf16" (tensor-core layers on BF16 operands).
     """
 
     def __init__(self, spec, weights, precision="fp32", shift=None, hbm_budget=0, _clone_of=None):
@@ -99,6 +99,11 @@ class Potential:
 
     def sync_status(self, stream=None):
         return lib().nnp_sync_status(self._h, _stream_ptr(stream))
+
+    def set_fused_chain(self, enable):
+        """Tensor-core paths: run L2, L3, B3 and B2 as one fused kernel (default)
+        or as four layer GEMMs."""
+        check(lib().nnp_set_fused_chain(self._h, 1 if enable else 0))
 
     def network_path(self):
         """'fp32_split', 'fp32_simt' or 'bf16': the path this handle's networks run."""

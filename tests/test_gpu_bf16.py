@@ -85,3 +85,44 @@ def test_bf16_batch_alone_equals_in_mix(torch_cuda):
         # identical BF16 arithmetic per row; only FP32 atomic order differs
         assert float(E.cpu()[0]) == pytest.approx(float(outs[k]["energy"].cpu()[0]), abs=1e-4)
         np.testing.assert_allclose(F.cpu().numpy(), outs[k]["forces"].cpu().numpy(), atol=1e-4)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp32_split"])
+@pytest.mark.parametrize("kind", ["ani4", "ani7x8"])
+def test_fused_chain_matches_layer_gemms(torch_cuda, precision, kind):
+    """The layers after the first as one fused kernel (activations in shared
+    memory) against the same layers as four GEMMs through HBM, on one batch: the
+    arithmetic is the same up to the order of FP32 accumulation, so energies and
+    forces agree to 1e-5 relative on the split path; with BF16 activations a
+    last-bit FP32 difference can flip a BF16 rounding, so there the bound is the
+    BF16 path's own error bound against the oracle.  Energy-only calls too."""
+    torch = torch_cuda
+    from paper_2207_14276_gb300 import Potential
+    spec, w = model_for(kind)
+    pot = Potential(spec, w, precision=precision)
+    if kind == "ani4":
+        systems = [synth.water_box(300, 20.5, 7, seed=41)] + list(synth.workload("molecules64")[0][:6])
+    else:
+        systems = [synth.solvated_solute(150, 60, 18.0, seed=6)]
+    d = [{"coords": torch.from_numpy(s.coords).cuda(), "species": torch.from_numpy(s.species).cuda(),
+          "box": None if s.box is None else list(s.box)} for s in systems]
+    res = {}
+    for fused in (True, False):
+        pot.set_fused_chain(fused)
+        full = pot.energy_forces_batch(d, atom_energies=True)
+        eonly = pot.energy_forces_batch(d, forces=False)
+        res[fused] = ([(float(o["energy"].cpu()[0]), o["forces"].cpu().numpy().astype(np.float64),
+                        o["atom_energies"].cpu().numpy().astype(np.float64)) for o in full],
+                      [float(o["energy"].cpu()[0]) for o in eonly])
+    for (e1, f1, a1), (e0, f0, a0), q1, q0 in zip(res[True][0], res[False][0], res[True][1], res[False][1]):
+        scale_e = float(np.abs(a0).sum()) + 1e-6
+        f_rms = float(np.sqrt(np.mean(f0 ** 2))) + 1e-9
+        d_rms = float(np.sqrt(np.mean((f1 - f0) ** 2)))
+        if precision == "fp32_split":
+            assert abs(e1 - e0) <= 1e-5 * scale_e
+            assert abs(q1 - q0) <= 1e-5 * scale_e
+            assert d_rms <= 1e-5 * f_rms
+        else:
+            assert abs(e1 - e0) <= 2e-3 * scale_e
+            assert abs(q1 - q0) <= 2e-3 * scale_e
+            assert d_rms <= 2e-2 * f_rms

@@ -111,10 +111,10 @@ def test_dense_box_neighbourhood_beyond_the_stage(torch_cuda):
     compare_neighbours(pot, s, pot.spec)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_split"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
 def test_water9000_fp32(torch_cuda, precision):
-    # "fp32" runs the fused FP32 kernel for this one-network model; "fp32_split"
-    # the tensor-core layers on split BF16 operands (three products per term)
+    # "fp32": tensor-core layers on split BF16 operands (three products per
+    # term); "fp32_simt": the fused FP32 FMA kernel of this one-network model
     pot, orc = make("ani4", precision=precision)
     systems, _, _ = synth.workload("water9000")
     s = systems[0]
@@ -129,7 +129,7 @@ def test_cos_scale_variant(torch_cuda):
     check_system(pot, orc, s)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_split"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
 def test_seven_species_solute(torch_cuda, precision):
     pot, orc = make("ani7", precision=precision)
     s = synth.solvated_solute(400, 120, 24.0, seed=5)
@@ -138,7 +138,7 @@ def test_seven_species_solute(torch_cuda, precision):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
 def test_ensemble_of_eight(torch_cuda, precision):
-    # "fp32" takes the split tensor-core path for ensembles; "fp32_simt" the FP32 FMA GEMMs
+    # "fp32" takes the split tensor-core path; "fp32_simt" the six FP32 FMA GEMMs
     pot, orc = make("ani7x8", precision=precision)
     s = synth.solvated_solute(150, 60, 18.0, seed=6)
     check_system(pot, orc, s)
@@ -320,7 +320,7 @@ def test_bounded_wait_times_out_and_context_survives(torch_cuda):
     check_system(pot, orc, s, aev=False)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp32_split"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp32_simt"])
 def test_energy_only_matches_full_evaluation(torch_cuda, precision):
     """Energy-only re-evaluation (no forces requested: backward kernels skipped)
     returns the energies of the full evaluation (same forward arithmetic)."""

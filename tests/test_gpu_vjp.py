@@ -35,10 +35,11 @@ def _norm_close(a, b, rel=1e-3):
     np.testing.assert_allclose(a, b, atol=rel * np.abs(b).max() + 1e-12)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_split"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
 def test_force_matching_batch_matches_oracle(torch_cuda, precision):
-    # a split-path handle runs its energy calls on the tensor cores and the VJP's
-    # networks in FP32; both must give the oracle's gradients
+    # an "fp32" handle runs its energy calls on the tensor cores (split operands)
+    # and the VJP's networks in FP32; a "fp32_simt" handle both in FP32; both must
+    # give the oracle's gradients
     torch = torch_cuda
     from paper_2207_14276_gb300 import Potential
     from paper_2207_14276_gb300.autograd import NNPBatchFunction
