@@ -70,6 +70,8 @@ def parse():
                          "instead of the fused per-network kernel")
     ap.add_argument("--no-bf16-beside", action="store_true",
                     help="skip the BF16-network measurement beside an FP32 headline")
+    ap.add_argument("--no-force-matching", action="store_true",
+                    help="skip the force-matching (double backward) measurement")
     ap.add_argument("--oracle-atoms", type=int, default=24,
                     help="seeded sample of atoms whose energies and forces are compared "
                          "with the FP64 oracle (0 to skip)")
@@ -124,8 +126,9 @@ def recorded_traffic(stage, workload):
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
     for line in open(path):
         f = line.split()
-        if len(f) >= 4 and not line.startswith("#") and f[0] == stage and f[1] == workload:
-            return int(f[2]) if f[3] == sha else None
+        if (len(f) >= 4 and not line.startswith("#") and f[0] == stage and f[1] == workload
+                and f[3] == sha):
+            return int(f[2])
     return None
 
 
@@ -477,6 +480,70 @@ def run_serving(rates, n_requests, precision="bf16", lanes=2, max_systems=256,
     return out
 
 
+def force_matching_section(dev, stream, steps=20, warmup=3):
+    """The differentiation workload: 64 molecules of 20-60 atoms (4-species model),
+    loss sum((F - F_target)^2) with F_target ~ N(0, 1 kcal/mol/A) (PCG64(4)),
+    gradients w.r.t. every weight and coordinate through the autograd wrapper
+    whose backward is the library's force vector-Jacobian product.  Timed per
+    forward + backward step with CUDA events; gradients compared once with the
+    FP64 oracle's (dual-number) force-matching gradient."""
+    import torch
+    import oracle
+    from paper_2207_14276_gb300 import Potential
+    from paper_2207_14276_gb300.autograd import NNPBatchFunction
+    spec = synth.model_spec("ani4")
+    w = synth.make_weights(spec, 1)
+    pot = Potential(spec, w)
+    mols, _, _ = synth.workload("molecules64")
+    rng = np.random.Generator(np.random.PCG64(4))
+    targets = [rng.normal(0.0, 1.0, size=(m.n_atoms, 3)) for m in mols]
+    sizes = [m.n_atoms for m in mols]
+    x0 = torch.from_numpy(np.concatenate([m.coords for m in mols])).to(dev)
+    sp = torch.from_numpy(np.concatenate([m.species for m in mols])).to(dev)
+    Ft = torch.from_numpy(np.concatenate(targets)).float().to(dev)
+    w0 = torch.from_numpy(w).to(dev)
+
+    def step():
+        x = x0.clone().requires_grad_(True)
+        wt = w0.clone().requires_grad_(True)
+        E, F = NNPBatchFunction.apply(x, wt, pot, sp, sizes)
+        loss = ((F - Ft) ** 2).sum()
+        loss.backward()
+        return x.grad, wt.grad
+
+    for _ in range(warmup):
+        step()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(steps):
+        gx, gw = step()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / steps
+    orc = oracle.Model(spec, w)
+    gw_ref = np.zeros(w.size)
+    gx_ref = []
+    for m, t in zip(mols, targets):
+        Fm = orc.energy_forces(m.coords, m.species)["forces"]
+        _, _, gxm, gwm = orc.force_matching(m.coords, m.species, 2 * (Fm - t))
+        gw_ref += gwm
+        gx_ref.append(gxm)
+    gx_ref = np.concatenate(gx_ref)
+
+    def err(a, b):
+        a = a.double().cpu().numpy().reshape(-1)
+        b = b.reshape(-1)
+        return {"max_abs_err_over_max_abs": float(np.abs(a - b).max() / np.abs(b).max()),
+                "norm_rel_err": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
+    n_at = sum(sizes)
+    return {"workload": "64 molecules of 20-60 atoms (H:C:N:O 12:7:3:2), 4-species model; loss "
+                        "sum((F - F_target)^2), F_target ~ N(0, 1 kcal/mol/A); gradients w.r.t. "
+                        "all weights and coordinates (forward + hand-written double backward)",
+            "ms_per_step": ms, "value": n_at / (ms / 1e3), "unit": UNIT + " (forward + backward)",
+            "errors_vs_oracle": {"dL_dcoords": err(gx, gx_ref), "dL_dweights": err(gw, gw_ref)}}
+
+
 # ------------------------------------------------------------------ our arm
 def md_trajectory(spec, w, precision, x0, sp, box, mask, n_eval, steps, skin, sigma, flush, dev):
     """Energy+force calls along a random-walk trajectory (each coordinate moves by
@@ -746,6 +813,10 @@ def run_ours(args):
             ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
             snap[name] = {"ms_per_batch": ms, "value": n_frames * n_eval / (ms / 1e3), "unit": UNIT}
 
+    fmatch = None
+    if not args.no_force_matching and rank == 0:
+        fmatch = force_matching_section(dev, stream)
+
     serving = None
     if args.serving_rates and rank == 0:
         rates = [float(r) for r in args.serving_rates.split(",") if r]
@@ -818,6 +889,7 @@ def run_ours(args):
         "persistent_lists": md,
         "snapshot_batch": snap,
         "respa_driver": respa,
+        "force_matching": fmatch,
     }
     print(json.dumps(out))
     if dist is not None:

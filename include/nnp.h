@@ -295,11 +295,13 @@ int nnp_sync_status(nnp_handle* h, void* stream);
 
 /* Length of the atomic environment vector. */
 int nnp_aev_dim(const nnp_handle* h);
-/* Tensor-core paths (NNP_BF16_MLP, NNP_FP32_SPLIT): enable != 0 (the default)
- * runs the layers after the first -- L2, L3 with the output layer, and their
- * backward B3, B2 -- as one fused kernel per 128-row tile with the activations
- * in shared memory (widths multiples of 16, at most 256); 0 runs them as four
- * layer GEMMs through HBM.  Both give the same result to rounding order.  No
+/* Tensor-core paths (NNP_BF16_MLP, NNP_FP32_SPLIT): enable != 0 runs the layers
+ * after the first -- L2, L3 with the output layer, and their backward B3, B2 --
+ * as one fused kernel per 128-row tile with the activations in shared memory
+ * (widths multiples of 16, at most 256); 0 runs them as four layer GEMMs
+ * through HBM.  Both give the same result to rounding order.  Default: on for
+ * NNP_FP32 / NNP_FP32_SPLIT handles, off for NNP_BF16_MLP (the faster choice of
+ * each on the 100k-atom 8-network workload).  Clones inherit the setting.  No
  * effect on NNP_FP32_SIMT handles. */
 int nnp_set_fused_chain(nnp_handle* h, int enable);
 /* The network path a handle runs: NNP_FP32_SPLIT, NNP_FP32_SIMT or NNP_BF16_MLP

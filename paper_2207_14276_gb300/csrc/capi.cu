@@ -110,8 +110,10 @@ struct nnp_handle {
   std::string gsig;       // signature of the captured call
   std::string last_sig;   // signature of the previous eager call
   int last_launches_graph = 0;
-  // tensor-core paths: the layers after the first as one fused kernel
-  bool fused_chain = true;
+  // tensor-core paths: the layers after the first as one fused kernel (set at
+  // creation: on for the split path, where it measured faster than the four
+  // layer GEMMs, off for BF16, where it measured slower)
+  bool fused_chain = false;
   // persistent neighbour lists with a Verlet skin (0: rebuilt on every call)
   float skin = 0.f;
   bool lists_valid = false;   // the lists in the arena belong to list_sig's batch layout
@@ -759,6 +761,7 @@ int nnp_create(const nnp_species_t* species, const nnp_aev_params_t* aev,
   nnp_handle* h = new nnp_handle;
   h->model = m.release();
   h->budget = hbm_budget_bytes;
+  h->fused_chain = (h->model->net == kNetSplit);
   if (!alloc_host_words(h)) {
     nnp_destroy(h);
     return fail(NNP_ERR_CUDA, "cudaMallocHost failed");
@@ -775,6 +778,7 @@ int nnp_clone(const nnp_handle* src, nnp_handle** out) {
   h->budget = src->budget;
   h->cap_r = src->cap_r;
   h->cap_a = src->cap_a;
+  h->fused_chain = src->fused_chain;
   if (!alloc_host_words(h)) {
     nnp_destroy(h);
     return fail(NNP_ERR_CUDA, "cudaMallocHost failed");

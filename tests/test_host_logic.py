@@ -125,6 +125,11 @@ def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     # a changed kernel source invalidates the record
     src.write_text("kernel v2\n")
     assert bench.recorded_traffic("mlp", "water9000") is None
+    # a record of the current source is found after older records of the stage
+    sha2 = hashlib.sha256(b"kernel v2\n").hexdigest()[:16]
+    with open(tmp_path / "profiles" / "dram_traffic.txt", "a") as f:
+        f.write(f"mlp water9000 12345 {sha2} profiles/y.md (a note)\n")
+    assert bench.recorded_traffic("mlp", "water9000") == 12345
 
 
 def test_oracle_baselines_run_on_the_host():
