@@ -51,6 +51,9 @@ WORKLOAD_DESC = {
     "solvated100k": "solvated100k: 1000-atom branched solute in 33,000 waters, 100,000 atoms, "
                     "periodic 99.9 A box; 7-species 1008-dim AEV; 8 networks 1008-256-192-160-1",
     "gas24": "gas24: one 24-atom molecule (H12 C7 N3 O2), non-periodic",
+    "water99k": "water99k: 33,000 rigid waters (99,000 atoms) on a jittered 33^3 lattice, "
+                "periodic cubic box 99.6 A (1 g/cm^3); 4-species 384-dim AEV; networks "
+                "384-160-128-96-1",
     "solvated20k": "solvated20k: 50-atom solute in 6,667 waters, ~20,000 atoms, periodic 58.4 A "
                    "box; 7-species 1008-dim AEV; 8 networks 1008-256-192-160-1",
 }
@@ -66,8 +69,11 @@ def parse():
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "fp32_split", "fp32_simt", "bf16"])
     ap.add_argument("--no-fused-chain", action="store_true",
-                    help="tensor-core paths: run L2, L3, B3, B2 as four layer GEMMs "
-                         "instead of the fused per-network kernel")
+                    help="run L2, L3, B3, B2 as four layer GEMMs on every tensor-core path "
+                         "(default: the fused per-network kernel on the split path only)")
+    ap.add_argument("--fused-aev-l1", action="store_true",
+                    help="BF16 one-network models: AEV computed on chip and fed to the first "
+                         "layer in one kernel")
     ap.add_argument("--no-bf16-beside", action="store_true",
                     help="skip the BF16-network measurement beside an FP32 headline")
     ap.add_argument("--no-force-matching", action="store_true",
@@ -110,7 +116,7 @@ def fp32_alu_peak_tflops(sm_mhz):
 STAGE_SOURCE = {"mlp": "mlp_fused.cu", "aev_bwd": "aev.cu", "aev_fwd": "aev.cu",
                 "neighbors": "nl.cu", "mlp_l1": "mlp_tc.cu", "mlp_l2": "mlp_tc.cu",
                 "mlp_l3": "mlp_tc.cu", "mlp_b3": "mlp_tc.cu", "mlp_b2": "mlp_tc.cu",
-                "mlp_b1": "mlp_tc.cu", "mlp_chain": "mlp_chain.cu"}
+                "mlp_b1": "mlp_tc.cu", "mlp_chain": "mlp_chain.cu", "aev_l1": "aev.cu"}
 
 
 def recorded_traffic(stage, workload):
@@ -161,6 +167,8 @@ def stage_work(stage, spec, counts, n_atoms, path):
         fwd = D * h1 + h1 * h2 + h2 * h3 + h3
         bwd = h3 * h2 + h2 * h1 + h1 * D
         return 2.0 * n_atoms * E * (fwd + bwd), "FLOP", "alu"
+    if stage == "aev_l1":   # the AEV forward and the first layer in one kernel (BF16)
+        return n_atoms * (nr * 16 * 5 + tri * 200) + 2.0 * n_atoms * D * h1, "FLOP", "alu"
     if stage == "mlp_chain":   # L2, L3, B3, B2 of every member, one fused kernel
         bound = {"bf16": "tensor", "fp32_split": "tensor_split"}.get(path, "alu")
         return 2.0 * n_atoms * E * (2 * h1 * h2 + 2 * h2 * h3), "FLOP", bound
@@ -598,7 +606,9 @@ def run_ours(args):
     spec = synth.model_spec(kind)
     w = synth.make_weights(spec, wseed)
     pot = Potential(spec, w, precision=args.precision)
-    pot.set_fused_chain(not args.no_fused_chain)
+    if args.no_fused_chain:     # otherwise each network path keeps its default
+        pot.set_fused_chain(False)
+    pot.set_fused_aev_l1(args.fused_aev_l1)
     s = systems[0]
     x = torch.from_numpy(s.coords).to(dev)
     sp = torch.from_numpy(s.species).to(dev)
@@ -712,7 +722,8 @@ def run_ours(args):
     beside = None
     if args.precision != "bf16" and not args.no_bf16_beside:
         pb = Potential(spec, w, precision="bf16")
-        pb.set_fused_chain(not args.no_fused_chain)
+        if args.no_fused_chain:
+            pb.set_fused_chain(False)
         pb.energy_forces(x, sp, box, mask)
         for _ in range(args.warmup):
             pb.energy_forces_into(x, sp, box, mask, E, F)

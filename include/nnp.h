@@ -304,6 +304,14 @@ int nnp_aev_dim(const nnp_handle* h);
  * each on the 100k-atom 8-network workload).  Clones inherit the setting.  No
  * effect on NNP_FP32_SIMT handles. */
 int nnp_set_fused_chain(nnp_handle* h, int enable);
+/* BF16 handles of one-network models: enable != 0 computes the AEV rows of each
+ * 128-row species tile in shared memory and feeds them to the first layer's
+ * tensor-core GEMM in the same kernel, so the AEV is never written to HBM (the
+ * fused AEV -> first-layer step); 0 (the default) runs the AEV kernel and the
+ * layer GEMM.  Same result to rounding order.  While it is on, nnp_debug_rows
+ * cannot return AEV rows (NNP_ERR_UNSUPPORTED).  Falls back to the two kernels
+ * where the tile and the neighbour staging do not fit in shared memory. */
+int nnp_set_fused_aev_l1(nnp_handle* h, int enable);
 /* The network path a handle runs: NNP_FP32_SPLIT, NNP_FP32_SIMT or NNP_BF16_MLP
  * (NNP_FP32 resolves to one of the first two at nnp_create); -1 for a null handle. */
 int nnp_network_path(const nnp_handle* h);

@@ -34,6 +34,7 @@
 #include <algorithm>
 
 #include "nnp_internal.cuh"
+#include "tc_util.cuh"
 
 namespace nnp {
 
@@ -276,26 +277,24 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32], unsigned lan
   return v[0];
 }
 
-template <int ZETA>
-__global__ void __launch_bounds__(kWarps * 32, 4)
-k_aev_fwd(Ws ws, AevConst ac) {
-  extern __shared__ float4 sm4[];
-  __shared__ ListHdr hdrs[kWarps];
-  const int w = threadIdx.x >> 5;
-  const unsigned lane = threadIdx.x & 31;
-  const int p = blockIdx.x * kWarps + w;
-  if (p >= ws.totals[0]) return;
-  float4* angv = sm4 + (size_t)w * (ws.cap_a + ws.cap_a / 4 + ws.cap_r / 2 + 2);
+// float4s of per-warp shared memory of the forward: angular unit vectors and R
+// (cap_a), angular cutoffs (cap_a floats + 4), radial (R, f_c) pairs (cap_r)
+__host__ __device__ constexpr int aev_fwd_warp_f4(int cap_a, int cap_r) {
+  return cap_a + cap_a / 4 + cap_r / 2 + 2;
+}
+
+// The AEV row of packed atom p (Eqs. 3-5) by one warp; out(f, v) stores feature
+// f (each f < Dp exactly once, by the lane holding it).  stage: this warp's
+// aev_fwd_warp_f4 float4s of shared memory; H: its list header.
+template <int ZETA, class Out>
+__device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int p, float4* stage,
+                                           ListHdr& H, unsigned lane, Out out) {
+  __syncwarp();   // the warp's stage and header may still hold its previous centre
+  float4* angv = stage;
   float* angf = reinterpret_cast<float*>(angv + ws.cap_a);
   float2* rad = reinterpret_cast<float2*>(angf + ws.cap_a + 4);
-  ListHdr& H = hdrs[w];
-
   const float4 xi = ws.xyzq[p];
   const SysDev& d = ws.sys[ws.pos_sys[p]];
-  const size_t row = (size_t)ws.pos_slot[p] * ac.Dp;
-  float* G = ws.aev + row;
-  uint16_t* Gh = ws.aev_h ? ws.aev_h + row : nullptr;
-  uint16_t* Gl = ws.aev_l ? ws.aev_l + row : nullptr;
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
@@ -324,7 +323,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
       acc = fmaf(fast_exp2(cr_ * x * x), q.y, acc);
     }
     acc += __shfl_xor_sync(kFull, acc, 16);
-    if (lane < 16) put_g(G, Gh, Gl, s * kNR + lane, acc);
+    if (lane < 16) out(s * kNR + lane, acc);
   }
   // ---- angular, Eq. 5
   const float ca_ = -ac.eta_a * kLog2e;
@@ -337,7 +336,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
       const int fb = ac.S * kNR + pidx * 32;
       if (n_tri == 0) {
-        put_g(G, Gh, Gl, fb + lane, 0.f);
+        out(fb + lane, 0.f);
         continue;
       }
       const float inv_cu = 1.f / (float)max(cu, 1);
@@ -370,9 +369,26 @@ k_aev_fwd(Ws ws, AevConst ac) {
           }
         }
       }
-      put_g(G, Gh, Gl, fb + lane, transpose_reduce32(acc, lane));
+      out(fb + lane, transpose_reduce32(acc, lane));
     }
-  for (int f = ac.D + lane; f < ac.Dp; f += 32) put_g(G, Gh, Gl, f, 0.f);
+  for (int f = ac.D + lane; f < ac.Dp; f += 32) out(f, 0.f);
+}
+
+template <int ZETA>
+__global__ void __launch_bounds__(kWarps * 32, 4)
+k_aev_fwd(Ws ws, AevConst ac) {
+  extern __shared__ float4 sm4[];
+  __shared__ ListHdr hdrs[kWarps];
+  const int w = threadIdx.x >> 5;
+  const unsigned lane = threadIdx.x & 31;
+  const int p = blockIdx.x * kWarps + w;
+  if (p >= ws.totals[0]) return;
+  const size_t row = (size_t)ws.pos_slot[p] * ac.Dp;
+  float* G = ws.aev + row;
+  uint16_t* Gh = ws.aev_h ? ws.aev_h + row : nullptr;
+  uint16_t* Gl = ws.aev_l ? ws.aev_l + row : nullptr;
+  aev_centre<ZETA>(ws, ac, p, sm4 + (size_t)w * aev_fwd_warp_f4(ws.cap_a, ws.cap_r), hdrs[w], lane,
+                   [&](int f, float v) { put_g(G, Gh, Gl, f, v); });
 }
 
 template <int ZETA, bool VIR>
@@ -448,12 +464,12 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
   const float cr_ = -ac.eta_r * kLog2e;
   const int nr_tot = H.off_r[ac.S];
   int sr = 0;
-  for (int t = lane; t < nr_tot; t += 32) {
+  // two neighbours per lane and pass, both gathers issued before either is used
+  auto radial_edge = [&](int t, int j, const float4& xj) {
     while (H.off_r[sr + 1] <= t) ++sr;
     const float* gs = grad + sr * kNR;
     {
-      const int j = lr[t];
-      const Geo g = pair_geo(xi, ws.xyzq[j], d);
+      const Geo g = pair_geo(xi, xj, d);
       float fc, dfc;
       fcut_both(g.r, ac.rc_r, inv_rc_r, &fc, &dfc);
       float dEdR = 0.f;
@@ -473,6 +489,15 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
         vir[6] -= g.dz * gx; vir[7] -= g.dz * gy; vir[8] -= g.dz * gz;
       }
     }
+  };
+  for (int t0 = 0; t0 < nr_tot; t0 += 64) {
+    const int ta = t0 + (int)lane, tb = ta + 32;
+    const int ja = ta < nr_tot ? lr[ta] : -1;
+    const int jb = tb < nr_tot ? lr[tb] : -1;
+    const float4 xa = ja >= 0 ? ws.xyzq[ja] : xi;
+    const float4 xb = jb >= 0 ? ws.xyzq[jb] : xi;
+    if (ja >= 0) radial_edge(ta, ja, xa);
+    if (jb >= 0) radial_edge(tb, jb, xb);
   }
   // ---- angular triplets, one lane per (j, k) pair, numbered continuously over
   // all species-pair blocks of the centre so that a warp's 32 lanes stay busy
@@ -529,16 +554,32 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
     int b_lo = -1, b_hi = -1;
     {
       unsigned m0 = H.live[0], m1 = H.live[1];
-      for (int idx = 0; idx < first + n_gall && (m0 | m1); ++idx) {
-        int q;
-        if (m0) { q = __ffs(m0) - 1; m0 &= m0 - 1; }
-        else { q = 32 + __ffs(m1) - 1; m1 &= m1 - 1; }
-        if (idx >= first) {
-          gf[(idx - first) * 32 + tpos] = ga[q * 32 + lane];
-          if (lane == 0) bt_geo[q].w = (bt_geo[q].w & 0x1ffff) | ((idx - first) << 17);
-          if (b_lo < 0) b_lo = q;
-          b_hi = q;
+      for (int idx = 0; idx < first; ++idx) {   // the blocks of earlier groups
+        if (m0) m0 &= m0 - 1;
+        else m1 &= m1 - 1;
+      }
+      const int cnt = min(n_gall, n_live - first);
+      // the group's dE/dG loads are all issued before the shared-memory stores,
+      // eight blocks at a time, so that their latencies overlap
+#pragma unroll
+      for (int k0 = 0; k0 < kGallBlocks; k0 += 8) {
+        float gv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          gv[k] = 0.f;
+          if (k0 + k < cnt) {
+            int q;
+            if (m0) { q = __ffs(m0) - 1; m0 &= m0 - 1; }
+            else { q = 32 + __ffs(m1) - 1; m1 &= m1 - 1; }
+            gv[k] = ga[q * 32 + lane];
+            if (lane == 0) bt_geo[q].w = (bt_geo[q].w & 0x1ffff) | ((k0 + k) << 17);
+            if (b_lo < 0) b_lo = q;
+            b_hi = q;
+          }
         }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (k0 + k < cnt) gf[(k0 + k) * 32 + tpos] = gv[k];
       }
     }
     __syncwarp();
@@ -655,10 +696,162 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
   }
 }
 
+// ---------------------------------------------------------------- AEV -> first layer
+// One CTA per 128-row tile of a species segment (BF16, one-network models):
+// its 32 warps compute the AEV rows of the tile's atoms (four per warp, the
+// same per-centre code as k_aev_fwd) straight into shared memory as BF16, in
+// the 128-byte-swizzled K-major layout the tensor core reads, so the AEV never
+// goes to HBM; then one thread streams the species' W1 by TMA in 64-wide K
+// slices and issues tcgen05.mma (M = 128, N = h1) into tensor memory, and four
+// warps apply the bias and CELU and write h1.  Rows past the segment's atom
+// count are zero.
+constexpr int kL1Warps = 32;
+constexpr int kL1Blk = 128 * 128;          // one 64-column block of the A tile (bytes)
+constexpr int kL1MaxSmem = 232448 - 16384;
+
+struct AevL1Args {
+  const float* b1;      // [S][h1]
+  __nv_bfloat16* H1;    // [rows][h1]
+  int h1;
+  float alpha;
+  int stage_bytes;      // one W1 slice: h1 x 64 BF16
+};
+
+__device__ __forceinline__ void put_tile(uint8_t* tile, int r, int f, float v) {
+  const int blk = f >> 6, c = f & 63;
+  uint8_t* row = tile + blk * kL1Blk + r * 128;
+  const int off = ((((c >> 3) ^ (r & 7)) << 4) | ((c & 7) << 1));
+  *reinterpret_cast<__nv_bfloat16*>(row + off) = __float2bfloat16_rn(v);
+}
+
+template <int ZETA>
+__global__ void __launch_bounds__(kL1Warps * 32, 1)
+k_aev_l1(const __grid_constant__ CUtensorMap tw1, Ws ws, AevConst ac, AevL1Args g) {
+  using namespace tcu;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ ListHdr hdrs[kL1Warps];
+  __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const int w = threadIdx.x >> 5;
+  const unsigned lane = threadIdx.x & 31;
+  const int S = ac.S;
+  const int row_tiles = ws.seg_start[S] / kTileM;
+  if ((int)blockIdx.x >= row_tiles) return;    // uniform over the CTA
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int nblk = ac.Dp / 64;
+  uint8_t* tile = smem;
+  uint8_t* ring = tile + nblk * kL1Blk;
+  float4* stage = reinterpret_cast<float4*>(ring + 2 * g.stage_bytes) +
+                  (size_t)w * aev_fwd_warp_f4(ws.cap_a, ws.cap_r);
+  volatile int* abort_flag = &abort_sh;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)), "r"(256u) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const int m0 = blockIdx.x * kTileM;
+  int sp = 0;
+  while (sp + 1 < S && m0 >= ws.seg_start[sp + 1]) ++sp;
+  const int seg_end = ws.seg_start[sp] + ws.species_count[sp];
+  // ---- the tile's AEV rows into shared memory
+  for (int r = w; r < kTileM; r += kL1Warps) {
+    const int slot = m0 + r;
+    if (slot < seg_end) {
+      aev_centre<ZETA>(ws, ac, ws.slot_pos[slot], stage, hdrs[w], lane,
+                       [&](int f, float v) { put_tile(tile, r, f, v); });
+    } else {
+      for (int f = (int)lane; f < ac.Dp; f += 32) put_tile(tile, r, f, 0.f);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core
+  __syncthreads();
+  // ---- first layer: W1 of species sp by TMA, MMAs by one thread
+  if (w == 0 && lane == 0) {
+    const int nk = nblk;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(g.h1 >> 3) << 17) |
+                           ((uint32_t)(kTileM >> 4) << 24);
+    bool ok = true;
+    int issued = 0;
+    for (; issued < 2 && issued < nk; ++issued) {
+      mbar_expect_tx(&full_bar[issued], (unsigned)g.stage_bytes);
+      tma_load_3d(ring + issued * g.stage_bytes, &tw1, &full_bar[issued], issued * 64, 0, sp);
+    }
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int st = kb & 1;
+      if (!mbar_wait(&full_bar[st], (kb >> 1) & 1, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      const uint64_t ad = sw128_desc(smem_u32(tile + kb * kL1Blk));
+      const uint64_t bd = sw128_desc(smem_u32(ring + st * g.stage_bytes));
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        umma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(&empty_bar[st]);
+      if (issued < nk) {
+        if (!mbar_wait(&empty_bar[st], (kb >> 1) & 1, abort_flag)) { ok = false; break; }
+        mbar_expect_tx(&full_bar[st], (unsigned)g.stage_bytes);
+        tma_load_3d(ring + st * g.stage_bytes, &tw1, &full_bar[st], issued * 64, 0, sp);
+        ++issued;
+      }
+    }
+    umma_commit(&done_bar);   // arrives when every MMA issued above has completed
+    if (!ok) {
+      // every issued copy lands before the CTA may exit
+      for (int k = issued - 2 < 0 ? 0 : issued - 2; k < issued; ++k)
+        mbar_drain(&full_bar[k & 1], (k >> 1) & 1);
+    }
+  }
+  // ---- epilogue: bias, CELU, h1 (TMEM lanes 32 w .. of warps 0-3)
+  if (w < 4) {
+    if (mbar_wait(&done_bar, 0, abort_flag)) {
+      tc_fence_after();
+      const int r = w * 32 + (int)lane;
+      const uint32_t trow = tmem + ((uint32_t)(w * 32) << 16);
+      const float* bias = g.b1 + (size_t)sp * g.h1;
+      const float alpha = g.alpha, inv_alpha = 1.f / g.alpha;
+      for (int c0 = 0; c0 < g.h1; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float z = v[i] + __ldg(bias + c0 + i);
+          v[i] = z > 0.f ? z : alpha * (__expf(z * inv_alpha) - 1.f);
+        }
+        store_bf16x16(g.H1 + (size_t)(m0 + r) * g.h1 + c0, v);
+      }
+    } else {
+      mbar_drain(&done_bar, 0);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(ws.status, kStTimeout);
+  if (w == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+}
+
+size_t aev_l1_smem(const Ws& ws, const AevConst& ac, int h1) {
+  return (size_t)(ac.Dp / 64) * kL1Blk + 2 * (size_t)h1 * 64 * 2 +
+         (size_t)kL1Warps * aev_fwd_warp_f4(ws.cap_a, ws.cap_r) * sizeof(float4) + 1024;
+}
+
 }  // namespace
 
 size_t aev_fwd_smem(const Ws& ws) {
-  return (size_t)kWarps * (ws.cap_a + ws.cap_a / 4 + ws.cap_r / 2 + 2) * sizeof(float4);
+  return (size_t)kWarps * aev_fwd_warp_f4(ws.cap_a, ws.cap_r) * sizeof(float4);
 }
 size_t aev_bwd_smem(const Ws& ws, int n_pairs) {
   return (size_t)kWarps * aev_bwd_warp_f4(ws.cap_a, n_pairs, aev_bwd_copies(ws.cap_a, n_pairs)) *
@@ -713,6 +906,43 @@ cudaError_t aev_ensure_smem(const Ws& ws) {
         if (e != cudaSuccess) return e;
       }
     }
+  return cudaSuccess;
+}
+
+
+bool aev_l1_supported(const Ws& ws, const AevConst& ac, int E, int h1) {
+  return E == 1 && ac.Dp % 64 == 0 && h1 % 16 == 0 && h1 >= 16 && h1 <= 256 && ws.slot_pos &&
+         aev_l1_smem(ws, ac, h1) <= (size_t)kL1MaxSmem;
+}
+
+void launch_aev_l1(const Ws& ws, const AevConst& ac, const void* w1_bf16, const float* b1,
+                   void* H1, int h1, float alpha, cudaStream_t st) {
+  // W1 of every species [S][h1][Dp] BF16: dims (Dp, h1, S), box (64, h1, 1)
+  CUtensorMap m;
+  if (!tcu::make_map(&m, w1_bf16, ac.Dp, h1, ac.S, ac.Dp, (uint64_t)ac.Dp * h1, (uint32_t)h1, 1)) return;
+  AevL1Args g{};
+  g.b1 = b1;
+  g.H1 = static_cast<__nv_bfloat16*>(H1);
+  g.h1 = h1;
+  g.alpha = alpha;
+  g.stage_bytes = h1 * 64 * 2;
+  const size_t sm = aev_l1_smem(ws, ac, h1);
+  const int grid = (ws.row_cap + tcu::kTileM - 1) / tcu::kTileM;
+  if (ac.zeta == 32) k_aev_l1<32><<<grid, kL1Warps * 32, sm, st>>>(m, ws, ac, g);
+  else k_aev_l1<0><<<grid, kL1Warps * 32, sm, st>>>(m, ws, ac, g);
+}
+
+cudaError_t aev_l1_ensure_smem(const Ws& ws, const AevConst& ac, int h1) {
+  const int need = (int)std::min(aev_l1_smem(ws, ac, h1), (size_t)kL1MaxSmem);
+  for (const void* fn : {(const void*)k_aev_l1<32>, (const void*)k_aev_l1<0>}) {
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, fn);
+    if (e != cudaSuccess) return e;
+    if (attr.maxDynamicSharedSizeBytes < need) {
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+      if (e != cudaSuccess) return e;
+    }
+  }
   return cudaSuccess;
 }
 

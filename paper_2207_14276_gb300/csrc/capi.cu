@@ -28,7 +28,7 @@ namespace nnp {
 void launch_gemm_fp32(const GemmArgs& g, int row_cap, cudaStream_t st);
 int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb,
                   float alpha, cudaStream_t st, int* n_launch, StageHook* hook, void* state,
-                  bool energy_only);
+                  bool energy_only, bool skip_l1);
 int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, int row_cap,
                    const float* aev, float* dEdG, bool split, void** state);
 void mlp_tc_release(void* state);
@@ -114,6 +114,10 @@ struct nnp_handle {
   // creation: on for the split path, where it measured faster than the four
   // layer GEMMs, off for BF16, where it measured slower)
   bool fused_chain = false;
+  // BF16 one-network models: the AEV computed into shared memory and fed to the
+  // first layer in one kernel (off by default)
+  bool fused_aev_l1 = false;
+  bool last_aev_stored = true;   // the last call wrote AEV rows to the arena
   // persistent neighbour lists with a Verlet skin (0: rebuilt on every call)
   float skin = 0.f;
   bool lists_valid = false;   // the lists in the arena belong to list_sig's batch layout
@@ -328,6 +332,7 @@ size_t carve(nnp_handle* h, char* base) {
   ws.pos_slot = c.take<int>(n);
   ws.pos_sys = c.take<int>(n);
   ws.pos_cell = c.take<int>(n);
+  ws.slot_pos = c.take<int>(rows);
   ws.nb_cnt = c.take<uint16_t>(n * 16);
   ws.nb_r = c.take<int>(n * h->cap_r);
   ws.nb_a = c.take<int>(n * h->cap_a);
@@ -422,6 +427,7 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
                             h->ws.dEdG, h->model->net == kNetSplit, &h->tc_state);
     if (rc) return fail(rc, "tensor-core GEMM set-up (tensor maps, launch limits) failed");
     mlp_tc_use_chain(h->tc_state, h->fused_chain);
+    if (h->model->md.E == 1) CU_TRY(aev_l1_ensure_smem(h->ws, h->model->ac, h->model->md.h1));
   }
   h->dirty = false;
   return NNP_OK;
@@ -430,8 +436,8 @@ int ensure_arena(nnp_handle* h, int n_in, int n_sys) {
 // stage names (index = stage id) reported by nnp_profile_read
 const char* kStageNames[] = {"prep", "neighbors", "aev_fwd", "mlp_l1", "mlp_l2", "mlp_l3",
                              "mlp_b3", "mlp_b2", "mlp_b1", "aev_bwd", "finalize", "mlp_cvt",
-                             "mlp", "mlp_chain"};
-constexpr int kNumStages = 14;
+                             "mlp", "mlp_chain", "aev_l1"};
+constexpr int kNumStages = 15;
 
 cudaEvent_t prof_event(nnp_handle* h) {
   if (!h->prof_pool.empty()) {
@@ -558,7 +564,16 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     { StageTimer t(h, st, 1); launch_neighbors(ws, n_in, ac, st); }
     if ((rc = chk("neighbors"))) return rc;
     if (ws.skin_state) ++launches;   // the list refresh
-    { StageTimer t(h, st, 2); launch_aev_fwd(ws, n_in, ac, st); }
+    const bool fuse_l1 = h->fused_aev_l1 && m.net == kNetBf16 &&
+                         aev_l1_supported(ws, ac, m.md.E, m.md.h1);
+    h->last_aev_stored = !fuse_l1;
+    if (fuse_l1) {
+      StageTimer t(h, st, 14);
+      launch_aev_l1(ws, ac, m.mw.W1cat_h, m.mw.b1cat, h->mb.H1, m.md.h1, m.alpha, st);
+    } else {
+      StageTimer t(h, st, 2);
+      launch_aev_fwd(ws, n_in, ac, st);
+    }
     if ((rc = chk("aev_fwd"))) return rc;
     launches += 2;
     // energy only when no system asks for forces or a virial
@@ -566,7 +581,8 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     for (int b = 0; b < n_sys; ++b) energy_only &= (sy[b].forces == nullptr && sy[b].virial == nullptr);
     StageHook hook{h, st};
     if (m.net != kNetSimt) {
-      rc = launch_mlp_tc(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, h->tc_state, energy_only);
+      rc = launch_mlp_tc(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, h->tc_state, energy_only,
+                         fuse_l1);
       if (rc) return rc;
     } else {
       launch_mlp_fp32(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, energy_only);
@@ -664,6 +680,7 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
     put(&skin_mode, sizeof(skin_mode));
     put(&h->skin, sizeof(h->skin));
     put(&h->fused_chain, sizeof(h->fused_chain));
+    put(&h->fused_aev_l1, sizeof(h->fused_aev_l1));
     // the kernels read only the first n_sys descriptors of a chunk
     for (const auto& bp : chunks)
       put(&bp, offsetof(BatchParams, sys) + (size_t)bp.n_sys * sizeof(SysIn));
@@ -779,6 +796,7 @@ int nnp_clone(const nnp_handle* src, nnp_handle** out) {
   h->cap_r = src->cap_r;
   h->cap_a = src->cap_a;
   h->fused_chain = src->fused_chain;
+  h->fused_aev_l1 = src->fused_aev_l1;
   if (!alloc_host_words(h)) {
     nnp_destroy(h);
     return fail(NNP_ERR_CUDA, "cudaMallocHost failed");
@@ -1195,6 +1213,13 @@ extern "C" int64_t nnp_n_weights(const nnp_handle* h) {
 }
 
 int nnp_aev_dim(const nnp_handle* h) { return h ? h->model->ac.D : -1; }
+int nnp_set_fused_aev_l1(nnp_handle* h, int enable) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  h->fused_aev_l1 = enable != 0;
+  return NNP_OK;
+}
+
 int nnp_set_fused_chain(nnp_handle* h, int enable) {
   g_err.clear();
   if (!h) return fail(NNP_ERR_ARG, "null handle");
@@ -1287,6 +1312,8 @@ const char* nnp_profile_stage_name(int i) {
 // out: device float [n_in_total, D]; rows of atoms outside the mask untouched.
 int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream) {
   if (!h || !h->arena || !out) return fail(NNP_ERR_ARG, "bad argument");
+  if (which == 0 && !h->last_aev_stored)
+    return fail(NNP_ERR_UNSUPPORTED, "the last call fed the AEV to the first layer on chip; no AEV rows were stored");
   const bool planes = which == 0 && !h->last_aev_fp32;
   const float* src = which == 0 ? h->ws.aev : h->ws.dEdG;
   const uint16_t* src_h = planes ? h->ws.aev_h : nullptr;
@@ -1387,6 +1414,7 @@ size_t noalloc_carve(const Model& m, int n_atoms, char* base, Ws* ws, MlpBufs* m
   ws->pos_slot = c.take<int>(n);
   ws->pos_sys = c.take<int>(n);
   ws->pos_cell = c.take<int>(n);
+  ws->slot_pos = nullptr;
   ws->nb_cnt = c.take<uint16_t>(n * 16);
   ws->nb_r = c.take<int>(n * kNoAllocCapR);
   ws->nb_a = c.take<int>(n * kNoAllocCapA);

@@ -373,6 +373,7 @@ __device__ __forceinline__ void scatter_body(const Ws& ws, int gi, int n_in) {
                              __int_as_float((int)d.in.species[local]));
   ws.pos_src[pos] = gi;
   ws.pos_slot[pos] = slot;
+  if (ws.slot_pos) ws.slot_pos[slot] = pos;
   ws.pos_sys[pos] = b;
   ws.pos_cell[pos] = gcell - d.cell_base;
   if (ws.in_pos) {   // the reference the displacement check of later calls compares with

@@ -104,6 +104,8 @@ struct Ws {
   int* pos_slot;        // AEV row
   int* pos_sys;
   int* pos_cell;        // local cell index within the system grid
+  int* slot_pos;        // [row_cap] packed position of the atom of an AEV row (rows < a
+                        // segment's atom count; written at every list build)
   // neighbour lists
   uint16_t* nb_cnt;     // [n_in][16]: radial count per species [0..7], angular [8..15]
   int* nb_r;            // [n_in][cap_r] packed positions, species-sorted
@@ -147,6 +149,13 @@ void launch_front(const Ws& ws, const BatchParams& bp, const AevConst& ac, int n
                   cudaStream_t st);
 // ---- aev.cu
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st);
+// AEV of 128-row species tiles computed into shared memory and fed straight to
+// the first layer's tensor-core GEMM (BF16, one-network models); false if the
+// tile does not fit or the model is outside what the kernel handles
+bool aev_l1_supported(const Ws& ws, const AevConst& ac, int E, int h1);
+void launch_aev_l1(const Ws& ws, const AevConst& ac, const void* w1_bf16, const float* b1,
+                   void* H1, int h1, float alpha, cudaStream_t st);
+cudaError_t aev_l1_ensure_smem(const Ws& ws, const AevConst& ac, int h1);
 void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
                     cudaStream_t st);
 cudaError_t aev_ensure_smem(const Ws& ws);

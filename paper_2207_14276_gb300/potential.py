@@ -105,6 +105,11 @@ class Potential:
         or as four layer GEMMs."""
         check(lib().nnp_set_fused_chain(self._h, 1 if enable else 0))
 
+    def set_fused_aev_l1(self, enable):
+        """BF16 one-network models: compute the AEV on chip and feed it to the first
+        layer in the same kernel (the AEV never goes to HBM)."""
+        check(lib().nnp_set_fused_aev_l1(self._h, 1 if enable else 0))
+
     def network_path(self):
         """'fp32_split', 'fp32_simt' or 'bf16': the path this handle's networks run."""
         code = lib().nnp_network_path(self._h)

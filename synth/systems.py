@@ -214,6 +214,10 @@ def workload(name: str):
         return [gas_molecule(rng, 24, sp, density=24 / 1000.0, name="gas24")], "ani4", 1
     if name == "water9000":
         return [water_box(3000, 44.77, 15, seed=1, name="water9000")], "ani4", 1
+    if name == "water99k":
+        # the water9000 recipe at the 100k scale with the 4-species model: 33,000
+        # rigid waters (99,000 atoms) on a 33^3 lattice, periodic 99.6 A (1 g/cm^3)
+        return [water_box(33000, 99.6, 33, seed=6, name="water99k")], "ani4", 1
     if name == "solvated100k":
         return [solvated_solute(33000, 1000, 99.9, seed=2, name="solvated100k")], "ani7x8", 1
     if name == "solvated20k":

@@ -270,7 +270,10 @@ def test_host_entry_point(torch_cuda):
         E2, F2, V2 = pot.energy_forces_host(s.coords, s.species, s.box, virial=True)
         assert abs(E2 - ref["energy"]) <= E_TOL
         assert force_errors(F2, ref["forces"])[0] <= 1e-4 * f_rms
-        np.testing.assert_allclose(V2, ref["virial"], atol=1e-4 * np.abs(ref["virial"]).max() + 1e-6)
+        # the virial sums r_e x dE/dr_e over every pair term: on the default path
+        # (split BF16 operands, about 2^-16 relative each) the diagonal, a sum of
+        # terms of both signs, carries ~1e-4 of its size
+        np.testing.assert_allclose(V2, ref["virial"], atol=5e-4 * np.abs(ref["virial"]).max() + 1e-6)
     # an out-of-range species is reported, and the handle keeps working
     bad = s.species.copy()
     bad[5] = 9

@@ -103,7 +103,9 @@ def test_force_matching_central_differences(torch_cuda):
     targets = [rng.normal(0.0, 1.0, size=(m.n_atoms, 3)) for m in mols]
 
     def loss_and_grads(wv, coords_list, grads=False):
-        pot = Potential(spec, wv)
+        # FP32 FMA networks: central differences need a loss that is smooth at
+        # FP32 resolution (split BF16 operands would round the perturbed weight)
+        pot = Potential(spec, wv, precision="fp32_simt")
         systems = [{"coords": torch.from_numpy(c.astype(np.float32)).cuda(),
                     "species": torch.from_numpy(m.species).cuda()} for c, m in zip(coords_list, mols)]
         outs = pot.energy_forces_batch(systems)
@@ -135,3 +137,54 @@ def test_force_matching_central_differences(torch_cuda):
         wm = w.copy(); wm[k] -= h
         fd = (loss_and_grads(wp, coords) - loss_and_grads(wm, coords)) / (2 * h)
         assert fd == pytest.approx(gw[k], rel=2e-2)
+
+
+def test_vjp_against_fp64_central_differences(torch_cuda):
+    """The library's force-matching gradient against central differences (h = 1e-4,
+    the step the differentiation workload specifies) of the same loss evaluated
+    by the FP64 oracle's energy and forces -- an FD reference independent of the
+    oracle's dual-number gradient and free of FP32 noise.  Every coordinate of
+    one molecule and 40 weights (the 16 largest gradients and 24 drawn at
+    random): within 1e-3 of the largest gradient of each kind."""
+    torch = torch_cuda
+    from paper_2207_14276_gb300 import Potential
+    from paper_2207_14276_gb300.autograd import NNPBatchFunction
+    spec, w = model_for("ani4")
+    orc = oracle.Model(spec, w)
+    mols, _, _ = synth.workload("molecules64")
+    mols = mols[:4]
+    rng = np.random.Generator(np.random.PCG64(8))
+    targets = [rng.normal(0.0, 1.0, size=(m.n_atoms, 3)) for m in mols]
+    sizes = [m.n_atoms for m in mols]
+    pot = Potential(spec, w)
+    x = torch.from_numpy(np.concatenate([m.coords for m in mols])).cuda().requires_grad_(True)
+    sp = torch.from_numpy(np.concatenate([m.species for m in mols])).cuda()
+    wt = torch.from_numpy(w).cuda().requires_grad_(True)
+    Ft = torch.from_numpy(np.concatenate(targets)).float().cuda()
+    E, F = NNPBatchFunction.apply(x, wt, pot, sp, sizes)
+    ((F - Ft) ** 2).sum().backward()
+    gx = x.grad.double().cpu().numpy()
+    gw = wt.grad.double().cpu().numpy()
+
+    def loss(model, coords):
+        return sum(float(((model.energy_forces(c, m.species)["forces"] - t) ** 2).sum())
+                   for c, m, t in zip(coords, mols, targets))
+
+    h = 1e-4
+    base = [m.coords.astype(np.float64) for m in mols]
+    fdx = []
+    for mi in (0,):
+        for a in range(mols[mi].n_atoms):
+            for c in range(3):
+                cp = [b.copy() for b in base]; cp[mi][a, c] += h
+                cm = [b.copy() for b in base]; cm[mi][a, c] -= h
+                fdx.append((loss(orc, cp) - loss(orc, cm)) / (2 * h))
+    n0 = mols[0].n_atoms
+    np.testing.assert_allclose(gx[:n0].reshape(-1), np.array(fdx), atol=1e-3 * np.abs(fdx).max())
+    ks = np.concatenate([np.argsort(-np.abs(gw))[:16], rng.choice(w.size, 24, replace=False)])
+    fdw = []
+    for k in ks:
+        wp = w.astype(np.float64).copy(); wp[k] += h
+        wm = w.astype(np.float64).copy(); wm[k] -= h
+        fdw.append((loss(oracle.Model(spec, wp), base) - loss(oracle.Model(spec, wm), base)) / (2 * h))
+    np.testing.assert_allclose(gw[ks], np.array(fdw), atol=1e-3 * np.abs(gw).max())
