@@ -68,9 +68,9 @@ def parse():
     ap.add_argument("--workload", default="solvated100k")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "fp32_split", "fp32_simt", "bf16"])
-    ap.add_argument("--no-fused-chain", action="store_true",
-                    help="run L2, L3, B3, B2 as four layer GEMMs on every tensor-core path "
-                         "(default: the fused per-network kernel on the split path only)")
+    ap.add_argument("--fused-chain", action="store_true",
+                    help="tensor-core paths: run L2, L3, B3, B2 as the fused per-network "
+                         "kernel instead of four layer GEMMs")
     ap.add_argument("--fused-aev-l1", action="store_true",
                     help="BF16 one-network models: AEV computed on chip and fed to the first "
                          "layer in one kernel")
@@ -606,8 +606,8 @@ def run_ours(args):
     spec = synth.model_spec(kind)
     w = synth.make_weights(spec, wseed)
     pot = Potential(spec, w, precision=args.precision)
-    if args.no_fused_chain:     # otherwise each network path keeps its default
-        pot.set_fused_chain(False)
+    if args.fused_chain:
+        pot.set_fused_chain(True)
     pot.set_fused_aev_l1(args.fused_aev_l1)
     s = systems[0]
     x = torch.from_numpy(s.coords).to(dev)
@@ -722,8 +722,8 @@ def run_ours(args):
     beside = None
     if args.precision != "bf16" and not args.no_bf16_beside:
         pb = Potential(spec, w, precision="bf16")
-        if args.no_fused_chain:
-            pb.set_fused_chain(False)
+        if args.fused_chain:
+            pb.set_fused_chain(True)
         pb.energy_forces(x, sp, box, mask)
         for _ in range(args.warmup):
             pb.energy_forces_into(x, sp, box, mask, E, F)

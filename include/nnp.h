@@ -299,9 +299,9 @@ int nnp_aev_dim(const nnp_handle* h);
  * after the first -- L2, L3 with the output layer, and their backward B3, B2 --
  * as one fused kernel per 128-row tile with the activations in shared memory
  * (widths multiples of 16, at most 256); 0 runs them as four layer GEMMs
- * through HBM.  Both give the same result to rounding order.  Default: on for
- * NNP_FP32 / NNP_FP32_SPLIT handles, off for NNP_BF16_MLP (the faster choice of
- * each on the 100k-atom 8-network workload).  Clones inherit the setting.  No
+ * through HBM.  Both give the same result to rounding order.  Default: off (on
+ * the 100k-atom 8-network workload the fused kernel ties with the four GEMMs on
+ * the split path and is slower on BF16).  Clones inherit the setting.  No
  * effect on NNP_FP32_SIMT handles. */
 int nnp_set_fused_chain(nnp_handle* h, int enable);
 /* BF16 handles of one-network models: enable != 0 computes the AEV rows of each

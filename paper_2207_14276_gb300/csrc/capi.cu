@@ -110,9 +110,9 @@ struct nnp_handle {
   std::string gsig;       // signature of the captured call
   std::string last_sig;   // signature of the previous eager call
   int last_launches_graph = 0;
-  // tensor-core paths: the layers after the first as one fused kernel (set at
-  // creation: on for the split path, where it measured faster than the four
-  // layer GEMMs, off for BF16, where it measured slower)
+  // tensor-core paths: the layers after the first as one fused kernel (off by
+  // default: on the 100k-atom ensemble it ties with the four layer GEMMs on the
+  // split path and is slower on BF16)
   bool fused_chain = false;
   // BF16 one-network models: the AEV computed into shared memory and fed to the
   // first layer in one kernel (off by default)
@@ -778,7 +778,6 @@ int nnp_create(const nnp_species_t* species, const nnp_aev_params_t* aev,
   nnp_handle* h = new nnp_handle;
   h->model = m.release();
   h->budget = hbm_budget_bytes;
-  h->fused_chain = (h->model->net == kNetSplit);
   if (!alloc_host_words(h)) {
     nnp_destroy(h);
     return fail(NNP_ERR_CUDA, "cudaMallocHost failed");

@@ -198,11 +198,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       const int m = tl.m0 + q * 32 + lane;
       // the backward's stored activations do not depend on the MMAs: their loads
       // are issued before the wait for the accumulator
-      constexpr bool kPre = (EPI == kEpiMul) && !SPLIT;
+      // (the split path also prefetches the low parts)
+      constexpr bool kPre = (EPI == kEpiMul);
       uint4 pre[kPre ? kMaxChunks : 1][2];
+      uint4 prel[kPre && SPLIT ? kMaxChunks : 1][2];
       if (kPre) {
-        const __nv_bfloat16* arow = static_cast<const __nv_bfloat16*>(g.aux) + (size_t)m * g.ld_aux +
-                                    (size_t)tl.e * g.aux_net + tl.n0;
+        const size_t oa = (size_t)m * g.ld_aux + (size_t)tl.e * g.aux_net + tl.n0;
+        const __nv_bfloat16* arow = static_cast<const __nv_bfloat16*>(g.aux) + oa;
+        const __nv_bfloat16* lrow = SPLIT ? static_cast<const __nv_bfloat16*>(g.aux2) + oa : nullptr;
 #pragma unroll
         for (int ci = 0; ci < kMaxChunks; ++ci) {
           const int c0 = half * 16 + 32 * ci;
@@ -210,6 +213,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
             const uint4* src = reinterpret_cast<const uint4*>(arow + c0);
             pre[ci][0] = src[0];
             pre[ci][1] = src[1];
+            if (SPLIT) {
+              const uint4* srl = reinterpret_cast<const uint4*>(lrow + c0);
+              prel[ci][0] = srl[0];
+              prel[ci][1] = srl[1];
+            }
           }
         }
       }
@@ -284,21 +292,23 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           // 1 + h / alpha otherwise (exp(z/alpha) = 1 + h/alpha on that branch)
           float a[16];
           const size_t o = (size_t)m * g.ldo + (size_t)tl.e * g.out_net + n;
-          if (SPLIT) {
-            // the stored activation h = hi + lo (about 16 significant bits)
-            const size_t oa = (size_t)m * g.ld_aux + (size_t)tl.e * g.aux_net + n;
-            float al[16];
-            load_bf16x16(static_cast<const __nv_bfloat16*>(g.aux) + oa, a);
-            load_bf16x16(static_cast<const __nv_bfloat16*>(g.aux2) + oa, al);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) a[i] += al[i];
-          } else {
+          {
             const uint32_t* w = reinterpret_cast<const uint32_t*>(pre[kPre ? ci : 0]);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
               a[2 * i] = f.x;
               a[2 * i + 1] = f.y;
+            }
+          }
+          if (SPLIT) {
+            // the stored activation h = hi + lo (about 16 significant bits)
+            const uint32_t* wl = reinterpret_cast<const uint32_t*>(prel[kPre && SPLIT ? ci : 0]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wl[i]));
+              a[2 * i] += f.x;
+              a[2 * i + 1] += f.y;
             }
           }
 #pragma unroll
@@ -540,7 +550,8 @@ void launch_wait_probe(int* status, unsigned limit, cudaStream_t st) {
 }
 
 int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, float alpha,
-                  cudaStream_t st, int* n_launch, StageHook* hook, void* state, bool energy_only) {
+                  cudaStream_t st, int* n_launch, StageHook* hook, void* state, bool energy_only,
+                  bool skip_l1) {
   (void)mw; (void)mb;
   TcState* s = static_cast<TcState*>(state);
   if (!s) return NNP_ERR_ARG;
@@ -549,6 +560,7 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
   const bool chain = s->chain && s->use_chain;
   const size_t n_plans = energy_only ? 3 : s->plans.size();
   for (size_t i = 0; i < n_plans; ++i) {
+    if (i == 0 && skip_l1) continue;   // the first layer ran with the AEV kernel
     if (chain && i >= 1 && i <= 4) {
       if (i == 1) {
         if (hook) hook->begin(13);
@@ -586,7 +598,7 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
 #undef NNP_TC_LAUNCH
     if (hook) hook->end();
   }
-  if (n_launch) *n_launch += chain ? (energy_only ? 2 : 3) : (int)n_plans;
+  if (n_launch) *n_launch += (chain ? (energy_only ? 2 : 3) : (int)n_plans) - (skip_l1 ? 1 : 0);
   return NNP_OK;
 }
 
