@@ -138,7 +138,21 @@ def recorded_traffic(stage, workload):
     return None
 
 
-def stage_work(stage, spec, counts, n_atoms, path):
+def sparse_fractions(masks, Dp, n_tile=256):
+    """(fraction of the AEV's 64-column K slices the first layer processes, fraction
+    of the last backward layer's N columns it computes) from the tile masks:
+    every live slice of a tile, and every n_tile-column block with one."""
+    if masks is None or len(masks) == 0:
+        return 1.0, 1.0
+    n_sl = (Dp + 63) // 64
+    k = float(np.mean([bin(int(m) & ((1 << n_sl) - 1)).count("1") for m in masks])) / n_sl
+    per = n_tile // 64
+    blocks = [(int(m) >> b) & ((1 << per) - 1) for m in masks for b in range(0, n_sl, per)]
+    nfrac = float(np.mean([1.0 if x else 0.0 for x in blocks]))
+    return k, nfrac
+
+
+def stage_work(stage, spec, counts, n_atoms, path, sparse=(1.0, 1.0)):
     """Algorithmic work of one launch of a stage: (amount, unit, bound).
 
     counts: mean radial neighbours n_r and angular neighbours n_a per atom.
@@ -149,7 +163,10 @@ def stage_work(stage, spec, counts, n_atoms, path):
     contraction and, backward, the derivatives and two edge gradients), and
     2 K N per row for a network layer.  path: the network path of the handle
     ('fp32_simt', 'fp32_split' or 'bf16'); a split-path layer issues three BF16
-    tensor products per term of its 2 K N, so its bound is the BF16 peak / 3."""
+    tensor products per term of its 2 K N, so its bound is the BF16 peak / 3.
+    sparse: the fractions of the first layer's K and the last backward layer's N
+    that sparse AEV rows leave (the rest multiplies exact zeros or yields
+    columns nothing reads)."""
     D = spec.widths[0]
     E = spec.n_ensemble
     h1, h2, h3 = spec.widths[1:4]
@@ -176,19 +193,23 @@ def stage_work(stage, spec, counts, n_atoms, path):
             "mlp_b3": (h3, h2 * E), "mlp_b2": (h2, h1 * E), "mlp_b1": (E * h1, D)}
     if stage in gemm:
         k, n = gemm[stage]
+        if stage == "mlp_l1":
+            k = k * sparse[0]
+        if stage == "mlp_b1":
+            n = n * sparse[1]
         bound = {"bf16": "tensor", "fp32_split": "tensor_split"}.get(path, "alu")
         return 2.0 * n_atoms * k * n, "FLOP", bound
     return None
 
 
-def roofline(stages, spec, counts, n_eval, path, peaks, peak_src, workload):
+def roofline(stages, spec, counts, n_eval, path, peaks, peak_src, workload, sparse=(1.0, 1.0)):
     """Roofline entry of the dominant stage (largest time over the profiled pass)."""
     live = [k for k in stages if stages[k][1] > 0]
     if not live:
         return None
     dom = max(live, key=lambda k: stages[k][0])
     dom_ms = stages[dom][0] / stages[dom][1]
-    work = stage_work(dom, spec, counts, n_eval, path)
+    work = stage_work(dom, spec, counts, n_eval, path, sparse)
     if work is None:
         return None
     amount, unit, bound = work
@@ -676,7 +697,9 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     clk = clocks.summary(t0, t1)
     path = pot.network_path()
-    roof = roofline(stages, spec, counts, n_eval, path, peaks, peak_src, args.workload)
+    Dp = (spec.widths[0] + 63) // 64 * 64
+    sparse = sparse_fractions(pot.tile_masks() if path != "fp32_simt" else None, Dp)
+    roof = roofline(stages, spec, counts, n_eval, path, peaks, peak_src, args.workload, sparse)
 
     # end to end through the host entry point (pinned host buffers, copies inside)
     e2e = None
@@ -737,7 +760,7 @@ def run_ours(args):
                   "latency_ms": {"p50": float(np.percentile(b_ms, 50)),
                                  "p99": float(np.percentile(b_ms, 99))},
                   "roofline": roofline(b_stages, spec, counts, n_eval, "bf16", peaks, peak_src,
-                                       args.workload),
+                                       args.workload, sparse_fractions(pb.tile_masks(), Dp)),
                   "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in b_stages.items()
                                          if v[1]}}
         if errors is not None:
@@ -896,6 +919,8 @@ def run_ours(args):
         "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1]},
         "stage_pass_ms_per_step": sum(prof_ms) / len(prof_ms),
         "neighbours_per_atom": {"radial": counts[0], "angular": counts[1]},
+        "sparse_aev_rows": {"first_layer_k_fraction": sparse[0],
+                            "last_layer_n_fraction": sparse[1]},
         "serving": serving,
         "persistent_lists": md,
         "snapshot_batch": snap,

@@ -304,6 +304,22 @@ int nnp_aev_dim(const nnp_handle* h);
  * the split path and is slower on BF16).  Clones inherit the setting.  No
  * effect on NNP_FP32_SIMT handles. */
 int nnp_set_fused_chain(nnp_handle* h, int enable);
+/* Tensor-core paths: enable != 0 (the default) writes each AEV row only in the
+ * 64-column slices that hold a species or species-pair block with any term
+ * (the rest of the row is zero: for a water molecule's atom most of the
+ * 7-species blocks), and runs the first layer over the slices that are live in
+ * some row of each 128-row tile and the last backward layer only for the
+ * columns of those slices; 0 writes and multiplies whole rows.  The result is
+ * the same (the skipped products are exact zeros; the dE/dG columns not
+ * computed are those the forces never read).  While it is on, nnp_debug_rows
+ * returns 0 for AEV slices a row does not hold and for dE/dG slices its tile
+ * does not compute. */
+int nnp_set_sparse_rows(nnp_handle* h, int enable);
+/* The live-slice masks of the last call's 128-row AEV tiles (bit k: columns
+ * 64k .. 64k+63), copied to out_host (at most max_tiles); *n_tiles receives the
+ * count (0 when the last call wrote whole rows).  Synchronises `stream`. */
+int nnp_debug_tile_masks(nnp_handle* h, void* stream, uint32_t* out_host, int max_tiles,
+                         int* n_tiles);
 /* BF16 handles of one-network models: enable != 0 computes the AEV rows of each
  * 128-row species tile in shared memory and feeds them to the first layer's
  * tensor-core GEMM in the same kernel, so the AEV is never written to HBM (the

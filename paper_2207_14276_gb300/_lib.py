@@ -46,7 +46,8 @@ EXPORTS = (
     "nnp_server_poll", "nnp_server_stats", "nnp_force_vjp_batch", "nnp_force_vjp",
     "nnp_n_weights", "nnp_debug_wait_probe", "nnp_set_skin", "nnp_list_stats",
     "nnp_integrate", "nnp_noalloc_max_atoms", "nnp_debug_cell_grid", "nnp_network_path",
-    "nnp_set_fused_chain", "nnp_set_fused_aev_l1",
+    "nnp_set_fused_chain", "nnp_set_fused_aev_l1", "nnp_set_sparse_rows",
+    "nnp_debug_tile_masks",
 )
 
 
@@ -121,6 +122,8 @@ def lib():
     L.nnp_network_path.argtypes = [P]
     L.nnp_set_fused_chain.argtypes = [P, i]
     L.nnp_set_fused_aev_l1.argtypes = [P, i]
+    L.nnp_set_sparse_rows.argtypes = [P, i]
+    L.nnp_debug_tile_masks.argtypes = [P, P, P, i, ctypes.POINTER(i)]
     L.nnp_last_launch_count.argtypes = [P]
     L.nnp_last_error.restype = ctypes.c_char_p
     L.nnp_last_error.argtypes = []

@@ -277,6 +277,41 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32], unsigned lan
   return v[0];
 }
 
+// The 64-column slices of a centre's AEV row that hold a block with any term:
+// radial block s (columns 16 s ..) when the centre has neighbours of species s,
+// angular block q of species pair (s, u) (columns 16 S + 32 q ..) when it has a
+// pair j < k of those species; bit 0 is always set.  All other slices of the row
+// are zero.  The same value on every lane.
+// pair_su[q] = s | u << 4 for species pair q (s <= u, upper triangle row-major)
+__device__ __forceinline__ void fill_pair_table(uint8_t* pair_su, const AevConst& ac) {
+  for (int q = threadIdx.x; q < ac.n_pairs; q += blockDim.x) {
+    int sp = 0, rem = q;
+    while (rem >= ac.S - sp) { rem -= ac.S - sp; ++sp; }
+    pair_su[q] = (uint8_t)(sp | ((sp + rem) << 4));
+  }
+}
+
+__device__ __forceinline__ uint32_t row_slices(const ListHdr& H, const AevConst& ac, unsigned lane,
+                                               const uint8_t* pair_su) {
+  uint32_t m = 1u;
+  if ((int)lane < ac.S && H.off_r[lane + 1] > H.off_r[lane]) m |= 1u << (((int)lane * kNR) >> 6);
+  for (int q = (int)lane; q < ac.n_pairs; q += 32) {
+    const int sp = pair_su[q] & 15, u = pair_su[q] >> 4;
+    const int cs = H.off_a[sp + 1] - H.off_a[sp], cu = H.off_a[u + 1] - H.off_a[u];
+    if (sp == u ? cs >= 2 : (cs > 0 && cu > 0)) {
+      const int f0 = ac.S * kNR + q * 32;
+      m |= (1u << (f0 >> 6)) | (1u << ((f0 + 31) >> 6));
+    }
+  }
+  return __reduce_or_sync(kFull, m);
+}
+
+// whether a block of `width` columns from f0 touches a slice of mask m
+__device__ __forceinline__ bool block_in(uint32_t m, int f0, int width) {
+  const int a = f0 >> 6, b = (f0 + width - 1) >> 6;
+  return (m >> a) & 1u || (m >> b) & 1u;
+}
+
 // float4s of per-warp shared memory of the forward: angular unit vectors and R
 // (cap_a), angular cutoffs (cap_a floats + 4), radial (R, f_c) pairs (cap_r)
 __host__ __device__ constexpr int aev_fwd_warp_f4(int cap_a, int cap_r) {
@@ -285,10 +320,13 @@ __host__ __device__ constexpr int aev_fwd_warp_f4(int cap_a, int cap_r) {
 
 // The AEV row of packed atom p (Eqs. 3-5) by one warp; out(f, v) stores feature
 // f (each f < Dp exactly once, by the lane holding it).  stage: this warp's
-// aev_fwd_warp_f4 float4s of shared memory; H: its list header.
+// aev_fwd_warp_f4 float4s of shared memory; H: its list header.  With sparse
+// set, only the blocks that touch a live slice of the row (row_slices) are
+// stored, and *mask receives the row's slice mask.
 template <int ZETA, class Out>
 __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int p, float4* stage,
-                                           ListHdr& H, unsigned lane, Out out) {
+                                           ListHdr& H, unsigned lane, Out out, bool sparse = false,
+                                           uint32_t* mask = nullptr, const uint8_t* pair_su = nullptr) {
   __syncwarp();   // the warp's stage and header may still hold its previous centre
   float4* angv = stage;
   float* angf = reinterpret_cast<float*>(angv + ws.cap_a);
@@ -296,6 +334,8 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
   const float4 xi = ws.xyzq[p];
   const SysDev& d = ws.sys[ws.pos_sys[p]];
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
+  const uint32_t m = sparse ? row_slices(H, ac, lane, pair_su) : ~0u;
+  if (mask) *mask = m;
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
   const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
@@ -323,7 +363,7 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
       acc = fmaf(fast_exp2(cr_ * x * x), q.y, acc);
     }
     acc += __shfl_xor_sync(kFull, acc, 16);
-    if (lane < 16) out(s * kNR + lane, acc);
+    if (lane < 16 && block_in(m, s * kNR, kNR)) out(s * kNR + lane, acc);
   }
   // ---- angular, Eq. 5
   const float ca_ = -ac.eta_a * kLog2e;
@@ -336,7 +376,7 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
       const int fb = ac.S * kNR + pidx * 32;
       if (n_tri == 0) {
-        out(fb + lane, 0.f);
+        if (block_in(m, fb, 32)) out(fb + lane, 0.f);
         continue;
       }
       const float inv_cu = 1.f / (float)max(cu, 1);
@@ -371,7 +411,8 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
       }
       out(fb + lane, transpose_reduce32(acc, lane));
     }
-  for (int f = ac.D + lane; f < ac.Dp; f += 32) out(f, 0.f);
+  for (int f = ac.D + lane; f < ac.Dp; f += 32)
+    if ((m >> (f >> 6)) & 1u) out(f, 0.f);
 }
 
 template <int ZETA>
@@ -379,16 +420,51 @@ __global__ void __launch_bounds__(kWarps * 32, 4)
 k_aev_fwd(Ws ws, AevConst ac) {
   extern __shared__ float4 sm4[];
   __shared__ ListHdr hdrs[kWarps];
+  __shared__ uint8_t pair_su[kMaxSpecies * (kMaxSpecies + 1) / 2];
   const int w = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31;
   const int p = blockIdx.x * kWarps + w;
+  const bool sparse = ws.row_mask != nullptr;
+  if (sparse) {
+    fill_pair_table(pair_su, ac);
+    __syncthreads();
+  }
   if (p >= ws.totals[0]) return;
   const size_t row = (size_t)ws.pos_slot[p] * ac.Dp;
   float* G = ws.aev + row;
   uint16_t* Gh = ws.aev_h ? ws.aev_h + row : nullptr;
   uint16_t* Gl = ws.aev_l ? ws.aev_l + row : nullptr;
+  uint32_t m = 0;
   aev_centre<ZETA>(ws, ac, p, sm4 + (size_t)w * aev_fwd_warp_f4(ws.cap_a, ws.cap_r), hdrs[w], lane,
-                   [&](int f, float v) { put_g(G, Gh, Gl, f, v); });
+                   [&](int f, float v) { put_g(G, Gh, Gl, f, v); }, sparse, &m, pair_su);
+  if (sparse && lane == 0) {
+    const int slot = ws.pos_slot[p];
+    ws.row_mask[slot] = m;
+    atomicOr(ws.tile_mask + (slot >> 7), m);
+  }
+}
+
+// One warp per AEV row of a species segment: zero the 64-column slices the row's
+// tile reads (tile mask) that the row did not write (row mask).  Padding rows
+// past a segment's atoms are left alone (their network outputs are never read).
+__global__ void __launch_bounds__(256) k_aev_fill(Ws ws, AevConst ac) {
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const unsigned lane = threadIdx.x & 31;
+  if (r >= ws.seg_start[ac.S]) return;
+  int s = 0;
+  while (s + 1 < ac.S && r >= ws.seg_start[s + 1]) ++s;
+  if (r >= ws.seg_start[s] + ws.species_count[s]) return;
+  uint32_t miss = ws.tile_mask[r >> 7] & ~ws.row_mask[r];
+  const size_t row = (size_t)r * ac.Dp;
+  while (miss) {
+    const int k = __ffs(miss) - 1;
+    miss &= miss - 1;
+    const int f = k * 64 + 2 * (int)lane;      // two columns per lane
+    if (f < ac.Dp) {
+      reinterpret_cast<uint32_t*>(ws.aev_h + row + f)[0] = 0u;
+      if (ws.aev_l) reinterpret_cast<uint32_t*>(ws.aev_l + row + f)[0] = 0u;
+    }
+  }
 }
 
 template <int ZETA, bool VIR>
@@ -864,6 +940,11 @@ void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st)
   const int grid = (n_in + kWarps - 1) / kWarps;
   if (ac.zeta == 32) k_aev_fwd<32><<<grid, kWarps * 32, sm, st>>>(ws, ac);
   else k_aev_fwd<0><<<grid, kWarps * 32, sm, st>>>(ws, ac);
+}
+
+void launch_aev_fill(const Ws& ws, const AevConst& ac, cudaStream_t st) {
+  if (!ws.row_mask) return;
+  k_aev_fill<<<(ws.row_cap + 7) / 8, 256, 0, st>>>(ws, ac);
 }
 
 void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,

@@ -118,6 +118,10 @@ struct nnp_handle {
   // first layer in one kernel (off by default)
   bool fused_aev_l1 = false;
   bool last_aev_stored = true;   // the last call wrote AEV rows to the arena
+  // tensor-core paths: AEV rows written only in their live 64-column slices, the
+  // first and last layer GEMMs restricted to them (exact: the rest is zero)
+  bool sparse_rows = true;
+  bool last_sparse = false;      // the last call ran with sparse rows
   // persistent neighbour lists with a Verlet skin (0: rebuilt on every call)
   float skin = 0.f;
   bool lists_valid = false;   // the lists in the arena belong to list_sig's batch layout
@@ -382,6 +386,10 @@ size_t carve(nnp_handle* h, char* base) {
   mb.aev_l = split ? c.take<char>(rows * Dp * 2) : nullptr;
   ws.aev_h = static_cast<uint16_t*>(mb.aev_h);
   ws.aev_l = static_cast<uint16_t*>(mb.aev_l);
+  // tensor-core paths: rows written only in their live slices (the first layer
+  // reads a tile's live slices, the last backward layer computes only those)
+  ws.row_mask = tc ? c.take<uint32_t>(rows) : nullptr;
+  ws.tile_mask = tc ? c.take<uint32_t>(rows / kRowTile + 1) : nullptr;
   return align_up(c.off, 256);
 }
 
@@ -567,12 +575,17 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     const bool fuse_l1 = h->fused_aev_l1 && m.net == kNetBf16 &&
                          aev_l1_supported(ws, ac, m.md.E, m.md.h1);
     h->last_aev_stored = !fuse_l1;
+    // sparse rows where the networks run on the tensor cores (ws.row_mask set)
+    Ws wa = ws;
+    if (!h->sparse_rows || fuse_l1) { wa.row_mask = nullptr; wa.tile_mask = nullptr; }
+    h->last_sparse = wa.row_mask != nullptr;
     if (fuse_l1) {
       StageTimer t(h, st, 14);
       launch_aev_l1(ws, ac, m.mw.W1cat_h, m.mw.b1cat, h->mb.H1, m.md.h1, m.alpha, st);
     } else {
       StageTimer t(h, st, 2);
-      launch_aev_fwd(ws, n_in, ac, st);
+      launch_aev_fwd(wa, n_in, ac, st);
+      if (wa.row_mask) { launch_aev_fill(wa, ac, st); ++launches; }
     }
     if ((rc = chk("aev_fwd"))) return rc;
     launches += 2;
@@ -581,7 +594,7 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     for (int b = 0; b < n_sys; ++b) energy_only &= (sy[b].forces == nullptr && sy[b].virial == nullptr);
     StageHook hook{h, st};
     if (m.net != kNetSimt) {
-      rc = launch_mlp_tc(ws, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, h->tc_state, energy_only,
+      rc = launch_mlp_tc(wa, m.md, m.mw, h->mb, m.alpha, st, &launches, &hook, h->tc_state, energy_only,
                          fuse_l1);
       if (rc) return rc;
     } else {
@@ -681,6 +694,7 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
     put(&h->skin, sizeof(h->skin));
     put(&h->fused_chain, sizeof(h->fused_chain));
     put(&h->fused_aev_l1, sizeof(h->fused_aev_l1));
+    put(&h->sparse_rows, sizeof(h->sparse_rows));
     // the kernels read only the first n_sys descriptors of a chunk
     for (const auto& bp : chunks)
       put(&bp, offsetof(BatchParams, sys) + (size_t)bp.n_sys * sizeof(SysIn));
@@ -1127,7 +1141,10 @@ extern "C" int nnp_force_vjp_batch(nnp_handle* h, int n_sys, const nnp_vjp_syste
   Ws ws = h->ws;
   ws.aev_h = nullptr;
   ws.aev_l = nullptr;
+  ws.row_mask = nullptr;      // the FP32 chain reads whole rows
+  ws.tile_mask = nullptr;
   h->last_aev_fp32 = true;
+  h->last_sparse = false;
   // the force VJP builds its own lists at the cutoffs in the shared buffers:
   // persistent lists of energy calls are rebuilt on the next such call
   struct SkinOff {
@@ -1212,6 +1229,29 @@ extern "C" int64_t nnp_n_weights(const nnp_handle* h) {
 }
 
 int nnp_aev_dim(const nnp_handle* h) { return h ? h->model->ac.D : -1; }
+int nnp_debug_tile_masks(nnp_handle* h, void* stream, uint32_t* out_host, int max_tiles,
+                         int* n_tiles) {
+  g_err.clear();
+  if (!h || !out_host || !n_tiles || max_tiles < 0) return fail(NNP_ERR_ARG, "bad argument");
+  *n_tiles = 0;
+  if (!h->arena || !h->last_sparse) return NNP_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU_TRY(cudaStreamSynchronize(st));
+  int seg = 0;
+  CU_TRY(cudaMemcpy(&seg, h->ws.seg_start + h->model->ac.S, sizeof(int), cudaMemcpyDeviceToHost));
+  const int n = std::min(seg / kRowTile, max_tiles);
+  if (n > 0) CU_TRY(cudaMemcpy(out_host, h->ws.tile_mask, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  *n_tiles = n;
+  return NNP_OK;
+}
+
+int nnp_set_sparse_rows(nnp_handle* h, int enable) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  h->sparse_rows = enable != 0;
+  return NNP_OK;
+}
+
 int nnp_set_fused_aev_l1(nnp_handle* h, int enable) {
   g_err.clear();
   if (!h) return fail(NNP_ERR_ARG, "null handle");
@@ -1317,8 +1357,10 @@ int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream) {
   const float* src = which == 0 ? h->ws.aev : h->ws.dEdG;
   const uint16_t* src_h = planes ? h->ws.aev_h : nullptr;
   const uint16_t* src_l = planes ? h->ws.aev_l : nullptr;
-  launch_gather_rows(h->ws, h->last_n_in, src, src_h, src_l, h->model->ac.Dp, h->model->ac.D, out,
-                     static_cast<cudaStream_t>(stream));
+  Ws gw = h->ws;
+  if (!h->last_sparse) gw.row_mask = nullptr;   // the last call wrote whole rows
+  launch_gather_rows(gw, h->last_n_in, src, src_h, src_l, h->model->ac.Dp, h->model->ac.D, out,
+                     which == 1, static_cast<cudaStream_t>(stream));
   CU_TRY(cudaGetLastError());
   return NNP_OK;
 }
@@ -1414,6 +1456,8 @@ size_t noalloc_carve(const Model& m, int n_atoms, char* base, Ws* ws, MlpBufs* m
   ws->pos_sys = c.take<int>(n);
   ws->pos_cell = c.take<int>(n);
   ws->slot_pos = nullptr;
+  ws->row_mask = nullptr;
+  ws->tile_mask = nullptr;
   ws->nb_cnt = c.take<uint16_t>(n * 16);
   ws->nb_r = c.take<int>(n * kNoAllocCapR);
   ws->nb_a = c.take<int>(n * kNoAllocCapA);

@@ -71,7 +71,21 @@ struct TcArgs {
   const int* seg_start;
   int S;
   int* status;
+  // sparse AEV rows (null: dense): the live 64-column slices of each 128-row
+  // tile; the first layer reads only those K slices, the last backward layer
+  // skips the N tiles with none of them
+  const uint32_t* kmask;
+  const uint32_t* nmask;
 };
+
+// which N tile of a row tile the last backward layer computes (all without nmask)
+__device__ __forceinline__ bool ntile_live(const TcArgs& g, int m0, int n0) {
+  if (!g.nmask) return true;
+  const uint32_t m = g.nmask[m0 >> 7];
+  const int a = n0 >> 6, b = (n0 + g.n_tile - 1) >> 6;
+  const uint32_t span = (b - a >= 31) ? ~0u : ((2u << (b - a)) - 1u);
+  return ((m >> a) & span) != 0u;
+}
 
 template <int EPI, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -130,8 +144,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       bool ok = true;
       for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
         const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.n_tile, g.seg_start, g.S);
+        if (!ntile_live(g, tl.m0, tl.n0)) continue;
+        const uint32_t km = g.kmask ? g.kmask[tl.m0 >> 7] : ~0u;
         const int a_c1 = tl.e * g.a_c1_per_e, b_c2 = tl.e * g.b_c2_per_e + tl.s;
-        for (int kb = 0; kb < g.n_k; ++kb, ++it) {
+        for (int kb = 0; kb < g.n_k; ++kb) {
+          if (!((km >> kb) & 1u)) continue;   // an all-zero K slice of the tile
           const int st = it % kStages;
           const unsigned round = it / kStages;
           if (it >= kStages && !mbar_wait(&empty_bar[st], (round - 1) & 1, abort_flag)) { ok = false; break; }
@@ -144,6 +161,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
             tma_load_3d(sa + a_bytes, &ta2, &full_bar[st], kb * kBK, a_c1, tl.m0);
             tma_load_3d(sb + b_bytes, &tb2, &full_bar[st], kb * kBK, tl.n0, b_c2);
           }
+          ++it;   // copies issued so far
         }
       }
       // every issued copy has landed before the CTA may exit
@@ -156,14 +174,20 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       // ---- MMA issuer
       int it = 0, j = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < T && ok; t += gridDim.x, ++j) {
+      for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
+        const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.n_tile, g.seg_start, g.S);
+        if (!ntile_live(g, tl.m0, tl.n0)) continue;
+        const uint32_t km = g.kmask ? g.kmask[tl.m0 >> 7] : ~0u;
         const int ab = j & 1;
         if (j >= 2 && !mbar_wait(&tempty_bar[ab], ((j >> 1) - 1) & 1, abort_flag)) break;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(ab * g.tmem_cols);
-        for (int kb = 0; kb < g.n_k; ++kb, ++it) {
+        bool first_k = true;
+        for (int kb = 0; kb < g.n_k; ++kb) {
+          if (!((km >> kb) & 1u)) continue;
           const int st = it % kStages;
           if (!mbar_wait(&full_bar[st], (it / kStages) & 1, abort_flag)) { ok = false; break; }
+          ++it;
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + st * stage_bytes);
           const uint32_t sb = sa + kParts * a_bytes;
@@ -171,7 +195,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {
             umma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), g.idesc,
-                      (kb > 0 || kk > 0) ? 1u : 0u);
+                      (!first_k || kk > 0) ? 1u : 0u);
             if (SPLIT) {
               const uint64_t adl = sw128_desc(sa + a_bytes), bdl = sw128_desc(sb + b_bytes);
               umma_bf16(d, adl + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), g.idesc, 1u);
@@ -179,8 +203,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
             }
           }
           umma_commit(&empty_bar[st]);
+          first_k = false;
         }
         if (ok) umma_commit(&tfull_bar[ab]);
+        ++j;
       }
       umma_commit(&done_bar);   // arrives when every MMA issued above has completed
       mbar_drain(&done_bar, 0);
@@ -192,9 +218,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     const float alpha = g.alpha, inv_alpha = 1.f / g.alpha;
     int j = 0;
     constexpr int kMaxChunks = 256 / 32;   // 16-column chunks of one warp per tile
-    for (int t = blockIdx.x; t < T; t += gridDim.x, ++j) {
-      const int ab = j & 1;
+    for (int t = blockIdx.x; t < T; t += gridDim.x) {
       const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.n_tile, g.seg_start, g.S);
+      if (!ntile_live(g, tl.m0, tl.n0)) continue;
+      const int ab = j & 1;
       const int m = tl.m0 + q * 32 + lane;
       // the backward's stored activations do not depend on the MMAs: their loads
       // are issued before the wait for the accumulator
@@ -329,6 +356,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar[ab]);
+      ++j;
     }
   }
   tc_fence_before();
@@ -559,6 +587,8 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
   // fused chain: plan 0 (L1), the chain (L2, L3, B3, B2), plan 5 (B1)
   const bool chain = s->chain && s->use_chain;
   const size_t n_plans = energy_only ? 3 : s->plans.size();
+  // sparse AEV rows of this call (the AEV kernel wrote the tile masks)
+  const uint32_t* tmask = (ws.row_mask && !skip_l1) ? ws.tile_mask : nullptr;
   for (size_t i = 0; i < n_plans; ++i) {
     if (i == 0 && skip_l1) continue;   // the first layer ran with the AEV kernel
     if (chain && i >= 1 && i <= 4) {
@@ -575,11 +605,23 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
     a.seg_start = ws.seg_start;
     a.S = md.S;
     a.status = ws.status;
+    a.kmask = (i == 0) ? tmask : nullptr;                       // L1: live K slices
+    a.nmask = (i == s->plans.size() - 1) ? tmask : nullptr;     // B1: live N tiles
     if (hook) hook->begin(p.stage_id);
     // the two epilogue warps of a row add their halves of the output dot product
     if (a.epi == kEpiCeluDot) cudaMemsetAsync(a.e_row, 0, sizeof(float) * (size_t)md.E * a.e_row_net, st);
+    // a masked layer skips N tiles by their index within a row tile; with a grid
+    // that is a multiple of the N tiles per row tile every CTA would keep one
+    // index (and the CTAs of the skipped ones would idle): take a grid coprime
+    // with that count
+    dim3 grid = p.grid;
+    if (a.nmask) {
+      const int ntn = (a.N + a.n_tile - 1) / a.n_tile;
+      auto gcd = [](int x, int y) { while (y) { const int t = x % y; x = y; y = t; } return x; };
+      while (grid.x > 1 && ntn > 1 && gcd((int)grid.x, ntn) != 1) --grid.x;
+    }
 #define NNP_TC_LAUNCH(EPI_, SPLIT_) \
-  k_gemm_tc<EPI_, SPLIT_><<<p.grid, kThreads, p.smem, st>>>(p.ta, p.tb, p.ta2, p.tb2, a)
+  k_gemm_tc<EPI_, SPLIT_><<<grid, kThreads, p.smem, st>>>(p.ta, p.tb, p.ta2, p.tb2, a)
     if (s->split) {
       switch (a.epi) {
         case kEpiCelu: NNP_TC_LAUNCH(kEpiCelu, true); break;

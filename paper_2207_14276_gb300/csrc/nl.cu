@@ -48,6 +48,9 @@ __device__ __forceinline__ int find_sys(const BatchParams& bp, int idx) {
 __device__ __forceinline__ void init_body(const Ws& ws, const BatchParams& bp, int zero_all,
                                           int n_in, int tid, int stride) {
   const bool rebuild = lists_rebuild(ws);
+  // the AEV kernel ORs this call's live slices into the tile masks
+  if (zero_all && ws.tile_mask)
+    for (int i = tid; i <= ws.row_cap / 128; i += stride) ws.tile_mask[i] = 0u;
   if (!rebuild) {
     // persistent lists: the grids and counts of the last build stay; only this
     // call's pointers are new, and the forces start again from zero

@@ -114,6 +114,11 @@ struct Ws {
   float* aev;           // [row_cap][Dp]
   uint16_t* aev_h;      // [row_cap][Dp] BF16 copy (bit patterns) for the tensor-core path, or null
   uint16_t* aev_l;      // [row_cap][Dp] split path: bf16(G - bf16(G)), or null
+  // tensor-core paths: 64-column slices of the AEV rows that hold a nonzero
+  // block (bit k = columns 64k .. 64k+63; bit 0 always set), per row and OR-ed
+  // over each 128-row tile; null: every row is written in full
+  uint32_t* row_mask;   // [row_cap]
+  uint32_t* tile_mask;  // [row_cap / 128 + 1]
   float* dEdG;          // [row_cap][Dp]
   float* atom_e;        // [row_cap] per-row energy (mean over the ensemble, incl. shift)
   float4* f_pos;        // [n_in] forces on packed atoms
@@ -149,6 +154,9 @@ void launch_front(const Ws& ws, const BatchParams& bp, const AevConst& ac, int n
                   cudaStream_t st);
 // ---- aev.cu
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st);
+// sparse rows (ws.row_mask set): zero the slices of each row that its tile reads
+// (tile mask) but the row itself left unwritten
+void launch_aev_fill(const Ws& ws, const AevConst& ac, cudaStream_t st);
 // AEV of 128-row species tiles computed into shared memory and fed straight to
 // the first layer's tensor-core GEMM (BF16, one-network models); false if the
 // tile does not fit or the model is outside what the kernel handles
@@ -165,7 +173,8 @@ size_t aev_bwd_smem(const Ws& ws, int n_pairs = kMaxSpecies * (kMaxSpecies + 1) 
 void launch_finalize_e(const Ws& ws, int n_in, const float* e_row, int E, int e_row_net,
                        const double* ebias, cudaStream_t st);
 void launch_gather_rows(const Ws& ws, int n_in, const float* rows, const uint16_t* rows_h,
-                        const uint16_t* rows_l, int ld, int D, float* out, cudaStream_t st);
+                        const uint16_t* rows_l, int ld, int D, float* out, int by_tile,
+                        cudaStream_t st);
 void launch_gather_nbrs(const Ws& ws, int n_in, int angular, int cap_out, int* out,
                         cudaStream_t st);
 

@@ -105,6 +105,21 @@ class Potential:
         or as four layer GEMMs."""
         check(lib().nnp_set_fused_chain(self._h, 1 if enable else 0))
 
+    def set_sparse_rows(self, enable):
+        """Tensor-core paths: write and multiply only the live 64-column slices of
+        the AEV rows (default on; the result is the same)."""
+        check(lib().nnp_set_sparse_rows(self._h, 1 if enable else 0))
+
+    def tile_masks(self, max_tiles=1 << 20, stream=None):
+        """Live 64-column slice masks of the last call's 128-row AEV tiles (numpy
+        uint32; empty when the last call wrote whole rows)."""
+        out = np.zeros(max_tiles, dtype=np.uint32)
+        n = ctypes.c_int()
+        check(lib().nnp_debug_tile_masks(self._h, _stream_ptr(stream),
+                                         out.ctypes.data_as(ctypes.c_void_p), max_tiles,
+                                         ctypes.byref(n)))
+        return out[:n.value]
+
     def set_fused_aev_l1(self, enable):
         """BF16 one-network models: compute the AEV on chip and feed it to the first
         layer in the same kernel (the AEV never goes to HBM)."""

@@ -95,10 +95,19 @@ def test_gas24_energy_forces_aev_neighbours(torch_cuda):
     s = systems[0]
     check_system(pot, orc, s)
     compare_neighbours(pot, s, pot.spec)
-    # dE/dG (the network gradient) elementwise
-    ref = orc.energy_forces(s.coords, s.species, want_dEdG=True)["dEdG"]
+    # dE/dG (the network gradient) elementwise, on the 64-column slices of each
+    # row that hold a nonzero AEV element: the columns the forces read (with
+    # sparse rows the library computes no others; dE/dG of an all-zero block
+    # multiplies dG/dr = 0)
+    r = orc.energy_forces(s.coords, s.species, want_aev=True, want_dEdG=True)
+    ref, G = r["dEdG"], r["aev"]
     g = pot.debug_rows(1, s.n_atoms).cpu().numpy()
-    np.testing.assert_allclose(g, ref, rtol=1e-4, atol=1e-7)
+    D = G.shape[1]
+    live = np.zeros_like(G, dtype=bool)
+    for k in range(0, D, 64):
+        live[:, k:k + 64] = np.any(G[:, k:k + 64] != 0.0, axis=1)[:, None]
+    assert live.any(axis=1).all()
+    np.testing.assert_allclose(g[live], ref[live], rtol=1e-4, atol=1e-7)
 
 
 def test_dense_box_neighbourhood_beyond_the_stage(torch_cuda):
@@ -417,3 +426,46 @@ def test_split_path_batch_of_small_molecules(torch_cuda, kind):
         assert abs(float(o["energy"].cpu()[0]) - ref["energy"]) <= E_TOL
         rms, _ = force_errors(o["forces"].cpu().numpy(), ref["forces"])
         assert rms <= 1e-4 * np.sqrt(np.mean(ref["forces"] ** 2)) + 1e-7
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("kind", ["ani4", "ani7x8"])
+def test_sparse_rows_equal_dense_rows(torch_cuda, precision, kind):
+    """AEV rows written only in their live slices, the first layer over the tile's
+    live K slices and the last backward layer over its live N tiles, against
+    whole rows, on a batch mixing water-like tiles (few live slices) with solute
+    and gas tiles (many).  The skipped products are exact zeros, but the tensor
+    cores' FP32 accumulation does not add an all-zero slice as an exact no-op,
+    so the two differ in the last bits of the first layer: by the FP32 bar on
+    the split path (energy 1e-5 relative, forces 1e-4 of their RMS), and by
+    BF16 rounding flips downstream on the BF16 path (1e-3 of sum_i |E_i|, 2e-3
+    of the force RMS).  The AEV rows read back equal the oracle's."""
+    torch = torch_cuda
+    pot, orc = make(kind, precision=precision)
+    if kind == "ani4":
+        systems = [synth.water_box(300, 20.5, 7, seed=41)] + list(synth.workload("molecules64")[0][:5])
+    else:
+        systems = [synth.solvated_solute(300, 60, 22.0, seed=6)]
+    d = [to_cuda(s) for s in systems]
+    res = {}
+    for sparse in (False, True):
+        pot.set_sparse_rows(sparse)
+        outs = pot.energy_forces_batch(d, atom_energies=True)
+        res[sparse] = [(float(o["energy"].cpu()[0]), o["forces"].cpu().numpy().astype(np.float64),
+                        o["atom_energies"].cpu().numpy().astype(np.float64)) for o in outs]
+    for (e1, f1, _), (e0, f0, a0) in zip(res[True], res[False]):
+        f_rms = float(np.sqrt(np.mean(f0 ** 2))) + 1e-12
+        d_rms = float(np.sqrt(np.mean((f1 - f0) ** 2)))
+        if precision == "fp32":
+            assert abs(e1 - e0) <= 1e-5 * (abs(e0) + 1.0)
+            assert d_rms <= 1e-4 * f_rms
+        else:
+            assert abs(e1 - e0) <= 1e-3 * float(np.abs(a0).sum()) + 1e-6
+            assert d_rms <= 2e-3 * f_rms
+    # the AEV rows of the last system, sparse, against the oracle
+    s = systems[-1]
+    pot.energy_forces_batch([d[-1]])
+    G = pot.debug_rows(0, s.n_atoms).cpu().numpy()
+    Gr = orc.energy_forces(s.coords, s.species, s.box, want_aev=True)["aev"]
+    tol = 2e-5 if precision == "fp32" else 5e-3
+    np.testing.assert_allclose(G, Gr, rtol=tol, atol=1e-6)
