@@ -325,8 +325,8 @@ __host__ __device__ constexpr int aev_fwd_warp_f4(int cap_a, int cap_r) {
 // stored, and *mask receives the row's slice mask.
 template <int ZETA, class Out>
 __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int p, float4* stage,
-                                           ListHdr& H, unsigned lane, Out out, bool sparse = false,
-                                           uint32_t* mask = nullptr, const uint8_t* pair_su = nullptr) {
+                                           ListHdr& H, unsigned lane, const uint8_t* pair_su,
+                                           Out out, bool sparse = false, uint32_t* mask = nullptr) {
   __syncwarp();   // the warp's stage and header may still hold its previous centre
   float4* angv = stage;
   float* angf = reinterpret_cast<float*>(angv + ws.cap_a);
@@ -357,6 +357,10 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
   for (int s = 0; s < ac.S; ++s) {
     float acc = 0.f;
     const int o = H.off_r[s], n = H.off_r[s + 1] - o;
+    if (n == 0) {   // no neighbour of this species: a zero block
+      if (lane < 16 && block_in(m, s * kNR, kNR)) out(s * kNR + lane, 0.f);
+      continue;
+    }
     for (int t = half; t < n; t += 2) {
       const float2 q = rad[o + t];
       const float x = q.x - my_shf;
@@ -365,20 +369,34 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
     acc += __shfl_xor_sync(kFull, acc, 16);
     if (lane < 16 && block_in(m, s * kNR, kNR)) out(s * kNR + lane, acc);
   }
-  // ---- angular, Eq. 5
+  // ---- angular, Eq. 5: the blocks of species pairs with a pair j < k, and the
+  // zero blocks of the other pairs where the row is written
   const float ca_ = -ac.eta_a * kLog2e;
-  int pidx = 0;
-  for (int s = 0; s < ac.S; ++s)
-    for (int u = s; u < ac.S; ++u, ++pidx) {
+  uint32_t live[2] = {0u, 0u}, zero[2] = {0u, 0u};
+  for (int h = 0; h * 32 < ac.n_pairs; ++h) {
+    const int q = h * 32 + (int)lane;
+    bool lv = false, zr = false;
+    if (q < ac.n_pairs) {
+      const int sp = pair_su[q] & 15, u = pair_su[q] >> 4;
+      const int cs = H.off_a[sp + 1] - H.off_a[sp], cu = H.off_a[u + 1] - H.off_a[u];
+      lv = sp == u ? cs >= 2 : (cs > 0 && cu > 0);
+      zr = !lv && block_in(m, ac.S * kNR + q * 32, 32);
+    }
+    live[h] = __ballot_sync(kFull, lv);
+    zero[h] = __ballot_sync(kFull, zr);
+  }
+  for (int h = 0; h < 2; ++h)
+    for (uint32_t z = zero[h]; z; z &= z - 1)
+      out(ac.S * kNR + (h * 32 + __ffs(z) - 1) * 32 + lane, 0.f);
+  for (int h = 0; h < 2; ++h)
+    for (uint32_t lv = live[h]; lv; lv &= lv - 1) {
+      const int q = h * 32 + __ffs(lv) - 1;
+      const int s = pair_su[q] & 15, u = pair_su[q] >> 4;
       const int os = H.off_a[s], cs = H.off_a[s + 1] - os;
       const int ou = H.off_a[u], cu = H.off_a[u + 1] - ou;
       const int same = (s == u);
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
-      const int fb = ac.S * kNR + pidx * 32;
-      if (n_tri == 0) {
-        if (block_in(m, fb, 32)) out(fb + lane, 0.f);
-        continue;
-      }
+      const int fb = ac.S * kNR + q * 32;
       const float inv_cu = 1.f / (float)max(cu, 1);
       float acc[32];
 #pragma unroll
@@ -425,10 +443,8 @@ k_aev_fwd(Ws ws, AevConst ac) {
   const unsigned lane = threadIdx.x & 31;
   const int p = blockIdx.x * kWarps + w;
   const bool sparse = ws.row_mask != nullptr;
-  if (sparse) {
-    fill_pair_table(pair_su, ac);
-    __syncthreads();
-  }
+  fill_pair_table(pair_su, ac);
+  __syncthreads();
   if (p >= ws.totals[0]) return;
   const size_t row = (size_t)ws.pos_slot[p] * ac.Dp;
   float* G = ws.aev + row;
@@ -436,7 +452,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
   uint16_t* Gl = ws.aev_l ? ws.aev_l + row : nullptr;
   uint32_t m = 0;
   aev_centre<ZETA>(ws, ac, p, sm4 + (size_t)w * aev_fwd_warp_f4(ws.cap_a, ws.cap_r), hdrs[w], lane,
-                   [&](int f, float v) { put_g(G, Gh, Gl, f, v); }, sparse, &m, pair_su);
+                   pair_su, [&](int f, float v) { put_g(G, Gh, Gl, f, v); }, sparse, &m);
   if (sparse && lane == 0) {
     const int slot = ws.pos_slot[p];
     ws.row_mask[slot] = m;
@@ -467,10 +483,138 @@ __global__ void __launch_bounds__(256) k_aev_fill(Ws ws, AevConst ac) {
   }
 }
 
+// ---- backward pieces shared by the warp-per-centre and CTA-per-centre kernels
+
+// One radial edge (Eq. 4) of centre i: dE/dr_ij from the S*16 radial dE/dG
+// values gs of neighbour j's species; the force on j goes to f_pos[j] at once,
+// the centre's share (and the virial) into the caller's accumulators.
+template <bool VIR>
+__device__ __forceinline__ void radial_edge_bwd(const Ws& ws, const AevConst& ac, const float4& xi,
+                                                const SysDev& d, int j, const float4& xj,
+                                                const float* gs, float inv_rc_r, float* fi,
+                                                float* vir) {
+  const float cr_ = -ac.eta_r * kLog2e;
+  const Geo g = pair_geo(xi, xj, d);
+  float fc, dfc;
+  fcut_both(g.r, ac.rc_r, inv_rc_r, &fc, &dfc);
+  float dEdR = 0.f;
+#pragma unroll
+  for (int r = 0; r < kNR; ++r) {
+    const float x = g.r - ac.shf_r[r];
+    const float e = fast_exp2(cr_ * x * x);
+    dEdR = fmaf(gs[r], e * fmaf(-2.f * ac.eta_r * x, fc, dfc), dEdR);
+  }
+  const float sc = dEdR * rcp_approx(g.r);
+  const float gx = sc * g.dx, gy = sc * g.dy, gz = sc * g.dz;
+  atomicAdd(&ws.f_pos[j], make_float4(-gx, -gy, -gz, 0.f));
+  fi[0] += gx; fi[1] += gy; fi[2] += gz;
+  if (VIR) {
+    vir[0] -= g.dx * gx; vir[1] -= g.dx * gy; vir[2] -= g.dx * gz;
+    vir[3] -= g.dy * gx; vir[4] -= g.dy * gy; vir[5] -= g.dy * gz;
+    vir[6] -= g.dz * gx; vir[7] -= g.dz * gy; vir[8] -= g.dz * gz;
+  }
+}
+
+// Block table of a centre's angular terms, built by one warp: per species pair
+// q, its geometry (os, cs, ou, cu | same << 16) in the species-sorted angular
+// list and the number of its first triplet in a numbering continuous over all
+// blocks (bt_start[n_pairs] = the centre's triplet count).
+__device__ __forceinline__ void build_block_table(const ListHdr& H, const AevConst& ac,
+                                                  unsigned lane, int4* bt_geo, int* bt_start) {
+  const int np = ac.n_pairs;
+  for (int q0 = 0, carry = 0; q0 < np; q0 += 32) {
+    const int q = q0 + lane;
+    int n_tri = 0;
+    if (q < np) {
+      int sp = 0, rem = q;
+      while (rem >= ac.S - sp) { rem -= ac.S - sp; ++sp; }
+      const int u = sp + rem;
+      const int os = H.off_a[sp], cs = H.off_a[sp + 1] - os;
+      const int ou = H.off_a[u], cu = H.off_a[u + 1] - ou;
+      const int same = (sp == u);
+      n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
+      bt_geo[q] = make_int4(os, cs, ou, cu | (same << 16));
+    }
+    int incl = n_tri;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, o);
+      if ((int)lane >= o) incl += v;
+    }
+    if (q < np) bt_start[q] = carry + incl - n_tri;
+    carry += __shfl_sync(kFull, incl, 31);
+    if (q0 + 32 >= np && lane == 0) bt_start[np] = carry;
+  }
+}
+
+// One angular triplet (Eq. 5) of a centre: neighbours j and k (unit vector and
+// R; f_c, f_c', 1/R), the 32 dE/dG values of their species-pair block as
+// [z] float4s of the four radial shells.  Returns dE/d(r_j) and dE/d(r_k)
+// (the force terms on j and k; their negatives act on the centre).
+template <int ZETA>
+__device__ __forceinline__ void triplet_bwd(const AevConst& ac, const float4& vj, const float4& vk,
+                                            const float4& fj4, const float4& fk4,
+                                            const float4* gblk, float3& uj, float3& uk) {
+  const float ca_ = -ac.eta_a * kLog2e;
+  const float m2eta = -2.f * ac.eta_a;
+  const float chat = vj.x * vk.x + vj.y * vk.y + vj.z * vk.z;
+  const float c = ac.cos_scale * chat;
+  const float sn = fmaxf(sin_theta(vj, vk, chat, ac.cos_scale), 1e-6f);
+  const float c_over_s = c * rcp_approx(sn);
+  const float rb = 0.5f * (vj.w + vk.w);
+  // contract the block's dE/dG over the 8 angle sections first:
+  //   F_a = sum_z g[a][z] B_z,  dF_a = sum_z g[a][z] dB_z/dc
+  float F[kNA] = {0.f, 0.f, 0.f, 0.f}, dF[kNA] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int z = 0; z < kNZ; ++z) {
+    const float base = fmaf(sn, ac.sin_z[z], fmaf(c, ac.cos_z[z], 1.f));
+    float B, B1;
+    if constexpr (ZETA == 32) {
+      // base >= 1 + cos(15 pi / 16) > 0: base^31 = base^32 / base
+      const float p2 = base * base, p4 = p2 * p2, p8 = p4 * p4, p16 = p8 * p8;
+      B = p16 * p16;
+      B1 = B * rcp_approx(base);
+    } else {
+      B1 = ipow<0>(base, ac.zeta - 1);
+      B = B1 * base;
+    }
+    const float dB = B1 * fmaf(-ac.sin_z[z], c_over_s, ac.cos_z[z]);
+    const float4 gz = gblk[z];
+    F[0] = fmaf(gz.x, B, F[0]); F[1] = fmaf(gz.y, B, F[1]);
+    F[2] = fmaf(gz.z, B, F[2]); F[3] = fmaf(gz.w, B, F[3]);
+    dF[0] = fmaf(gz.x, dB, dF[0]); dF[1] = fmaf(gz.y, dB, dF[1]);
+    dF[2] = fmaf(gz.z, dB, dF[2]); dF[3] = fmaf(gz.w, dB, dF[3]);
+  }
+  float tc = 0.f, tR = 0.f, tf = 0.f;
+#pragma unroll
+  for (int a = 0; a < kNA; ++a) {
+    const float x = rb - ac.shf_a[a];
+    const float A = fast_exp2(ca_ * x * x);
+    const float AF = A * F[a];
+    tf += AF;
+    tR = fmaf(m2eta * x, AF, tR);
+    tc = fmaf(A, dF[a], tc);
+  }
+  const float fjk = fj4.x * fk4.x;
+  tc *= ac.ang_pre * (float)ac.zeta * fjk;  // dE/dc, c = cos_scale * cos_hat
+  tR *= ac.ang_pre * fjk;                    // dE/dRbar
+  tf *= ac.ang_pre;                          // dE/d(f_j f_k)
+  const float dEdchat = ac.cos_scale * tc;
+  const float sj = dEdchat * fj4.z, sk = dEdchat * fk4.z;
+  const float rj = 0.5f * tR + tf * fj4.y * fk4.x;
+  const float rk = 0.5f * tR + tf * fj4.x * fk4.y;
+  uj = make_float3(sj * (vk.x - chat * vj.x) + rj * vj.x, sj * (vk.y - chat * vj.y) + rj * vj.y,
+                   sj * (vk.z - chat * vj.z) + rj * vj.z);
+  uk = make_float3(sk * (vj.x - chat * vk.x) + rk * vk.x, sk * (vj.y - chat * vk.y) + rk * vk.y,
+                   sk * (vj.z - chat * vk.z) + rk * vk.z);
+}
+
+// Warp per centre, for centres with at most cap_l angular neighbours (the
+// per-warp shared-memory region is sized for cap_l); a centre with more is
+// appended to ws.heavy (count in totals[2]) for k_aev_bwd_heavy and skipped.
 template <int ZETA, bool VIR>
 __global__ void __launch_bounds__(kWarps * 32, 4)
-k_aev_bwd(Ws ws, AevConst ac, int log_r) {
-  constexpr bool want_virial = VIR;
+k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
   extern __shared__ float4 sm4[];
   __shared__ ListHdr hdrs[kWarps];
   const int w = threadIdx.x >> 5;
@@ -478,15 +622,15 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
   const int p = blockIdx.x * kWarps + w;
   if (p >= ws.totals[0]) return;
   const int n_copy = 1 << log_r;
-  float4* angv = sm4 + (size_t)w * aev_bwd_warp_f4(ws.cap_a, ac.n_pairs, n_copy);
-  float4* angf = angv + ws.cap_a;          // fc, dfc
+  float4* angv = sm4 + (size_t)w * aev_bwd_warp_f4(cap_l, ac.n_pairs, n_copy);
+  float4* angf = angv + cap_l;             // fc, dfc
   // dE/du per angular neighbour as three arrays (x, y, z), each [neighbour][copy]:
   // lane l adds into copy l mod n_copy, and lanes adding into consecutive
   // neighbours hit consecutive banks
-  float* accx = reinterpret_cast<float*>(angf + ws.cap_a);
-  float* accy = accx + ws.cap_a * n_copy;
-  float* accz = accy + ws.cap_a * n_copy;
-  float4* past_acc = angf + ws.cap_a + (3 * ws.cap_a * n_copy + 3) / 4;
+  float* accx = reinterpret_cast<float*>(angf + cap_l);
+  float* accy = accx + cap_l * n_copy;
+  float* accz = accy + cap_l * n_copy;
+  float4* past_acc = angf + cap_l + (3 * cap_l * n_copy + 3) / 4;
   float* grad = reinterpret_cast<float*>(past_acc);  // S*16 radial dE/dG
   // dE/dG of up to kGallBlocks angular blocks with triplets, [slot][z][a]
   const int n_gall = min(ac.n_pairs, kGallBlocks);
@@ -499,6 +643,10 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
   const SysDev& d = ws.sys[ws.pos_sys[p]];
   const float* g_row = ws.dEdG + (size_t)ws.pos_slot[p] * ac.Dp;
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
+  if (H.off_a[ac.S] > cap_l) {
+    if (lane == 0) ws.heavy[atomicAdd(ws.totals + 2, 1)] = p;
+    return;
+  }
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
   const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
@@ -536,75 +684,30 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
 #pragma unroll
   for (int k = 0; k < 9; ++k) vir[k] = 0.f;
   // ---- radial edges, one lane per neighbour, numbered continuously over the
-  // species blocks of the list (a lane finds its neighbour's species block)
-  const float cr_ = -ac.eta_r * kLog2e;
+  // species blocks of the list (a lane finds its neighbour's species block);
+  // two neighbours per lane and pass, both gathers issued before either is used
   const int nr_tot = H.off_r[ac.S];
   int sr = 0;
-  // two neighbours per lane and pass, both gathers issued before either is used
-  auto radial_edge = [&](int t, int j, const float4& xj) {
-    while (H.off_r[sr + 1] <= t) ++sr;
-    const float* gs = grad + sr * kNR;
-    {
-      const Geo g = pair_geo(xi, xj, d);
-      float fc, dfc;
-      fcut_both(g.r, ac.rc_r, inv_rc_r, &fc, &dfc);
-      float dEdR = 0.f;
-#pragma unroll
-      for (int r = 0; r < kNR; ++r) {
-        const float x = g.r - ac.shf_r[r];
-        const float e = fast_exp2(cr_ * x * x);
-        dEdR = fmaf(gs[r], e * fmaf(-2.f * ac.eta_r * x, fc, dfc), dEdR);
-      }
-      const float sc = dEdR * rcp_approx(g.r);
-      const float gx = sc * g.dx, gy = sc * g.dy, gz = sc * g.dz;
-      atomicAdd(&ws.f_pos[j], make_float4(-gx, -gy, -gz, 0.f));
-      fi[0] += gx; fi[1] += gy; fi[2] += gz;
-      if (want_virial) {
-        vir[0] -= g.dx * gx; vir[1] -= g.dx * gy; vir[2] -= g.dx * gz;
-        vir[3] -= g.dy * gx; vir[4] -= g.dy * gy; vir[5] -= g.dy * gz;
-        vir[6] -= g.dz * gx; vir[7] -= g.dz * gy; vir[8] -= g.dz * gz;
-      }
-    }
-  };
   for (int t0 = 0; t0 < nr_tot; t0 += 64) {
     const int ta = t0 + (int)lane, tb = ta + 32;
     const int ja = ta < nr_tot ? lr[ta] : -1;
     const int jb = tb < nr_tot ? lr[tb] : -1;
     const float4 xa = ja >= 0 ? ws.xyzq[ja] : xi;
     const float4 xb = jb >= 0 ? ws.xyzq[jb] : xi;
-    if (ja >= 0) radial_edge(ta, ja, xa);
-    if (jb >= 0) radial_edge(tb, jb, xb);
+    if (ja >= 0) {
+      while (H.off_r[sr + 1] <= ta) ++sr;
+      radial_edge_bwd<VIR>(ws, ac, xi, d, ja, xa, grad + sr * kNR, inv_rc_r, fi, vir);
+    }
+    if (jb >= 0) {
+      while (H.off_r[sr + 1] <= tb) ++sr;
+      radial_edge_bwd<VIR>(ws, ac, xi, d, jb, xb, grad + sr * kNR, inv_rc_r, fi, vir);
+    }
   }
   // ---- angular triplets, one lane per (j, k) pair, numbered continuously over
   // all species-pair blocks of the centre so that a warp's 32 lanes stay busy
   // across block boundaries
-  const float ca_ = -ac.eta_a * kLog2e;
-  const float m2eta = -2.f * ac.eta_a;
   const int np = ac.n_pairs;
-  // block table: geometry (os, cs, ou, cu | same << 16) and first triplet number
-  for (int q0 = 0, carry = 0; q0 < np; q0 += 32) {
-    const int q = q0 + lane;
-    int n_tri = 0;
-    if (q < np) {
-      int sp = 0, rem = q;
-      while (rem >= ac.S - sp) { rem -= ac.S - sp; ++sp; }
-      const int u = sp + rem;
-      const int os = H.off_a[sp], cs = H.off_a[sp + 1] - os;
-      const int ou = H.off_a[u], cu = H.off_a[u + 1] - ou;
-      const int same = (sp == u);
-      n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
-      bt_geo[q] = make_int4(os, cs, ou, cu | (same << 16));
-    }
-    int incl = n_tri;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(kFull, incl, o);
-      if ((int)lane >= o) incl += v;
-    }
-    if (q < np) bt_start[q] = carry + incl - n_tri;
-    carry += __shfl_sync(kFull, incl, 31);
-    if (q0 + 32 >= np && lane == 0) bt_start[np] = carry;
-  }
+  build_block_table(H, ac, lane, bt_geo, bt_start);
   __syncwarp();   // the block table is complete
   // the dE/dG blocks with triplets, in block order; a group of up to n_gall of
   // them at a time is staged (its 32 values, index 8a + z, transposed to [z][a]
@@ -637,8 +740,7 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
       const int cnt = min(n_gall, n_live - first);
       // the group's dE/dG loads are all issued before the shared-memory stores,
       // eight blocks at a time, so that their latencies overlap
-#pragma unroll
-      for (int k0 = 0; k0 < kGallBlocks; k0 += 8) {
+      for (int k0 = 0; k0 < cnt; k0 += 8) {
         float gv[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -674,65 +776,17 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
       }
       int j, k;
       decode_pair_diag(t - bt_start[bl], same, cs, cu, inv_cs, inv_cu, &j, &k);
-      {
-          const int tj = os + j, tk = ou + k;
-          const float4 vj = angv[tj], vk = angv[tk];
-          const float4 fj4 = angf[tj], fk4 = angf[tk];
-          const float chat = vj.x * vk.x + vj.y * vk.y + vj.z * vk.z;
-          const float c = ac.cos_scale * chat;
-          const float sn = fmaxf(sin_theta(vj, vk, chat, ac.cos_scale), 1e-6f);
-          const float c_over_s = c * rcp_approx(sn);
-          const float rb = 0.5f * (vj.w + vk.w);
-          // contract the block's dE/dG over the 8 angle sections first:
-          //   F_a = sum_z g[a][z] B_z,  dF_a = sum_z g[a][z] dB_z/dc
-          float F[kNA] = {0.f, 0.f, 0.f, 0.f}, dF[kNA] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-          for (int z = 0; z < kNZ; ++z) {
-            const float base = fmaf(sn, ac.sin_z[z], fmaf(c, ac.cos_z[z], 1.f));
-            float B, B1;
-            if constexpr (ZETA == 32) {
-              // base >= 1 + cos(15 pi / 16) > 0: base^31 = base^32 / base
-              const float p2 = base * base, p4 = p2 * p2, p8 = p4 * p4, p16 = p8 * p8;
-              B = p16 * p16;
-              B1 = B * rcp_approx(base);
-            } else {
-              B1 = ipow<0>(base, ac.zeta - 1);
-              B = B1 * base;
-            }
-            const float dB = B1 * fmaf(-ac.sin_z[z], c_over_s, ac.cos_z[z]);
-            const float4 gz = gblk[z];
-            F[0] = fmaf(gz.x, B, F[0]); F[1] = fmaf(gz.y, B, F[1]);
-            F[2] = fmaf(gz.z, B, F[2]); F[3] = fmaf(gz.w, B, F[3]);
-            dF[0] = fmaf(gz.x, dB, dF[0]); dF[1] = fmaf(gz.y, dB, dF[1]);
-            dF[2] = fmaf(gz.z, dB, dF[2]); dF[3] = fmaf(gz.w, dB, dF[3]);
-          }
-          float tc = 0.f, tR = 0.f, tf = 0.f;
-#pragma unroll
-          for (int a = 0; a < kNA; ++a) {
-            const float x = rb - ac.shf_a[a];
-            const float A = fast_exp2(ca_ * x * x);
-            const float AF = A * F[a];
-            tf += AF;
-            tR = fmaf(m2eta * x, AF, tR);
-            tc = fmaf(A, dF[a], tc);
-          }
-          const float fjk = fj4.x * fk4.x;
-          tc *= ac.ang_pre * (float)ac.zeta * fjk;  // dE/dc, c = cos_scale * cos_hat
-          tR *= ac.ang_pre * fjk;                    // dE/dRbar
-          tf *= ac.ang_pre;                          // dE/d(f_j f_k)
-          const float dEdchat = ac.cos_scale * tc;
-          const float sj = dEdchat * fj4.z, sk = dEdchat * fk4.z;
-          const float rj = 0.5f * tR + tf * fj4.y * fk4.x;
-          const float rk = 0.5f * tR + tf * fj4.x * fk4.y;
-          const int cp = (int)lane & (n_copy - 1);
-          const int aj = (tj << log_r) | cp, ak = (tk << log_r) | cp;
-          atomicAdd(accx + aj, sj * (vk.x - chat * vj.x) + rj * vj.x);
-          atomicAdd(accy + aj, sj * (vk.y - chat * vj.y) + rj * vj.y);
-          atomicAdd(accz + aj, sj * (vk.z - chat * vj.z) + rj * vj.z);
-          atomicAdd(accx + ak, sk * (vj.x - chat * vk.x) + rk * vk.x);
-          atomicAdd(accy + ak, sk * (vj.y - chat * vk.y) + rk * vk.y);
-          atomicAdd(accz + ak, sk * (vj.z - chat * vk.z) + rk * vk.z);
-      }
+      const int tj = os + j, tk = ou + k;
+      float3 uj, uk;
+      triplet_bwd<ZETA>(ac, angv[tj], angv[tk], angf[tj], angf[tk], gblk, uj, uk);
+      const int cp = (int)lane & (n_copy - 1);
+      const int aj = (tj << log_r) | cp, ak = (tk << log_r) | cp;
+      atomicAdd(accx + aj, uj.x);
+      atomicAdd(accy + aj, uj.y);
+      atomicAdd(accz + aj, uj.z);
+      atomicAdd(accx + ak, uk.x);
+      atomicAdd(accy + ak, uk.y);
+      atomicAdd(accz + ak, uk.z);
     }
     __syncwarp();   // the group's slots are refilled by the next group
   }
@@ -748,7 +802,7 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
     const float4 v = angv[t];
     atomicAdd(&ws.f_pos[__float_as_int(angf[t].w)], make_float4(-a.x, -a.y, -a.z, 0.f));
     fi[0] += a.x; fi[1] += a.y; fi[2] += a.z;
-    if (want_virial) {
+    if (VIR) {
       const float ux = v.x * v.w, uy = v.y * v.w, uz = v.z * v.w;
       vir[0] -= ux * a.x; vir[1] -= ux * a.y; vir[2] -= ux * a.z;
       vir[3] -= uy * a.x; vir[4] -= uy * a.y; vir[5] -= uy * a.z;
@@ -762,12 +816,169 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r) {
     fi[2] += __shfl_xor_sync(kFull, fi[2], o);
   }
   if (lane == 0) atomicAdd(&ws.f_pos[p], make_float4(fi[0], fi[1], fi[2], 0.f));
-  if (want_virial && d.in.virial) {
+  if (VIR && d.in.virial) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       float v = vir[k];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
       if (lane == 0) atomicAdd(d.in.virial + k, (double)v);
+    }
+  }
+}
+
+// CTA per centre, for the centres k_aev_bwd handed on (more than its cap_l
+// angular neighbours: a dense solute core can have a hundred, i.e. thousands of
+// triplets).  The CTA's eight warps share the centre's staged neighbours and all
+// its angular dE/dG blocks and split its radial edges and triplets; every warp
+// adds into its own copies of the per-neighbour accumulators (lane l into copy
+// (l mod n_lane) of its warp's n_lane), summed once at the end.  Persistent:
+// CTAs stride over the ws.heavy list.
+constexpr int kHeavyThreads = 256;
+
+__host__ __device__ constexpr size_t aev_bwd_heavy_smem(int cap_a, int n_pairs, int n_lane) {
+  return (size_t)2 * cap_a * 16 +                        // angv, angf
+         (size_t)3 * cap_a * (kHeavyThreads / 32) * n_lane * 4 +  // accumulators
+         (size_t)kMaxSpecies * kNR * 4 +                  // radial dE/dG
+         (size_t)n_pairs * 32 * 4 +                       // angular dE/dG, [q][z][a]
+         (size_t)n_pairs * 16 + (size_t)(n_pairs + 1) * 4 + 16;   // block table
+}
+
+template <int ZETA, bool VIR>
+__global__ void __launch_bounds__(kHeavyThreads)
+k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
+  extern __shared__ float4 smh[];
+  __shared__ ListHdr H;
+  __shared__ float red[kHeavyThreads / 32][12];
+  const int n_lane = 1 << log_n;
+  const int n_acc = (kHeavyThreads / 32) << log_n;      // copies per neighbour
+  const int cap = ws.cap_a;
+  const int tid = threadIdx.x, w = tid >> 5;
+  const unsigned lane = tid & 31;
+  float4* angv = smh;
+  float4* angf = angv + cap;
+  float* accx = reinterpret_cast<float*>(angf + cap);   // [neighbour][copy]
+  float* accy = accx + (size_t)cap * n_acc;
+  float* accz = accy + (size_t)cap * n_acc;
+  float* grad = accz + (size_t)cap * n_acc;
+  float* gf = grad + kMaxSpecies * kNR;
+  const float4* gall = reinterpret_cast<const float4*>(gf);
+  int4* bt_geo = reinterpret_cast<int4*>(gf + ac.n_pairs * 32);
+  int* bt_start = reinterpret_cast<int*>(bt_geo + ac.n_pairs);
+  const int np = ac.n_pairs;
+  const int n_heavy = ws.totals[2];
+  const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
+  for (int h = blockIdx.x; h < n_heavy; h += gridDim.x) {
+    const int p = ws.heavy[h];
+    __syncthreads();   // the previous centre's shared data are no longer read
+    if (w == 0) load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
+    __syncthreads();
+    const float4 xi = ws.xyzq[p];
+    const SysDev& d = ws.sys[ws.pos_sys[p]];
+    const float* g_row = ws.dEdG + (size_t)ws.pos_slot[p] * ac.Dp;
+    const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
+    const int* la = ws.nb_a + (size_t)p * ws.cap_a;
+    const int na = H.off_a[ac.S], nr = H.off_r[ac.S];
+    for (int t = tid; t < na; t += kHeavyThreads) {
+      const int j = la[t];
+      const Geo g = pair_geo(xi, ws.xyzq[j], d);
+      const float inv = rcp_approx(g.r);
+      angv[t] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
+      float fc, dfc;
+      fcut_both(g.r, ac.rc_a, inv_rc_a, &fc, &dfc);
+      angf[t] = make_float4(fc, dfc, inv, __int_as_float(j));
+    }
+    for (int i = tid; i < na * n_acc; i += kHeavyThreads) {
+      accx[i] = 0.f;
+      accy[i] = 0.f;
+      accz[i] = 0.f;
+    }
+    for (int f = tid; f < ac.S * kNR; f += kHeavyThreads) grad[f] = g_row[f];
+    if (w == 0) build_block_table(H, ac, lane, bt_geo, bt_start);
+    __syncthreads();
+    // every block with triplets: its 32 dE/dG values (index 8a + z) as [z][a]
+    const float* ga = g_row + ac.S * kNR;
+    for (int i = tid; i < np * 32; i += kHeavyThreads) {
+      const int q = i >> 5, l = i & 31;
+      if (bt_start[q + 1] > bt_start[q]) gf[q * 32 + (l & 7) * 4 + (l >> 3)] = ga[i];
+    }
+    __syncthreads();
+    float fi[3] = {0.f, 0.f, 0.f};
+    float vir[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) vir[k] = 0.f;
+    int sr = 0;
+    for (int t = tid; t < nr; t += kHeavyThreads) {
+      while (H.off_r[sr + 1] <= t) ++sr;
+      const int j = lr[t];
+      radial_edge_bwd<VIR>(ws, ac, xi, d, j, ws.xyzq[j], grad + sr * kNR, inv_rc_r, fi, vir);
+    }
+    const int n_tri = bt_start[np];
+    const int cp = w * n_lane + ((int)lane & (n_lane - 1));
+    int bl = 0, cur = -1;
+    int os = 0, cs = 0, ou = 0, cu = 0, same = 0;
+    float inv_cs = 0.f, inv_cu = 0.f;
+    for (int t = tid; t < n_tri; t += kHeavyThreads) {
+      while (bt_start[bl + 1] <= t) ++bl;
+      if (bl != cur) {
+        cur = bl;
+        const int4 g4 = bt_geo[bl];
+        os = g4.x; cs = g4.y; ou = g4.z; cu = g4.w & 0xffff; same = (g4.w >> 16) & 1;
+        inv_cs = 1.f / (float)max(cs, 1);
+        inv_cu = 1.f / (float)max(cu, 1);
+      }
+      int j, k;
+      decode_pair_diag(t - bt_start[bl], same, cs, cu, inv_cs, inv_cu, &j, &k);
+      const int tj = os + j, tk = ou + k;
+      float3 uj, uk;
+      triplet_bwd<ZETA>(ac, angv[tj], angv[tk], angf[tj], angf[tk], gall + bl * 8, uj, uk);
+      const int aj = tj * n_acc + cp, ak = tk * n_acc + cp;
+      atomicAdd(accx + aj, uj.x);
+      atomicAdd(accy + aj, uj.y);
+      atomicAdd(accz + aj, uj.z);
+      atomicAdd(accx + ak, uk.x);
+      atomicAdd(accy + ak, uk.y);
+      atomicAdd(accz + ak, uk.z);
+    }
+    __syncthreads();
+    for (int t = tid; t < na; t += kHeavyThreads) {
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int c = 0; c < n_acc; ++c) {
+        const int i = t * n_acc + c;
+        a.x += accx[i];
+        a.y += accy[i];
+        a.z += accz[i];
+      }
+      const float4 v = angv[t];
+      atomicAdd(&ws.f_pos[__float_as_int(angf[t].w)], make_float4(-a.x, -a.y, -a.z, 0.f));
+      fi[0] += a.x; fi[1] += a.y; fi[2] += a.z;
+      if (VIR) {
+        const float ux = v.x * v.w, uy = v.y * v.w, uz = v.z * v.w;
+        vir[0] -= ux * a.x; vir[1] -= ux * a.y; vir[2] -= ux * a.z;
+        vir[3] -= uy * a.x; vir[4] -= uy * a.y; vir[5] -= uy * a.z;
+        vir[6] -= uz * a.x; vir[7] -= uz * a.y; vir[8] -= uz * a.z;
+      }
+    }
+    // the centre's force and the virial: warp sums, then warp 0 over the warps
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      fi[0] += __shfl_xor_sync(kFull, fi[0], o);
+      fi[1] += __shfl_xor_sync(kFull, fi[1], o);
+      fi[2] += __shfl_xor_sync(kFull, fi[2], o);
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+        if (VIR) vir[k] += __shfl_xor_sync(kFull, vir[k], o);
+    }
+    if (lane == 0) {
+      red[w][0] = fi[0]; red[w][1] = fi[1]; red[w][2] = fi[2];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) red[w][3 + k] = VIR ? vir[k] : 0.f;
+    }
+    __syncthreads();
+    if (tid < 12) {
+      float v = 0.f;
+      for (int k = 0; k < kHeavyThreads / 32; ++k) v += red[k][tid];
+      if (tid < 3) atomicAdd(reinterpret_cast<float*>(&ws.f_pos[p]) + tid, v);
+      else if (VIR && d.in.virial) atomicAdd(d.in.virial + (tid - 3), (double)v);
     }
   }
 }
@@ -809,6 +1020,7 @@ k_aev_l1(const __grid_constant__ CUtensorMap tw1, Ws ws, AevConst ac, AevL1Args 
   __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
+  __shared__ uint8_t pair_su[kMaxSpecies * (kMaxSpecies + 1) / 2];
   const int w = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31;
   const int S = ac.S;
@@ -835,6 +1047,7 @@ k_aev_l1(const __grid_constant__ CUtensorMap tw1, Ws ws, AevConst ac, AevL1Args 
                      smem_u32(&tmem_base_sh)), "r"(256u) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  fill_pair_table(pair_su, ac);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -847,7 +1060,7 @@ k_aev_l1(const __grid_constant__ CUtensorMap tw1, Ws ws, AevConst ac, AevL1Args 
   for (int r = w; r < kTileM; r += kL1Warps) {
     const int slot = m0 + r;
     if (slot < seg_end) {
-      aev_centre<ZETA>(ws, ac, ws.slot_pos[slot], stage, hdrs[w], lane,
+      aev_centre<ZETA>(ws, ac, ws.slot_pos[slot], stage, hdrs[w], lane, pair_su,
                        [&](int f, float v) { put_tile(tile, r, f, v); });
     } else {
       for (int f = (int)lane; f < ac.Dp; f += 32) put_tile(tile, r, f, 0.f);
@@ -929,9 +1142,26 @@ size_t aev_l1_smem(const Ws& ws, const AevConst& ac, int h1) {
 size_t aev_fwd_smem(const Ws& ws) {
   return (size_t)kWarps * aev_fwd_warp_f4(ws.cap_a, ws.cap_r) * sizeof(float4);
 }
+// angular neighbours the warp-per-centre backward handles; centres with more go
+// to the CTA-per-centre kernel
+constexpr int kLightCapA = 48;
+static int light_cap(const Ws& ws) { return std::min(ws.cap_a, kLightCapA); }
+
 size_t aev_bwd_smem(const Ws& ws, int n_pairs) {
-  return (size_t)kWarps * aev_bwd_warp_f4(ws.cap_a, n_pairs, aev_bwd_copies(ws.cap_a, n_pairs)) *
+  const int cap_l = light_cap(ws);
+  return (size_t)kWarps * aev_bwd_warp_f4(cap_l, n_pairs, aev_bwd_copies(cap_l, n_pairs)) *
          sizeof(float4);
+}
+
+// lane copies per warp of the CTA-per-centre kernel's accumulators: as many as
+// keep its shared memory within 96 KiB (two CTAs per SM), at most 4
+static int heavy_log_n(const Ws& ws, int n_pairs) {
+  for (int l = 2; l > 0; --l)
+    if (aev_bwd_heavy_smem(ws.cap_a, n_pairs, 1 << l) <= 96 * 1024) return l;
+  return 0;
+}
+static size_t heavy_smem(const Ws& ws, int n_pairs) {
+  return aev_bwd_heavy_smem(ws.cap_a, n_pairs, 1 << heavy_log_n(ws, n_pairs));
 }
 
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st) {
@@ -950,16 +1180,31 @@ void launch_aev_fill(const Ws& ws, const AevConst& ac, cudaStream_t st) {
 void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
                     cudaStream_t st) {
   if (n_in <= 0) return;
+  const int cap_l = light_cap(ws);
   const size_t sm = aev_bwd_smem(ws, ac.n_pairs);
-  const int copies = aev_bwd_copies(ws.cap_a, ac.n_pairs);
+  const int copies = aev_bwd_copies(cap_l, ac.n_pairs);
   const int log_r = copies == 4 ? 2 : copies == 2 ? 1 : 0;
   const int grid = (n_in + kWarps - 1) / kWarps;
   if (ac.zeta == 32) {
-    if (want_virial) k_aev_bwd<32, true><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r);
-    else k_aev_bwd<32, false><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r);
+    if (want_virial) k_aev_bwd<32, true><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r, cap_l);
+    else k_aev_bwd<32, false><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r, cap_l);
   } else {
-    if (want_virial) k_aev_bwd<0, true><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r);
-    else k_aev_bwd<0, false><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r);
+    if (want_virial) k_aev_bwd<0, true><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r, cap_l);
+    else k_aev_bwd<0, false><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r, cap_l);
+  }
+  if (ws.cap_a <= cap_l) return;   // no centre can have more neighbours than the warps took
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int hgrid = std::max(1, std::min(n_in, 4 * std::max(sms, 1)));
+  const size_t hs = heavy_smem(ws, ac.n_pairs);
+  const int log_n = heavy_log_n(ws, ac.n_pairs);
+  if (ac.zeta == 32) {
+    if (want_virial) k_aev_bwd_heavy<32, true><<<hgrid, kHeavyThreads, hs, st>>>(ws, ac, log_n);
+    else k_aev_bwd_heavy<32, false><<<hgrid, kHeavyThreads, hs, st>>>(ws, ac, log_n);
+  } else {
+    if (want_virial) k_aev_bwd_heavy<0, true><<<hgrid, kHeavyThreads, hs, st>>>(ws, ac, log_n);
+    else k_aev_bwd_heavy<0, false><<<hgrid, kHeavyThreads, hs, st>>>(ws, ac, log_n);
   }
 }
 
@@ -972,13 +1217,20 @@ cudaError_t aev_ensure_smem(const Ws& ws) {
   for (int np = 1; np <= kMaxSpecies * (kMaxSpecies + 1) / 2; ++np)
     need_b = std::max(need_b, (int)aev_bwd_smem(ws, np));
   const int need_f = (int)aev_fwd_smem(ws);
+  int need_h = 0;
+  for (int np = 1; np <= kMaxSpecies * (kMaxSpecies + 1) / 2; ++np)
+    need_h = std::max(need_h, (int)heavy_smem(ws, np));
   const void* fwd[2] = {(const void*)k_aev_fwd<32>, (const void*)k_aev_fwd<0>};
   const void* bwd[4] = {(const void*)k_aev_bwd<32, false>, (const void*)k_aev_bwd<32, true>,
                         (const void*)k_aev_bwd<0, false>, (const void*)k_aev_bwd<0, true>};
-  for (int pass = 0; pass < 2; ++pass)
+  const void* hvy[4] = {(const void*)k_aev_bwd_heavy<32, false>,
+                        (const void*)k_aev_bwd_heavy<32, true>,
+                        (const void*)k_aev_bwd_heavy<0, false>,
+                        (const void*)k_aev_bwd_heavy<0, true>};
+  for (int pass = 0; pass < 3; ++pass)
     for (int i = 0; i < (pass == 0 ? 2 : 4); ++i) {
-      const void* fn = pass == 0 ? fwd[i] : bwd[i];
-      const int need = pass == 0 ? need_f : need_b;
+      const void* fn = pass == 0 ? fwd[i] : pass == 1 ? bwd[i] : hvy[i];
+      const int need = pass == 0 ? need_f : pass == 1 ? need_b : need_h;
       cudaFuncAttributes attr;
       cudaError_t e = cudaFuncGetAttributes(&attr, fn);
       if (e != cudaSuccess) return e;

@@ -344,6 +344,7 @@ size_t carve(nnp_handle* h, char* base) {
   ws.dEdG = c.take<float>(rows * Dp);
   ws.atom_e = c.take<float>(rows);
   ws.f_pos = c.take<float4>(n);
+  ws.heavy = c.take<int>(n);
   if (h->skin > 0.f) {
     ws.skin_state = c.take<int>(4);
     ws.ref = c.take<float4>(n);
@@ -1465,6 +1466,7 @@ size_t noalloc_carve(const Model& m, int n_atoms, char* base, Ws* ws, MlpBufs* m
   ws->dEdG = c.take<float>(rows * Dp);
   ws->atom_e = c.take<float>(rows);
   ws->f_pos = c.take<float4>(n);
+  ws->heavy = c.take<int>(n);
   *mb = MlpBufs{};
   if (!mlp_fused_supported(m.md)) {   // the fused kernel needs no activation buffers
     mb->H1 = c.take<float>(rows * E * m.md.h1);

@@ -122,6 +122,8 @@ struct Ws {
   float* dEdG;          // [row_cap][Dp]
   float* atom_e;        // [row_cap] per-row energy (mean over the ensemble, incl. shift)
   float4* f_pos;        // [n_in] forces on packed atoms
+  int* heavy;           // [n_in] packed positions of the centres the warp-per-centre
+                        // AEV backward hands on (count in totals[2])
   // persistent neighbour lists with a skin (null skin_state: rebuilt every call)
   int* skin_state;      // [4]: max displacement (float bits), forced rebuild, builds, lists valid
   float half_skin;      // rebuild when an atom moved farther than this since the build

@@ -409,6 +409,26 @@ def test_centres_with_more_live_blocks_than_staged(torch_cuda):
     check_system(pot, orc, s)
 
 
+@pytest.mark.parametrize("precision", ["fp32_split", "fp32_simt"])
+def test_dense_centres_take_the_cta_per_centre_backward(torch_cuda, precision):
+    """A compact branched solute in water: its core atoms have more than 48
+    angular neighbours (thousands of triplets each), so the warp-per-centre force
+    kernel hands them to the CTA-per-centre one, while the waters stay on the
+    warp kernel.  Energy, forces and virial of the mix against the oracle."""
+    pot, orc = make("ani7", precision=precision)
+    s = synth.solvated_solute(300, 200, 22.0, seed=17)
+    x = s.coords.astype(np.float64)
+    d = x[:, None, :] - x[None, :, :]
+    d -= s.box * np.round(d / s.box)
+    n_a = ((np.linalg.norm(d, axis=-1) <= 3.5).sum(1) - 1)
+    assert (n_a > 48).sum() >= 5 and (n_a <= 48).sum() > 500
+    check_system(pot, orc, s, aev=False)
+    out = pot.energy_forces_batch([to_cuda(s)], virial=True)[0]
+    ref = orc.energy_forces(s.coords, s.species, s.box)
+    np.testing.assert_allclose(out["virial"].cpu().numpy().reshape(3, 3), ref["virial"],
+                               atol=1e-4 * np.abs(ref["virial"]).max() + 1e-6)
+
+
 @pytest.mark.parametrize("kind", ["ani4", "ani7x8"])
 def test_split_path_batch_of_small_molecules(torch_cuda, kind):
     """The split tensor-core path on a batch of 20-60-atom molecules: few 128-row
