@@ -53,7 +53,9 @@ enum {
   NNP_ERR_CUDA = 7,           /* a CUDA runtime call failed                            */
   NNP_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up                    */
   NNP_PENDING = 9,            /* result not ready yet                                  */
-  NNP_ERR_UNSUPPORTED = 10    /* hyper-parameters outside what the kernels implement   */
+  NNP_ERR_UNSUPPORTED = 10,   /* hyper-parameters outside what the kernels implement   */
+  NNP_ERR_BOUNDS = 11         /* bounds-checked build only: a kernel found an index out
+                                 of range, skipped the access and recorded the site     */
 };
 
 /* precision of the per-species networks (AEVs, their backward and the forces
@@ -295,6 +297,25 @@ int nnp_sync_status(nnp_handle* h, void* stream);
 
 /* Length of the atomic environment vector. */
 int nnp_aev_dim(const nnp_handle* h);
+
+/* ---------------------------------------------------------------- build variants
+ * The library also builds as libnnp_debug.so with index checks in its kernels
+ * (the neighbour lists' entries and the cells they come from, the packed
+ * positions and AEV rows, the force targets and triplet slots of the AEV
+ * backward, the GEMM epilogues' output rows).  A failed check skips the access,
+ * sets a flag in the handle's status word and records the first failing site;
+ * the call then returns NNP_ERR_BOUNDS with the site in nnp_last_error().  It
+ * stands in for a memory checker: same API, same results, slower kernels.
+ * nnp_build_flags: NNP_BUILD_BOUNDS_CHECKS set in the bounds-checked build. */
+#define NNP_BUILD_BOUNDS_CHECKS 1
+int nnp_build_flags(void);
+
+/* The check itself, run on the host (for tests of the check's bookkeeping):
+ * returns 1 if 0 <= i < n, else ORs 32 into status[0] (status[0..3], caller
+ * memory), stores `site` (1..10, as listed above in that order) in status[3] if
+ * it holds 0, and returns 0.  Returns -1 (nnp_last_error says why) for a null
+ * status or an unknown site. */
+int nnp_debug_check_index(int site, int64_t i, int64_t n, int* status);
 /* Tensor-core paths (NNP_BF16_MLP, NNP_FP32_SPLIT): enable != 0 runs the layers
  * after the first -- L2, L3 with the output layer, and their backward B3, B2 --
  * as one fused kernel per 128-row tile with the activations in shared memory

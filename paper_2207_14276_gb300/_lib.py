@@ -10,7 +10,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libnnp.so")
+# NNP_DEBUG_BOUNDS=1 in the environment selects the bounds-checked build
+DEBUG_BOUNDS = os.environ.get("NNP_DEBUG_BOUNDS", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libnnp_debug.so" if DEBUG_BOUNDS else "libnnp.so")
 
 NNP_OK = 0
 NNP_ERR_ARG = 1
@@ -23,6 +25,8 @@ NNP_ERR_CUDA = 7
 NNP_ERR_TIMEOUT = 8
 NNP_PENDING = 9
 NNP_ERR_UNSUPPORTED = 10
+NNP_ERR_BOUNDS = 11
+NNP_BUILD_BOUNDS_CHECKS = 1
 NNP_FP32 = 0
 NNP_BF16_MLP = 1
 NNP_FP32_SPLIT = 2
@@ -33,7 +37,7 @@ PRECISIONS = {"fp32": NNP_FP32, "bf16": NNP_BF16_MLP, "fp32_split": NNP_FP32_SPL
 STATUS_NAMES = {
     0: "NNP_OK", 1: "NNP_ERR_ARG", 2: "NNP_ERR_SPECIES", 3: "NNP_ERR_BOX_TOO_SMALL",
     4: "NNP_ERR_NONFINITE", 5: "NNP_ERR_CAPACITY", 6: "NNP_ERR_OOM", 7: "NNP_ERR_CUDA",
-    8: "NNP_ERR_TIMEOUT", 9: "NNP_PENDING", 10: "NNP_ERR_UNSUPPORTED",
+    8: "NNP_ERR_TIMEOUT", 9: "NNP_PENDING", 10: "NNP_ERR_UNSUPPORTED", 11: "NNP_ERR_BOUNDS",
 }
 
 # every symbol include/nnp.h declares (checked by the CPU test-suite)
@@ -47,7 +51,7 @@ EXPORTS = (
     "nnp_n_weights", "nnp_debug_wait_probe", "nnp_set_skin", "nnp_list_stats",
     "nnp_integrate", "nnp_noalloc_max_atoms", "nnp_debug_cell_grid", "nnp_network_path",
     "nnp_set_fused_chain", "nnp_set_fused_aev_l1", "nnp_set_sparse_rows",
-    "nnp_debug_tile_masks",
+    "nnp_debug_tile_masks", "nnp_build_flags", "nnp_debug_check_index",
 )
 
 
@@ -119,6 +123,8 @@ def lib():
     L.nnp_energy_forces_host.argtypes = [P, i64, P, P, P, P, P, P, P]
     L.nnp_sync_status.argtypes = [P, P]
     L.nnp_aev_dim.argtypes = [P]
+    L.nnp_build_flags.argtypes = []
+    L.nnp_debug_check_index.argtypes = [i, i64, i64, ctypes.POINTER(i)]
     L.nnp_network_path.argtypes = [P]
     L.nnp_set_fused_chain.argtypes = [P, i]
     L.nnp_set_fused_aev_l1.argtypes = [P, i]

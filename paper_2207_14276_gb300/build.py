@@ -14,6 +14,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnnp.so")
+# the bounds-checked variant: the same sources with -DNNP_DEBUG_BOUNDS
+OBJ_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libnnp_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "--expt-relaxed-constexpr"]
@@ -37,17 +40,24 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: bool = True) -> str:
+    """Build libnnp.so and (debug=True) the bounds-checked libnnp_debug.so; the
+    translation units of both variants compile in one parallel pass."""
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "nnp.h"))
-    objs, jobs = [], []
-    for src in sources():
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        if force or _stale(obj, [src] + headers):
-            jobs.append([nvcc, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj])
+    variants = [(OBJ, LIB, [])] + ([(OBJ_DEBUG, LIB_DEBUG, ["-DNNP_DEBUG_BOUNDS"])] if debug else [])
+    jobs, links = [], []
+    for obj_dir, lib, defs in variants:
+        os.makedirs(obj_dir, exist_ok=True)
+        objs, n_jobs = [], len(jobs)
+        for src in sources():
+            obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
+            objs.append(obj)
+            if force or _stale(obj, [src] + headers):
+                jobs.append([nvcc, *ARCH, *FLAGS, *defs, *extra_flags, "-c", src, "-o", obj])
+        if force or len(jobs) > n_jobs or not os.path.exists(lib):
+            links.append((lib, objs))
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         results = list(ex.map(lambda cmd: subprocess.run(cmd, capture_output=True, text=True), jobs))
     for cmd, r in zip(jobs, results):
@@ -56,10 +66,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(r.stdout, r.stderr)
         if r.returncode:
             raise RuntimeError(f"nvcc failed for {cmd[-3]}")
-    if force or jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    for lib, objs in links:
+        tmp = lib + f".tmp{os.getpid()}"
         subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     return LIB
 
 

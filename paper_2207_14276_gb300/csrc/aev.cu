@@ -108,11 +108,14 @@ __device__ __forceinline__ Geo pair_geo(const float4& xi, const float4& xj, cons
 // A lane takes two entries per pass and issues both gathers before either is used.
 template <class Visit>
 __device__ __forceinline__ void stage_list(int n, const int* lst, const float4& xi, const SysDev& d,
-                                           const float4* xyzq, unsigned lane, Visit visit) {
+                                           const Ws& ws, unsigned lane, Visit visit) {
+  const float4* xyzq = ws.xyzq;
   for (int t0 = 0; t0 < n; t0 += 64) {
     const int ta = t0 + (int)lane, tb = ta + 32;
-    const int ja = ta < n ? lst[ta] : -1;
-    const int jb = tb < n ? lst[tb] : -1;
+    int ja = ta < n ? lst[ta] : -1;
+    int jb = tb < n ? lst[tb] : -1;
+    if (ja >= 0 && !NNP_IN_BOUNDS(ws.status, kSiteAevNeighbour, ja, ws.totals[0])) ja = -1;
+    if (jb >= 0 && !NNP_IN_BOUNDS(ws.status, kSiteAevNeighbour, jb, ws.totals[0])) jb = -1;
     const float4 xa = ja >= 0 ? xyzq[ja] : xi;
     const float4 xb = jb >= 0 ? xyzq[jb] : xi;
     if (ja >= 0) visit(ta, ja, pair_geo(xi, xa, d));
@@ -339,11 +342,11 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
   const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
-  stage_list(H.off_r[ac.S], lr, xi, d, ws.xyzq, lane,
+  stage_list(H.off_r[ac.S], lr, xi, d, ws, lane,
              [&](int slot, int, const Geo& g) {
                rad[slot] = make_float2(g.r, fcut(g.r, ac.rc_r, inv_rc_r));
              });
-  stage_list(H.off_a[ac.S], la, xi, d, ws.xyzq, lane,
+  stage_list(H.off_a[ac.S], la, xi, d, ws, lane,
              [&](int slot, int, const Geo& g) {
                const float inv = rcp_approx(g.r);
                angv[slot] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
@@ -446,6 +449,7 @@ k_aev_fwd(Ws ws, AevConst ac) {
   fill_pair_table(pair_su, ac);
   __syncthreads();
   if (p >= ws.totals[0]) return;
+  if (!NNP_IN_BOUNDS(ws.status, kSiteAevRow, ws.pos_slot[p], ws.row_cap)) return;
   const size_t row = (size_t)ws.pos_slot[p] * ac.Dp;
   float* G = ws.aev + row;
   uint16_t* Gh = ws.aev_h ? ws.aev_h + row : nullptr;
@@ -644,7 +648,10 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
   const float* g_row = ws.dEdG + (size_t)ws.pos_slot[p] * ac.Dp;
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
   if (H.off_a[ac.S] > cap_l) {
-    if (lane == 0) ws.heavy[atomicAdd(ws.totals + 2, 1)] = p;
+    if (lane == 0) {
+      const int hi = atomicAdd(ws.totals + 2, 1);
+      if (NNP_IN_BOUNDS(ws.status, kSiteBwdHeavy, hi, ws.n_in)) ws.heavy[hi] = p;
+    }
     return;
   }
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
@@ -659,7 +666,7 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
     gr[i] = f < ac.S * kNR ? g_row[f] : 0.f;
   }
   // angular neighbours: unit vector and R, (f_c, f_c', 1/R, packed index)
-  stage_list(H.off_a[ac.S], la, xi, d, ws.xyzq, lane,
+  stage_list(H.off_a[ac.S], la, xi, d, ws, lane,
              [&](int slot, int j, const Geo& g) {
                const float inv = rcp_approx(g.r);
                angv[slot] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
@@ -690,8 +697,10 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
   int sr = 0;
   for (int t0 = 0; t0 < nr_tot; t0 += 64) {
     const int ta = t0 + (int)lane, tb = ta + 32;
-    const int ja = ta < nr_tot ? lr[ta] : -1;
-    const int jb = tb < nr_tot ? lr[tb] : -1;
+    int ja = ta < nr_tot ? lr[ta] : -1;
+    int jb = tb < nr_tot ? lr[tb] : -1;
+    if (ja >= 0 && !NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, ja, ws.totals[0])) ja = -1;
+    if (jb >= 0 && !NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, jb, ws.totals[0])) jb = -1;
     const float4 xa = ja >= 0 ? ws.xyzq[ja] : xi;
     const float4 xb = jb >= 0 ? ws.xyzq[jb] : xi;
     if (ja >= 0) {
@@ -777,6 +786,9 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
       int j, k;
       decode_pair_diag(t - bt_start[bl], same, cs, cu, inv_cs, inv_cu, &j, &k);
       const int tj = os + j, tk = ou + k;
+      if (!NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tj, na_tot) ||
+          !NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tk, na_tot))
+        continue;
       float3 uj, uk;
       triplet_bwd<ZETA>(ac, angv[tj], angv[tk], angf[tj], angf[tk], gblk, uj, uk);
       const int cp = (int)lane & (n_copy - 1);
@@ -800,7 +812,9 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
       a.z += accz[i];
     }
     const float4 v = angv[t];
-    atomicAdd(&ws.f_pos[__float_as_int(angf[t].w)], make_float4(-a.x, -a.y, -a.z, 0.f));
+    const int jt = __float_as_int(angf[t].w);
+    if (NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, jt, ws.totals[0]))
+      atomicAdd(&ws.f_pos[jt], make_float4(-a.x, -a.y, -a.z, 0.f));
     fi[0] += a.x; fi[1] += a.y; fi[2] += a.z;
     if (VIR) {
       const float ux = v.x * v.w, uy = v.y * v.w, uz = v.z * v.w;
@@ -879,7 +893,8 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
     const int* la = ws.nb_a + (size_t)p * ws.cap_a;
     const int na = H.off_a[ac.S], nr = H.off_r[ac.S];
     for (int t = tid; t < na; t += kHeavyThreads) {
-      const int j = la[t];
+      int j = la[t];
+      if (!NNP_IN_BOUNDS(ws.status, kSiteAevNeighbour, j, ws.totals[0])) j = p;
       const Geo g = pair_geo(xi, ws.xyzq[j], d);
       const float inv = rcp_approx(g.r);
       angv[t] = make_float4(g.dx * inv, g.dy * inv, g.dz * inv, g.r);
@@ -910,6 +925,7 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
     for (int t = tid; t < nr; t += kHeavyThreads) {
       while (H.off_r[sr + 1] <= t) ++sr;
       const int j = lr[t];
+      if (!NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, j, ws.totals[0])) continue;
       radial_edge_bwd<VIR>(ws, ac, xi, d, j, ws.xyzq[j], grad + sr * kNR, inv_rc_r, fi, vir);
     }
     const int n_tri = bt_start[np];
@@ -929,6 +945,9 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
       int j, k;
       decode_pair_diag(t - bt_start[bl], same, cs, cu, inv_cs, inv_cu, &j, &k);
       const int tj = os + j, tk = ou + k;
+      if (!NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tj, na) ||
+          !NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tk, na))
+        continue;
       float3 uj, uk;
       triplet_bwd<ZETA>(ac, angv[tj], angv[tk], angf[tj], angf[tk], gall + bl * 8, uj, uk);
       const int aj = tj * n_acc + cp, ak = tk * n_acc + cp;
@@ -949,7 +968,9 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
         a.z += accz[i];
       }
       const float4 v = angv[t];
-      atomicAdd(&ws.f_pos[__float_as_int(angf[t].w)], make_float4(-a.x, -a.y, -a.z, 0.f));
+      const int jt = __float_as_int(angf[t].w);
+      if (NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, jt, ws.totals[0]))
+        atomicAdd(&ws.f_pos[jt], make_float4(-a.x, -a.y, -a.z, 0.f));
       fi[0] += a.x; fi[1] += a.y; fi[2] += a.z;
       if (VIR) {
         const float ux = v.x * v.w, uy = v.y * v.w, uz = v.z * v.w;

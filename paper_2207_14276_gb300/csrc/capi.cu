@@ -880,6 +880,16 @@ int nnp_energy_forces_batch(nnp_handle* h, int n_sys, const nnp_system_t* system
 
 namespace {
 
+const char* bounds_site_name(int site) {
+  static const char* names[kSiteCount] = {
+      "an unknown site", "cell binning (cell index)", "scatter (packed position)",
+      "neighbour search (list entry)", "AEV kernels (staged neighbour)", "AEV forward (row slot)",
+      "AEV backward (force target)", "AEV backward (triplet slot)",
+      "AEV backward (dense-centre list)", "finalize (row slot)",
+      "tensor-core epilogue (output row)"};
+  return (site > 0 && site < kSiteCount) ? names[site] : names[0];
+}
+
 // enqueue the read-back and reset of the device status word on st
 cudaError_t enqueue_status_read(nnp_handle* h, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(h->status_host, h->ws.status, 4 * sizeof(int),
@@ -894,6 +904,9 @@ int status_result(nnp_handle* h) {
   if (f & kStSpecies) return fail(NNP_ERR_SPECIES, "species index out of range");
   if (f & kStNonFinite) return fail(NNP_ERR_NONFINITE, "non-finite coordinate in the ML region");
   if (f & kStTimeout) return fail(NNP_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (f & kStBounds)
+    return fail(NNP_ERR_BOUNDS, std::string("index out of range at ") +
+                                    bounds_site_name(h->status_host[3]) + " (access skipped)");
   if (f & (kStCapacity | kStCells)) {
     const int need_r = h->status_host[1], need_a = h->status_host[2];
     if (need_r > kStageCap)
@@ -1230,6 +1243,17 @@ extern "C" int64_t nnp_n_weights(const nnp_handle* h) {
 }
 
 int nnp_aev_dim(const nnp_handle* h) { return h ? h->model->ac.D : -1; }
+
+int nnp_build_flags(void) { return kBoundsChecked ? NNP_BUILD_BOUNDS_CHECKS : 0; }
+
+int nnp_debug_check_index(int site, int64_t i, int64_t n, int* status) {
+  g_err.clear();
+  if (!status || site <= kSiteNone || site >= kSiteCount) {
+    fail(NNP_ERR_ARG, "bad argument");
+    return -1;
+  }
+  return bounds_ok(status, site, i, n) ? 1 : 0;
+}
 int nnp_debug_tile_masks(nnp_handle* h, void* stream, uint32_t* out_host, int max_tiles,
                          int* n_tiles) {
   g_err.clear();

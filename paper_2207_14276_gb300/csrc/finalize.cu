@@ -22,7 +22,8 @@ __global__ void k_finalize(Ws ws, const float* e_row, int E, int e_row_net,
   double Ei = 0.0;
   if (live) {
     b = ws.pos_sys[p];
-    const int slot = ws.pos_slot[p];
+    int slot = ws.pos_slot[p];
+    if (!NNP_IN_BOUNDS(ws.status, kSiteFinalize, slot, ws.row_cap)) slot = 0;
     const int s = __float_as_int(ws.xyzq[p].w);
     float acc = 0.f;
     for (int e = 0; e < E; ++e) acc += e_row[(size_t)e * e_row_net + slot];

@@ -223,13 +223,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       if (!ntile_live(g, tl.m0, tl.n0)) continue;
       const int ab = j & 1;
       const int m = tl.m0 + q * 32 + lane;
+      const bool row_ok = NNP_IN_BOUNDS(g.status, kSiteGemmRow, m, g.seg_start[g.S]);
       // the backward's stored activations do not depend on the MMAs: their loads
       // are issued before the wait for the accumulator
       // (the split path also prefetches the low parts)
       constexpr bool kPre = (EPI == kEpiMul);
       uint4 pre[kPre ? kMaxChunks : 1][2];
       uint4 prel[kPre && SPLIT ? kMaxChunks : 1][2];
-      if (kPre) {
+      if (kPre && row_ok) {
         const size_t oa = (size_t)m * g.ld_aux + (size_t)tl.e * g.aux_net + tl.n0;
         const __nv_bfloat16* arow = static_cast<const __nv_bfloat16*>(g.aux) + oa;
         const __nv_bfloat16* lrow = SPLIT ? static_cast<const __nv_bfloat16*>(g.aux2) + oa : nullptr;
@@ -281,7 +282,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
         const int n = tl.n0 + c0;
         float v[16];
         tmem_ld16(trow + (uint32_t)c0, v);
-        if (n >= g.N) continue;
+        if (n >= g.N || !row_ok) continue;
         if (EPI == kEpiCelu || EPI == kEpiCeluDot) {
           float b[16];
 #pragma unroll
@@ -352,7 +353,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       }
       // the two warps of a row each add their half of the output-layer dot product
       // (e_row starts at zero; a sum of two terms does not depend on their order)
-      if (EPI == kEpiCeluDot) atomicAdd(g.e_row + (size_t)tl.e * g.e_row_net + m, dot);
+      if (EPI == kEpiCeluDot && row_ok) atomicAdd(g.e_row + (size_t)tl.e * g.e_row_net + m, dot);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar[ab]);

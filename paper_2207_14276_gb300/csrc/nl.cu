@@ -295,6 +295,7 @@ __device__ __forceinline__ void bin_body(const Ws& ws, int gi, int n_in) {
   const int s = d.in.species[local];
   const int cx = cell_coord(x, d, 0), cy = cell_coord(y, d, 1), cz = cell_coord(z, d, 2);
   const int gcell = d.cell_base + (cx * d.nc[1] + cy) * d.nc[2] + cz;
+  if (!NNP_IN_BOUNDS(ws.status, kSiteBinCell, gcell, ws.cell_cap)) return;
   const int rank = atomicAdd(&ws.cell_count[gcell], 1);
   const unsigned sg = __match_any_sync(act, s);
   const int leader = __ffs(sg) - 1;
@@ -371,6 +372,8 @@ __device__ __forceinline__ void scatter_body(const Ws& ws, int gi, int n_in) {
   const int gcell = ws.in_cell[gi];
   const int pos = ws.cell_start[gcell] + ws.in_rank[gi];
   const int slot = ws.in_slot[gi];
+  if (!NNP_IN_BOUNDS(ws.status, kSiteScatterPos, pos, n_in)) return;
+  if (!NNP_IN_BOUNDS(ws.status, kSiteAevRow, slot, ws.row_cap)) return;
   ws.xyzq[pos] = make_float4(wrap_coord(d.in.coords[3 * local + 0], d, 0),
                              wrap_coord(d.in.coords[3 * local + 1], d, 1),
                              wrap_coord(d.in.coords[3 * local + 2], d, 2),
@@ -558,11 +561,11 @@ __device__ void centre_lists_global(const Ws& ws, const AevConst& ac, int p, int
       const unsigned ba = __ballot_sync(0xffffffffu, ma);
       if (mr) {
         const int at = wr_r + cr + __popc(br & lanemask_lt());
-        if (at < ws.cap_r) out_r[at] = j;
+        if (at < ws.cap_r && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j, ws.totals[0])) out_r[at] = j;
       }
       if (ma) {
         const int at = wr_a + ca + __popc(ba & lanemask_lt());
-        if (at < ws.cap_a) out_a[at] = j;
+        if (at < ws.cap_a && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j, ws.totals[0])) out_a[at] = j;
       }
       cr += __popc(br);
       ca += __popc(ba);
@@ -630,11 +633,11 @@ __device__ __forceinline__ void centre_lists_staged(const Ws& ws, const AevConst
       const unsigned ba = __ballot_sync(0xffffffffu, ang);
       if (keep) {
         const int at = wr_r + cr + __popc(br & lanemask_lt());
-        if (at < ws.cap_r) out_r[at] = j;
+        if (at < ws.cap_r && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j, ws.totals[0])) out_r[at] = j;
       }
       if (ang) {
         const int at = wr_a + ca + __popc(ba & lanemask_lt());
-        if (at < ws.cap_a) out_a[at] = j;
+        if (at < ws.cap_a && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j, ws.totals[0])) out_a[at] = j;
       }
       cr += __popc(br);
       ca += __popc(ba);
@@ -837,11 +840,11 @@ __global__ void __launch_bounds__(256) k_list_refresh(Ws ws, AevConst ac) {
       const unsigned ba = __ballot_sync(0xffffffffu, ang);
       if (keep) {
         const int at = wr_r + cr + __popc(br & lanemask_lt());
-        if (at < ws.cap_r) out_r[at] = j;
+        if (at < ws.cap_r && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j, ws.totals[0])) out_r[at] = j;
       }
       if (ang) {
         const int at = wr_a + ca + __popc(ba & lanemask_lt());
-        if (at < ws.cap_a) out_a[at] = j;
+        if (at < ws.cap_a && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j, ws.totals[0])) out_a[at] = j;
       }
       cr += __popc(br);
       ca += __popc(ba);

@@ -22,7 +22,49 @@ enum : int {
   kStCapacity = 4,
   kStCells = 8,
   kStTimeout = 16,
+  kStBounds = 32,    // a checked index was out of range (bounds-checked builds only)
 };
+
+// ---- index checks of the bounds-checked build (-DNNP_DEBUG_BOUNDS, built as
+// libnnp_debug.so).  A failed check sets kStBounds in the status word, records
+// the first failing site in status[3] and makes the caller skip the access;
+// the host turns it into NNP_ERR_BOUNDS.  In the normal build NNP_IN_BOUNDS is
+// `true` and its arguments are not evaluated.
+enum BoundsSite : int {
+  kSiteNone = 0,
+  kSiteBinCell,          // cell binning: global cell index < cell capacity
+  kSiteScatterPos,       // scatter: packed position < batch atoms
+  kSiteNbCandidate,      // neighbour search: list entry < ML atoms
+  kSiteAevNeighbour,     // AEV kernels: staged neighbour < ML atoms
+  kSiteAevRow,           // AEV forward: row slot < row capacity
+  kSiteBwdNeighbour,     // AEV backward: force target < ML atoms
+  kSiteBwdTriplet,       // AEV backward: triplet's neighbour slots < list length
+  kSiteBwdHeavy,         // AEV backward: dense-centre list index < batch atoms
+  kSiteFinalize,         // finalize: row slot < row capacity
+  kSiteGemmRow,          // tensor-core epilogue: output row < row capacity
+  kSiteCount
+};
+
+__host__ __device__ inline bool bounds_ok(int* status, int site, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+#ifdef __CUDA_ARCH__
+  atomicOr(status, kStBounds);
+  atomicCAS(status + 3, 0, site);
+#else
+  status[0] |= kStBounds;
+  if (status[3] == 0) status[3] = site;
+#endif
+  return false;
+}
+
+#ifdef NNP_DEBUG_BOUNDS
+#define NNP_IN_BOUNDS(status, site, i, n) \
+  ::nnp::bounds_ok((status), (site), (long long)(i), (long long)(n))
+constexpr bool kBoundsChecked = true;
+#else
+#define NNP_IN_BOUNDS(status, site, i, n) true
+constexpr bool kBoundsChecked = false;
+#endif
 
 // AEV hyper-parameters in the form the kernels use
 struct AevConst {
