@@ -297,12 +297,12 @@ __device__ __forceinline__ void fill_pair_table(uint8_t* pair_su, const AevConst
 __device__ __forceinline__ uint32_t row_slices(const ListHdr& H, const AevConst& ac, unsigned lane,
                                                const uint8_t* pair_su) {
   uint32_t m = 1u;
-  if ((int)lane < ac.S && H.off_r[lane + 1] > H.off_r[lane]) m |= 1u << (((int)lane * kNR) >> 6);
+  if ((int)lane < ac.S && H.off_r[lane + 1] > H.off_r[lane]) m |= 1u << (ac.rcol[lane] >> 6);
   for (int q = (int)lane; q < ac.n_pairs; q += 32) {
     const int sp = pair_su[q] & 15, u = pair_su[q] >> 4;
     const int cs = H.off_a[sp + 1] - H.off_a[sp], cu = H.off_a[u + 1] - H.off_a[u];
     if (sp == u ? cs >= 2 : (cs > 0 && cu > 0)) {
-      const int f0 = ac.S * kNR + q * 32;
+      const int f0 = ac.acol[q];
       m |= (1u << (f0 >> 6)) | (1u << ((f0 + 31) >> 6));
     }
   }
@@ -361,7 +361,7 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
     float acc = 0.f;
     const int o = H.off_r[s], n = H.off_r[s + 1] - o;
     if (n == 0) {   // no neighbour of this species: a zero block
-      if (lane < 16 && block_in(m, s * kNR, kNR)) out(s * kNR + lane, 0.f);
+      if (lane < 16 && block_in(m, ac.rcol[s], kNR)) out(ac.rcol[s] + lane, 0.f);
       continue;
     }
     for (int t = half; t < n; t += 2) {
@@ -370,7 +370,7 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
       acc = fmaf(fast_exp2(cr_ * x * x), q.y, acc);
     }
     acc += __shfl_xor_sync(kFull, acc, 16);
-    if (lane < 16 && block_in(m, s * kNR, kNR)) out(s * kNR + lane, acc);
+    if (lane < 16 && block_in(m, ac.rcol[s], kNR)) out(ac.rcol[s] + lane, acc);
   }
   // ---- angular, Eq. 5: the blocks of species pairs with a pair j < k, and the
   // zero blocks of the other pairs where the row is written
@@ -383,14 +383,14 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
       const int sp = pair_su[q] & 15, u = pair_su[q] >> 4;
       const int cs = H.off_a[sp + 1] - H.off_a[sp], cu = H.off_a[u + 1] - H.off_a[u];
       lv = sp == u ? cs >= 2 : (cs > 0 && cu > 0);
-      zr = !lv && block_in(m, ac.S * kNR + q * 32, 32);
+      zr = !lv && block_in(m, ac.acol[q], 32);
     }
     live[h] = __ballot_sync(kFull, lv);
     zero[h] = __ballot_sync(kFull, zr);
   }
   for (int h = 0; h < 2; ++h)
     for (uint32_t z = zero[h]; z; z &= z - 1)
-      out(ac.S * kNR + (h * 32 + __ffs(z) - 1) * 32 + lane, 0.f);
+      out(ac.acol[h * 32 + __ffs(z) - 1] + lane, 0.f);
   for (int h = 0; h < 2; ++h)
     for (uint32_t lv = live[h]; lv; lv &= lv - 1) {
       const int q = h * 32 + __ffs(lv) - 1;
@@ -399,7 +399,7 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
       const int ou = H.off_a[u], cu = H.off_a[u + 1] - ou;
       const int same = (s == u);
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
-      const int fb = ac.S * kNR + q * 32;
+      const int fb = ac.acol[q];
       const float inv_cu = 1.f / (float)max(cu, 1);
       float acc[32];
 #pragma unroll
@@ -663,7 +663,7 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
 #pragma unroll
   for (int i = 0; i < kMaxSpecies * kNR / 32; ++i) {
     const int f = (int)lane + 32 * i;
-    gr[i] = f < ac.S * kNR ? g_row[f] : 0.f;
+    gr[i] = f < ac.S * kNR ? g_row[ac.rcol[f >> 4] + (f & 15)] : 0.f;
   }
   // angular neighbours: unit vector and R, (f_c, f_c', 1/R, packed index)
   stage_list(H.off_a[ac.S], la, xi, d, ws, lane,
@@ -721,7 +721,6 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
   // the dE/dG blocks with triplets, in block order; a group of up to n_gall of
   // them at a time is staged (its 32 values, index 8a + z, transposed to [z][a]
   // so that an angle section is one 16-byte load) and its triplets processed
-  const float* ga = g_row + ac.S * kNR;
   float* gf = reinterpret_cast<float*>(gall);
   {
     const unsigned l0 = __ballot_sync(kFull, (int)lane < np && bt_start[lane + 1] > bt_start[lane]);
@@ -758,7 +757,7 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
             int q;
             if (m0) { q = __ffs(m0) - 1; m0 &= m0 - 1; }
             else { q = 32 + __ffs(m1) - 1; m1 &= m1 - 1; }
-            gv[k] = ga[q * 32 + lane];
+            gv[k] = g_row[ac.acol[q] + lane];
             if (lane == 0) bt_geo[q].w = (bt_geo[q].w & 0x1ffff) | ((k0 + k) << 17);
             if (b_lo < 0) b_lo = q;
             b_hi = q;
@@ -907,14 +906,13 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
       accy[i] = 0.f;
       accz[i] = 0.f;
     }
-    for (int f = tid; f < ac.S * kNR; f += kHeavyThreads) grad[f] = g_row[f];
+    for (int f = tid; f < ac.S * kNR; f += kHeavyThreads) grad[f] = g_row[ac.rcol[f >> 4] + (f & 15)];
     if (w == 0) build_block_table(H, ac, lane, bt_geo, bt_start);
     __syncthreads();
     // every block with triplets: its 32 dE/dG values (index 8a + z) as [z][a]
-    const float* ga = g_row + ac.S * kNR;
     for (int i = tid; i < np * 32; i += kHeavyThreads) {
       const int q = i >> 5, l = i & 31;
-      if (bt_start[q + 1] > bt_start[q]) gf[q * 32 + (l & 7) * 4 + (l >> 3)] = ga[i];
+      if (bt_start[q + 1] > bt_start[q]) gf[q * 32 + (l & 7) * 4 + (l >> 3)] = g_row[ac.acol[q] + l];
     }
     __syncthreads();
     float fi[3] = {0.f, 0.f, 0.f};

@@ -72,6 +72,9 @@ struct Model {
   float alpha = 0.1f;
   MlpWeights mw{};
   double* ebias = nullptr;  // device [S]
+  std::vector<int16_t> col_of_feat;   // AEV column of each feature of the paper's order [D]
+  int16_t* col_of_feat_dev = nullptr; // the same on the device
+  int16_t* feat_of_col_dev = nullptr; // its inverse [D]
   std::vector<void*> allocs;
   ~Model() {
     for (void* p : allocs) cudaFree(p);
@@ -138,6 +141,44 @@ struct nnp_handle {
 namespace {
 
 // ---------------------------------------------------------------- model setup
+// Column layout of the AEV rows.  The paper lists the radial blocks species by
+// species, then the angular blocks by species pair (s <= u, row-major).  The
+// library keeps each block's values but stores the blocks ordered by how common
+// their species are in solvated biomolecular systems (H, O, C, N, S, F, Cl, then
+// by atomic number): a species' radial block, then its pairs with the species
+// before it and with itself.  A water atom's row then holds all its nonzero
+// values (radial H, O; angular HH, HO, OO) in its first 128 columns, so the
+// sparse-row GEMMs skip most of the rest.  The first layer's weights are placed
+// to match, and the diagnostic reads return the paper's order.
+void aev_layout(AevConst& ac, const int* z, std::vector<int16_t>& col_of_feat) {
+  const int S = ac.S;
+  static const int kCommon[] = {1, 8, 6, 7, 16, 9, 17};
+  auto rank = [&](int s) {
+    for (int i = 0; i < 7; ++i)
+      if (kCommon[i] == z[s]) return i;
+    return 7 + std::max(z[s], 0);
+  };
+  struct Blk { int k0, k1, k2, angular, idx; };
+  std::vector<Blk> blocks;
+  for (int s = 0; s < S; ++s) blocks.push_back({rank(s), 0, 0, 0, s});
+  for (int s = 0, q = 0; s < S; ++s)
+    for (int u = s; u < S; ++u, ++q)
+      blocks.push_back({std::max(rank(s), rank(u)), 1, std::min(rank(s), rank(u)), 1, q});
+  std::stable_sort(blocks.begin(), blocks.end(), [](const Blk& x, const Blk& y) {
+    return x.k0 != y.k0 ? x.k0 < y.k0 : x.k1 != y.k1 ? x.k1 < y.k1 : x.k2 < y.k2;
+  });
+  col_of_feat.assign(ac.D, 0);
+  int c = 0;
+  for (const Blk& b : blocks) {
+    const int width = b.angular ? kNA * kNZ : kNR;
+    const int f0 = b.angular ? S * kNR + b.idx * kNA * kNZ : b.idx * kNR;
+    if (b.angular) ac.acol[b.idx] = (int16_t)c;
+    else ac.rcol[b.idx] = (int16_t)c;
+    for (int i = 0; i < width; ++i) col_of_feat[f0 + i] = (int16_t)(c + i);
+    c += width;
+  }
+}
+
 int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
                 const nnp_weights_t* w, int precision) {
   if (!sp || !a || !w) return fail(NNP_ERR_ARG, "null argument");
@@ -172,6 +213,7 @@ int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
   ac.cos_scale = a->cos_scale;
   ac.zeta = (int)zr;
   ac.ang_pre = (float)std::pow(2.0, 1.0 - zr);
+  aev_layout(ac, sp->atomic_numbers, m->col_of_feat);
   const int* wd = w->widths;
   if (wd[0] != ac.D) return fail(NNP_ERR_ARG, "widths[0] must equal the AEV length");
   if (wd[4] != 1) return fail(NNP_ERR_ARG, "output width must be 1");
@@ -211,8 +253,9 @@ int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
       const float* B4 = p; p += 1;
       for (int o = 0; o < h1; ++o) {
         for (int k = 0; k < D; ++k) {
-          W1cat[((size_t)s * E * h1 + e * h1 + o) * Dp + k] = L1[(size_t)o * D + k];
-          W1Tcat[((size_t)s * Dp + k) * E * h1 + e * h1 + o] = L1[(size_t)o * D + k] / (float)E;
+          const int c = m->col_of_feat[k];   // feature k of the paper's order
+          W1cat[((size_t)s * E * h1 + e * h1 + o) * Dp + c] = L1[(size_t)o * D + k];
+          W1Tcat[((size_t)s * Dp + c) * E * h1 + e * h1 + o] = L1[(size_t)o * D + k] / (float)E;
         }
         b1cat[(size_t)s * E * h1 + e * h1 + o] = B1[o];
       }
@@ -258,6 +301,14 @@ int build_model(Model* m, const nnp_species_t* sp, const nnp_aev_params_t* a,
   if ((rc = upf(W2T, &m->mw.W2T))) return rc;
   if ((rc = upf(W1Tcat, &m->mw.W1Tcat))) return rc;
   if ((rc = upload(ebias.data(), S * sizeof(double), reinterpret_cast<void**>(&m->ebias)))) return rc;
+  std::vector<int16_t> feat_of_col(D);
+  for (int k = 0; k < D; ++k) feat_of_col[m->col_of_feat[k]] = (int16_t)k;
+  if ((rc = upload(m->col_of_feat.data(), D * sizeof(int16_t),
+                   reinterpret_cast<void**>(&m->col_of_feat_dev))))
+    return rc;
+  if ((rc = upload(feat_of_col.data(), D * sizeof(int16_t),
+                   reinterpret_cast<void**>(&m->feat_of_col_dev))))
+    return rc;
   if (m->net != kNetSimt) {
     // BF16 copies of the GEMM operands (round to nearest even); the split path
     // also keeps the rounded remainders w - bf16(w)
@@ -1111,7 +1162,9 @@ void vjp_weight_grads(nnp_handle* h, float* out, cudaStream_t st) {
   a.X1 = v.dl1; a.X2 = v.dl1d; a.ldx = E * h1; a.x_net = h1;
   a.Y1 = ws.aev; a.Y2 = v.U; a.ldy = Dp; a.y_net = 0;
   a.n_out = h1; a.n_in = Dp; a.n_in_real = D; a.layer_off = 0;
+  a.feat_of_col = m.feat_of_col_dev;   // W1's columns back in the paper's feature order
   launch_wgrad(a, ws, v, E, st);
+  a.feat_of_col = nullptr;
   a.X1 = v.dl2; a.X2 = v.dl2d; a.ldx = E * h2; a.x_net = h2;
   a.Y1 = v.H1; a.Y2 = v.H1d; a.ldy = E * h1; a.y_net = h1;
   a.n_out = h2; a.n_in = h1; a.n_in_real = h1; a.layer_off = off2;
@@ -1384,8 +1437,8 @@ int nnp_debug_rows(nnp_handle* h, int which, float* out, void* stream) {
   const uint16_t* src_l = planes ? h->ws.aev_l : nullptr;
   Ws gw = h->ws;
   if (!h->last_sparse) gw.row_mask = nullptr;   // the last call wrote whole rows
-  launch_gather_rows(gw, h->last_n_in, src, src_h, src_l, h->model->ac.Dp, h->model->ac.D, out,
-                     which == 1, static_cast<cudaStream_t>(stream));
+  launch_gather_rows(gw, h->last_n_in, src, src_h, src_l, h->model->ac.Dp, h->model->ac.D,
+                     h->model->col_of_feat_dev, out, which == 1, static_cast<cudaStream_t>(stream));
   CU_TRY(cudaGetLastError());
   return NNP_OK;
 }

@@ -53,11 +53,13 @@ __global__ void k_finalize(Ws ws, const float* e_row, int E, int e_row_net,
   }
 }
 
-// out[src_atom][f] = rows[slot][f] for f < D (rows of the batch's input atoms)
-// rows: FP32, or (rows_h != null) BF16 bit patterns widened to FP32, plus the
-// low BF16 parts rows_l of the split path if given
+// out[src_atom][f] = rows[slot][col[f]] for f < D (rows of the batch's input
+// atoms; col: the AEV column of feature f of the paper's order); rows: FP32, or
+// (rows_h != null) BF16 bit patterns widened to FP32, plus the low BF16 parts
+// rows_l of the split path if given
 __global__ void k_gather_rows(Ws ws, const float* rows, const uint16_t* rows_h,
-                              const uint16_t* rows_l, int ld, int D, float* out, int by_tile) {
+                              const uint16_t* rows_l, int ld, int D, const int16_t* col,
+                              float* out, int by_tile) {
   const int p = blockIdx.x;
   if (p >= ws.totals[0]) return;
   const int slot = ws.pos_slot[p];
@@ -66,9 +68,10 @@ __global__ void k_gather_rows(Ws ws, const float* rows, const uint16_t* rows_h,
   // (dE/dG: not computed) mask read as 0
   const uint32_t m = !ws.row_mask ? ~0u : by_tile ? ws.tile_mask[slot >> 7] : ws.row_mask[slot];
   for (int f = threadIdx.x; f < D; f += blockDim.x) {
-    const size_t i = (size_t)slot * ld + f;
+    const int c = col[f];
+    const size_t i = (size_t)slot * ld + c;
     float v;
-    if (!((m >> (f >> 6)) & 1u)) { out[(size_t)gi * D + f] = 0.f; continue; }
+    if (!((m >> (c >> 6)) & 1u)) { out[(size_t)gi * D + f] = 0.f; continue; }
     if (rows_h) {
       v = __uint_as_float((unsigned)rows_h[i] << 16);
       if (rows_l) v += __uint_as_float((unsigned)rows_l[i] << 16);
@@ -101,10 +104,10 @@ void launch_finalize_e(const Ws& ws, int n_in, const float* e_row, int E, int e_
 }
 
 void launch_gather_rows(const Ws& ws, int n_in, const float* rows, const uint16_t* rows_h,
-                        const uint16_t* rows_l, int ld, int D, float* out, int by_tile,
-                        cudaStream_t st) {
+                        const uint16_t* rows_l, int ld, int D, const int16_t* col, float* out,
+                        int by_tile, cudaStream_t st) {
   if (n_in <= 0) return;
-  k_gather_rows<<<n_in, 128, 0, st>>>(ws, rows, rows_h, rows_l, ld, D, out, by_tile);
+  k_gather_rows<<<n_in, 128, 0, st>>>(ws, rows, rows_h, rows_l, ld, D, col, out, by_tile);
 }
 
 void launch_gather_nbrs(const Ws& ws, int n_in, int angular, int cap_out, int* out,

@@ -80,6 +80,13 @@ struct AevConst {
   int zeta;         // integer exponent
   float ang_pre;    // 2^(1-zeta)
   float skin;       // Verlet skin of the neighbour lists (0: lists at the cutoffs)
+  // Column layout of an AEV row: each block holds the paper's values, but the
+  // blocks are stored in an order that puts those of common species first
+  // (nnp_create fixes it from the atomic numbers); rcol[s]: first column of
+  // radial block s, acol[q]: first column of angular block q (species pair q in
+  // the paper's order).  Every block starts at a multiple of 16.
+  int16_t rcol[kMaxSpecies];
+  int16_t acol[kMaxSpecies * (kMaxSpecies + 1) / 2];
 };
 
 // per-system descriptor as passed in kernel parameters (host-filled part)
@@ -217,8 +224,8 @@ size_t aev_bwd_smem(const Ws& ws, int n_pairs = kMaxSpecies * (kMaxSpecies + 1) 
 void launch_finalize_e(const Ws& ws, int n_in, const float* e_row, int E, int e_row_net,
                        const double* ebias, cudaStream_t st);
 void launch_gather_rows(const Ws& ws, int n_in, const float* rows, const uint16_t* rows_h,
-                        const uint16_t* rows_l, int ld, int D, float* out, int by_tile,
-                        cudaStream_t st);
+                        const uint16_t* rows_l, int ld, int D, const int16_t* col, float* out,
+                        int by_tile, cudaStream_t st);
 void launch_gather_nbrs(const Ws& ws, int n_in, int angular, int cap_out, int* out,
                         cudaStream_t st);
 

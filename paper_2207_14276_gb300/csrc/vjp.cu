@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev_jvp(Ws ws, AevConst ac, Vjp
       acc = fmaf(fast_exp2(cr_ * x * x) * fmaf(-2.f * ac.eta_r * x, q.y, q.z), q.w, acc);
     }
     acc += __shfl_xor_sync(kFull, acc, 16);
-    if (lane < 16) U[s * kNR + lane] = acc;
+    if (lane < 16) U[ac.rcol[s] + lane] = acc;
   }
   const float ca_ = -ac.eta_a * kLog2e;
   const float m2eta = -2.f * ac.eta_a;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev_jvp(Ws ws, AevConst ac, Vjp
       const int ou = H.off_a[u], cu = H.off_a[u + 1] - ou;
       const int same = (s == u);
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
-      float* Ub = U + ac.S * kNR + pidx * 32;
+      float* Ub = U + ac.acol[pidx];
       if (n_tri == 0) {
         Ub[lane] = 0.f;
         continue;
@@ -316,9 +316,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev_bwd_dual(Ws ws, AevConst ac
   const int na_tot = H.off_a[ac.S];
   const int* lr = ws.nb_r + (size_t)p * ws.cap_r;
   const int* la = ws.nb_a + (size_t)p * ws.cap_a;
-  for (int f = lane; f < ac.S * kNR; f += 32) {
-    grad[f] = g_row[f];
-    gtan[f] = q_row[f];
+  for (int f = lane; f < ac.S * kNR; f += 32) {   // radial blocks, species by species
+    const int c = ac.rcol[f >> 4] + (f & 15);
+    grad[f] = g_row[c];
+    gtan[f] = q_row[c];
   }
   for (int t = lane; t < na_tot; t += 32) {
     const int j = la[t];
@@ -385,8 +386,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev_bwd_dual(Ws ws, AevConst ac
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
       if (n_tri == 0) continue;
       const float inv_cu = 1.f / (float)max(cu, 1);
-      const float* gb = g_row + ac.S * kNR + pidx * 32;
-      const float* qb = q_row + ac.S * kNR + pidx * 32;
+      const float* gb = g_row + ac.acol[pidx];
+      const float* qb = q_row + ac.acol[pidx];
       for (int t0 = 0; t0 < n_tri; t0 += 32) {
         const int t = t0 + lane;
         if (t >= n_tri) continue;
@@ -563,7 +564,8 @@ __global__ void __launch_bounds__(256) k_wgrad(WgradArgs a, const int* seg_start
   for (int i = 0; i < 4; ++i) {
     const int o = o0 + ty + 8 * i;
     if (o >= a.n_out) continue;
-    if (k < a.n_in_real) base[(size_t)o * a.n_in_real + k] = a.scale * acc[i];
+    if (k < a.n_in_real)
+      base[(size_t)o * a.n_in_real + (a.feat_of_col ? a.feat_of_col[k] : k)] = a.scale * acc[i];
     else if (k == a.n_in) base[(size_t)a.n_out * a.n_in_real + o] = a.scale * acc[i];
   }
 }

@@ -29,6 +29,7 @@ struct WgradArgs {
   float scale;
   float* out;
   long long per_net, layer_off;
+  const int16_t* feat_of_col;   // first layer: paper index of the feature of AEV column k
 };
 
 cudaError_t vjp_set_smem(const Ws& ws);

@@ -95,17 +95,18 @@ def test_gas24_energy_forces_aev_neighbours(torch_cuda):
     s = systems[0]
     check_system(pot, orc, s)
     compare_neighbours(pot, s, pot.spec)
-    # dE/dG (the network gradient) elementwise, on the 64-column slices of each
-    # row that hold a nonzero AEV element: the columns the forces read (with
-    # sparse rows the library computes no others; dE/dG of an all-zero block
-    # multiplies dG/dr = 0)
+    # dE/dG (the network gradient) elementwise, on the AEV blocks (16 radial or
+    # 32 angular features) of each row that hold a nonzero element: the entries
+    # the forces read (with sparse rows the library computes no others; dE/dG
+    # of an all-zero block multiplies dG/dr = 0)
     r = orc.energy_forces(s.coords, s.species, want_aev=True, want_dEdG=True)
     ref, G = r["dEdG"], r["aev"]
     g = pot.debug_rows(1, s.n_atoms).cpu().numpy()
-    D = G.shape[1]
+    S = pot.spec.aev.n_species
+    edges = [16 * k for k in range(S + 1)] + [16 * S + 32 * q for q in range(1, S * (S + 1) // 2 + 1)]
     live = np.zeros_like(G, dtype=bool)
-    for k in range(0, D, 64):
-        live[:, k:k + 64] = np.any(G[:, k:k + 64] != 0.0, axis=1)[:, None]
+    for a, b in zip(edges[:-1], edges[1:]):
+        live[:, a:b] = np.any(G[:, a:b] != 0.0, axis=1)[:, None]
     assert live.any(axis=1).all()
     np.testing.assert_allclose(g[live], ref[live], rtol=1e-4, atol=1e-7)
 
