@@ -202,7 +202,7 @@ k_chain_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUten
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
-        const Tile tl = tile_of(t, 1, row_tiles, 0, g.seg_start, g.S);
+        const Tile tl = tile_of(t, 1, row_tiles, g.E, 0, g.seg_start, g.S);
         const int c2 = tl.e * g.S + tl.s;
         for (int ph = 0; ph < n_ph && ok; ++ph) {
           int K, N;
@@ -303,7 +303,7 @@ k_chain_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUten
     int fulls[2] = {0, 0};   // accumulations of each TMEM region waited for so far
     bool ok = true;
     for (int t = blockIdx.x; t < T && ok; t += gridDim.x, ++tc) {
-      const Tile tl = tile_of(t, 1, row_tiles, 0, g.seg_start, g.S);
+      const Tile tl = tile_of(t, 1, row_tiles, g.E, 0, g.seg_start, g.S);
       const int m = tl.m0 + r;
       const size_t es = (size_t)tl.e * g.S + tl.s;
       // this tile's b2, b3 and w4 into shared memory (double-buffered by tile;

@@ -143,7 +143,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
-        const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.n_tile, g.seg_start, g.S);
+        const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.nets, g.n_tile, g.seg_start, g.S);
         if (!ntile_live(g, tl.m0, tl.n0)) continue;
         const uint32_t km = g.kmask ? g.kmask[tl.m0 >> 7] : ~0u;
         const int a_c1 = tl.e * g.a_c1_per_e, b_c2 = tl.e * g.b_c2_per_e + tl.s;
@@ -175,7 +175,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       int it = 0, j = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
-        const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.n_tile, g.seg_start, g.S);
+        const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.nets, g.n_tile, g.seg_start, g.S);
         if (!ntile_live(g, tl.m0, tl.n0)) continue;
         const uint32_t km = g.kmask ? g.kmask[tl.m0 >> 7] : ~0u;
         const int ab = j & 1;
@@ -219,7 +219,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     int j = 0;
     constexpr int kMaxChunks = 256 / 32;   // 16-column chunks of one warp per tile
     for (int t = blockIdx.x; t < T; t += gridDim.x) {
-      const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.n_tile, g.seg_start, g.S);
+      const Tile tl = tile_of(t, n_tiles_n, row_tiles, g.nets, g.n_tile, g.seg_start, g.S);
       if (!ntile_live(g, tl.m0, tl.n0)) continue;
       const int ab = j & 1;
       const int m = tl.m0 + q * 32 + lane;

@@ -191,12 +191,16 @@ struct Tile {
   int m0, n0, e, s;
 };
 
-__device__ __forceinline__ Tile tile_of(int t, int n_tiles_n, int row_tiles, int n_tile,
+// tile t of a layer over (N tile, network, row tile), N tile fastest, then the
+// network: the CTAs working at the same time read the weights of all networks
+// (not 152 copies of one network's) and neighbouring column ranges of the same
+// rows of the activations
+__device__ __forceinline__ Tile tile_of(int t, int n_tiles_n, int row_tiles, int nets, int n_tile,
                                         const int* seg_start, int S) {
   Tile tl;
   const int ni = t % n_tiles_n, rest = t / n_tiles_n;
-  tl.m0 = (rest % row_tiles) * kTileM;
-  tl.e = rest / row_tiles;
+  tl.e = rest % nets;
+  tl.m0 = (rest / nets) * kTileM;
   tl.n0 = ni * n_tile;
   int s = 0;
   while (s + 1 < S && tl.m0 >= seg_start[s + 1]) ++s;
