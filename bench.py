@@ -202,8 +202,35 @@ def stage_work(stage, spec, counts, n_atoms, path, sparse=(1.0, 1.0)):
     return None
 
 
+def gemm_bytes(stage, spec, n_atoms, path, sparse=(1.0, 1.0)):
+    """Compulsory DRAM bytes of one launch of a tensor-core layer: its activation
+    input A, the stored activation it multiplies by CELU' (B3, B2), and its
+    output, each once (the weights stay in L2).  Stored values take 4 bytes on
+    the split path (high and low BF16 parts) and 2 on the BF16 path; the first
+    layer reads the live K fraction of the AEV rows, the last writes FP32 dE/dG
+    over the live N fraction.  None for other stages."""
+    if path not in ("fp32_split", "bf16"):
+        return None
+    D = spec.widths[0]
+    E = spec.n_ensemble
+    h1, h2, h3 = spec.widths[1:4]
+    v = 4 if path == "fp32_split" else 2
+    n = float(n_atoms)
+    per_row = {"mlp_l1": D * sparse[0] * v + E * h1 * v,
+               "mlp_l2": E * h1 * v + E * h2 * v,
+               "mlp_l3": E * h2 * v + E * h3 * v + E * 4,
+               "mlp_b3": E * h3 * v + 2 * E * h2 * v,
+               "mlp_b2": E * h2 * v + 2 * E * h1 * v,
+               "mlp_b1": E * h1 * v + D * sparse[1] * 4}
+    return n * per_row[stage] if stage in per_row else None
+
+
 def roofline(stages, spec, counts, n_eval, path, peaks, peak_src, workload, sparse=(1.0, 1.0)):
-    """Roofline entry of the dominant stage (largest time over the profiled pass)."""
+    """Roofline entry of the dominant stage (largest time over the profiled pass).
+
+    A tensor-core layer has two ceilings, its FLOPs at the tensor peak and its
+    compulsory bytes at the HBM peak; the entry reports the one that binds (the
+    longer of the two times) and lists both under "ceilings"."""
     live = [k for k in stages if stages[k][1] > 0]
     if not live:
         return None
@@ -235,6 +262,18 @@ def roofline(stages, spec, counts, n_eval, path, peaks, peak_src, workload, spar
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock "
                                "(the measured-peaks file has no FP32 figure)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    nbytes = gemm_bytes(dom, spec, n_eval, path, sparse) if roof["bound"] == "tensor" else None
+    if nbytes is not None:
+        bw = float(peaks["hbm_gbs"])
+        hbm = {"bound": "hbm", "achieved": nbytes / (dom_ms / 1e3) / 1e9, "peak": bw, "unit": "GB/s",
+               "peak_source": f"{peak_src} (hbm_gbs)", "work_per_launch": nbytes}
+        hbm["frac"] = hbm["achieved"] / bw
+        ten = {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "peak_source", "frac")}
+        ten["work_per_launch"] = amount
+        roof["ceilings"] = {"tensor": ten, "hbm": hbm}
+        if hbm["frac"] > ten["frac"]:   # the bytes take longer than the FLOPs at their peaks
+            roof.update({k: hbm[k] for k in ("bound", "achieved", "peak", "unit", "peak_source", "frac")})
+            amount, unit = nbytes, "B"
     roof["traffic"] = recorded_traffic(dom, workload)
     roof.update({"kernel": dom, "launch_ms": dom_ms, "work_per_launch": amount,
                  "work_unit": unit, "network_path": path,

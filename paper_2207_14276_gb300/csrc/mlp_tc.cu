@@ -14,8 +14,9 @@
 //            other 16-column chunk (w / 4 picks which); bias, CELU, the width-1
 //            output layer as a dot product, and in the backward the product
 //            with CELU'(z) rebuilt from the stored activation (1 for h > 0,
-//            1 + h/alpha otherwise); BF16 (FP32 for dE/dG) stores; then it
-//            releases the accumulator to the MMA warp.
+//            1 + h/alpha otherwise); each 32-row x 16-column chunk goes through
+//            a staging slot in shared memory to a TMA store (BF16, or FP32 for
+//            dE/dG); then it releases the accumulator to the MMA warp.
 // With two accumulators the epilogue of one tile overlaps the MMAs of the next.
 // The N tiles of a row tile are adjacent in the tile order (concurrent CTAs
 // share the row tile of A in L2).
@@ -51,8 +52,11 @@ constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr int kMaxStages = 4;
 // dynamic shared memory limit: the 227 KB per block minus the kernel's static
-// shared memory (barriers, bias and w4 staging) and some headroom
-constexpr int kMaxDynSmem = 232448 - 16384;
+// shared memory (barriers) and some headroom
+constexpr int kMaxDynSmem = 232448 - 2048;
+// output staging of an epilogue warp: slots of 32 rows x 16 columns (BF16 high
+// part at 0 and low part at 1 KB, or FP32), each written out by one TMA store
+constexpr int kSlotBytes = 2048;
 
 struct TcArgs {
   int N, K, n_tile, n_k, tmem_cols, stages, nets;
@@ -76,6 +80,7 @@ struct TcArgs {
   // skips the N tiles with none of them
   const uint32_t* kmask;
   const uint32_t* nmask;
+  int n_slot;            // output staging slots per epilogue warp (1 or 2)
 };
 
 // which N tile of a row tile the last backward layer computes (all without nmask)
@@ -87,17 +92,59 @@ __device__ __forceinline__ bool ntile_live(const TcArgs& g, int m0, int n0) {
   return ((m >> a) & span) != 0u;
 }
 
+// One 32-row x 16-column chunk of an epilogue warp's output, through shared
+// memory: every lane writes its row's 16 values into the warp's staging slot,
+// then lane 0 stores the box with TMA (full-line writes, where direct stores of
+// one row per lane would send 32 scattered 32-byte pieces per instruction).
+// OUT: 0 BF16, 1 BF16 high and low parts (to / to2), 2 FP32.
+template <int OUT>
+__device__ __forceinline__ void stage_store(uint8_t* slot, const float (&v)[16], int lane,
+                                            const CUtensorMap* to, const CUtensorMap* to2, int x,
+                                            int y) {
+  if (OUT == 2) {
+    float4* d = reinterpret_cast<float4*>(slot + lane * 64);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  } else {
+    uint32_t wh[8], wl[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      wh[i] = *reinterpret_cast<const uint32_t*>(&h);
+      if (OUT == 1) {
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+        wl[i] = *reinterpret_cast<const uint32_t*>(&l);
+      }
+    }
+    uint4* dh = reinterpret_cast<uint4*>(slot + lane * 32);
+    dh[0] = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    dh[1] = make_uint4(wh[4], wh[5], wh[6], wh[7]);
+    if (OUT == 1) {
+      uint4* dl = reinterpret_cast<uint4*>(slot + 1024 + lane * 32);
+      dl[0] = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+      dl[1] = make_uint4(wl[4], wl[5], wl[6], wl[7]);
+    }
+  }
+  fence_async_smem();
+  __syncwarp();
+  if (lane == 0) {
+    tma_store_2d(to, slot, x, y);
+    if (OUT == 1) tma_store_2d(to2, slot + 1024, x, y);
+    bulk_commit();
+  }
+}
+
 template <int EPI, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
           const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb2,
+          const __grid_constant__ CUtensorMap to, const __grid_constant__ CUtensorMap to2,
           TcArgs g) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], done_bar;
   __shared__ uint32_t tmem_base_sh;
-  // per epilogue warp: the bias and output-layer weights of its columns of a tile
-  __shared__ __align__(16) float epi_sh[kEpiWarps][2][128];
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kStages = g.stages;
@@ -105,6 +152,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   const int a_bytes = kBM * kBK * 2, b_bytes = g.n_tile * kBK * 2;
   constexpr int kParts = SPLIT ? 2 : 1;
   const int stage_bytes = kParts * (a_bytes + b_bytes);   // multiple of 1024
+  // after the ring: the epilogue warps' staging slots, then (CELU layers) per
+  // epilogue warp the bias and output-layer weights of its columns of a tile
+  uint8_t* stg = smem + kStages * stage_bytes;
+  float* epi_sh = reinterpret_cast<float*>(stg + kEpiWarps * g.n_slot * kSlotBytes);
   volatile int* abort_flag = &abort_sh;
 
   if (threadIdx.x == 0) {
@@ -216,6 +267,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     // 16-column chunk starting at chunk w / 4
     const int q = warp & 3, half = warp >> 2;
     const float alpha = g.alpha, inv_alpha = 1.f / g.alpha;
+    constexpr int kOut = EPI == kEpiStore ? 2 : SPLIT ? 1 : 0;
+    // BF16 forward layers store straight from registers (measured faster there:
+    // 32 bytes per row and chunk; the split and backward layers gain from the
+    // staged TMA stores)
+    constexpr bool kDirect = !SPLIT && (EPI == kEpiCelu || EPI == kEpiCeluDot);
+    uint8_t* my_slots = stg + warp * g.n_slot * kSlotBytes;
+    float* my_epi = epi_sh + warp * 2 * 128;
+    int n_st = 0;   // chunks this warp has stored
     int j = 0;
     constexpr int kMaxChunks = 256 / 32;   // 16-column chunks of one warp per tile
     for (int t = blockIdx.x; t < T; t += gridDim.x) {
@@ -227,27 +286,31 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       // the backward's stored activations do not depend on the MMAs: their loads
       // are issued before the wait for the accumulator
       // (the split path also prefetches the low parts)
+      // (the first kPD chunks; each later chunk's load is issued when the chunk
+      // kPD before it has been used, which bounds the registers they hold)
       constexpr bool kPre = (EPI == kEpiMul);
-      uint4 pre[kPre ? kMaxChunks : 1][2];
-      uint4 prel[kPre && SPLIT ? kMaxChunks : 1][2];
-      if (kPre && row_ok) {
-        const size_t oa = (size_t)m * g.ld_aux + (size_t)tl.e * g.aux_net + tl.n0;
-        const __nv_bfloat16* arow = static_cast<const __nv_bfloat16*>(g.aux) + oa;
-        const __nv_bfloat16* lrow = SPLIT ? static_cast<const __nv_bfloat16*>(g.aux2) + oa : nullptr;
-#pragma unroll
-        for (int ci = 0; ci < kMaxChunks; ++ci) {
-          const int c0 = half * 16 + 32 * ci;
-          if (c0 < g.n_tile && tl.n0 + c0 < g.N) {
-            const uint4* src = reinterpret_cast<const uint4*>(arow + c0);
-            pre[ci][0] = src[0];
-            pre[ci][1] = src[1];
-            if (SPLIT) {
-              const uint4* srl = reinterpret_cast<const uint4*>(lrow + c0);
-              prel[ci][0] = srl[0];
-              prel[ci][1] = srl[1];
-            }
+      constexpr int kPD = SPLIT ? 4 : kMaxChunks;
+      uint4 pre[kPre ? kPD : 1][2];
+      uint4 prel[kPre && SPLIT ? kPD : 1][2];
+      const size_t oa = (size_t)m * g.ld_aux + (size_t)tl.e * g.aux_net + tl.n0;
+      const __nv_bfloat16* arow = kPre ? static_cast<const __nv_bfloat16*>(g.aux) + oa : nullptr;
+      const __nv_bfloat16* lrow = (kPre && SPLIT) ? static_cast<const __nv_bfloat16*>(g.aux2) + oa : nullptr;
+      auto fetch_aux = [&](int ci) {
+        const int c0 = half * 16 + 32 * ci;
+        if (kPre && row_ok && c0 < g.n_tile && tl.n0 + c0 < g.N) {
+          const uint4* src = reinterpret_cast<const uint4*>(arow + c0);
+          pre[ci % kPD][0] = src[0];
+          pre[ci % kPD][1] = src[1];
+          if (SPLIT) {
+            const uint4* srl = reinterpret_cast<const uint4*>(lrow + c0);
+            prel[ci % kPD][0] = srl[0];
+            prel[ci % kPD][1] = srl[1];
           }
         }
+      };
+      if (kPre) {
+#pragma unroll
+        for (int ci = 0; ci < kPD; ++ci) fetch_aux(ci);
       }
       // the bias (and output-layer weights) of this warp's columns, also fetched
       // before the wait: lane l holds entries l + 32 i of the warp's 16-column chunks
@@ -264,11 +327,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       }
       if (!mbar_wait(&tfull_bar[ab], (j >> 1) & 1, abort_flag)) break;
       if (EPI == kEpiCelu || EPI == kEpiCeluDot) {
-        __syncwarp();   // the previous tile's reads of epi_sh are done
+        __syncwarp();   // the previous tile's reads of the warp's bias slots are done
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          epi_sh[warp][0][lane + 32 * i] = bpre[i];
-          epi_sh[warp][1][lane + 32 * i] = wpre[i];
+          my_epi[lane + 32 * i] = bpre[i];
+          my_epi[128 + lane + 32 * i] = wpre[i];
         }
         __syncwarp();
       }
@@ -282,19 +345,19 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
         const int n = tl.n0 + c0;
         float v[16];
         tmem_ld16(trow + (uint32_t)c0, v);
-        if (n >= g.N || !row_ok) continue;
+        if (n >= g.N) continue;
         if (EPI == kEpiCelu || EPI == kEpiCeluDot) {
           float b[16];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const float4 t4 = *reinterpret_cast<const float4*>(&epi_sh[warp][0][ci * 16 + 4 * k]);
+            const float4 t4 = *reinterpret_cast<const float4*>(&my_epi[ci * 16 + 4 * k]);
             b[4 * k] = t4.x; b[4 * k + 1] = t4.y; b[4 * k + 2] = t4.z; b[4 * k + 3] = t4.w;
           }
           float w4[16];
           if (EPI == kEpiCeluDot) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              const float4 t4 = *reinterpret_cast<const float4*>(&epi_sh[warp][1][ci * 16 + 4 * k]);
+              const float4 t4 = *reinterpret_cast<const float4*>(&my_epi[128 + ci * 16 + 4 * k]);
               w4[4 * k] = t4.x; w4[4 * k + 1] = t4.y; w4[4 * k + 2] = t4.z; w4[4 * k + 3] = t4.w;
             }
           }
@@ -310,18 +373,12 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
               v[i] = h;   // CELU' is rebuilt from h where it is needed
             }
           }
-          const size_t o = (size_t)m * g.ldo + (size_t)tl.e * g.out_net + n;
-          if (SPLIT)
-            store_split16(static_cast<__nv_bfloat16*>(g.out) + o, static_cast<__nv_bfloat16*>(g.out2) + o, v);
-          else
-            store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + o, v);
         } else if (EPI == kEpiMul) {
           // aux holds the layer's stored activation h = CELU(z): CELU'(z) = 1 for h > 0,
           // 1 + h / alpha otherwise (exp(z/alpha) = 1 + h/alpha on that branch)
           float a[16];
-          const size_t o = (size_t)m * g.ldo + (size_t)tl.e * g.out_net + n;
           {
-            const uint32_t* w = reinterpret_cast<const uint32_t*>(pre[kPre ? ci : 0]);
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(pre[kPre ? ci % kPD : 0]);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
@@ -331,7 +388,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           }
           if (SPLIT) {
             // the stored activation h = hi + lo (about 16 significant bits)
-            const uint32_t* wl = reinterpret_cast<const uint32_t*>(prel[kPre && SPLIT ? ci : 0]);
+            const uint32_t* wl = reinterpret_cast<const uint32_t*>(prel[kPre && SPLIT ? ci % kPD : 0]);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wl[i]));
@@ -339,17 +396,30 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
               a[2 * i + 1] += f.y;
             }
           }
+          if (ci + kPD < kMaxChunks) fetch_aux(ci + kPD);   // the slot just read is free
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] *= (a[i] > 0.f) ? 1.f : fmaf(a[i], inv_alpha, 1.f);
-          if (SPLIT)
-            store_split16(static_cast<__nv_bfloat16*>(g.out) + o, static_cast<__nv_bfloat16*>(g.out2) + o, v);
-          else
-            store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + o, v);
-        } else {
-          float4* o = reinterpret_cast<float4*>(static_cast<float*>(g.out) + (size_t)m * g.ldo + n);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
         }
+        if (kDirect && !row_ok) continue;   // bounds-checked build only
+        if (!row_ok) {   // bounds-checked build only: a row past the segments stays zero
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        }
+        if (kDirect) {
+          store_bf16x16(static_cast<__nv_bfloat16*>(g.out) + (size_t)m * g.ldo +
+                            (size_t)tl.e * g.out_net + n, v);
+          continue;
+        }
+        // the chunk through the next staging slot, once the store that last used
+        // it has read it
+        uint8_t* slot = my_slots + (n_st % g.n_slot) * kSlotBytes;
+        if (lane == 0) {
+          if (g.n_slot == 2) bulk_wait_read<1>();
+          else bulk_wait_read<0>();
+        }
+        __syncwarp();
+        stage_store<kOut>(slot, v, lane, &to, &to2, tl.e * g.out_net + n, tl.m0 + q * 32);
+        ++n_st;
       }
       // the two warps of a row each add their half of the output-layer dot product
       // (e_row starts at zero; a sum of two terms does not depend on their order)
@@ -359,6 +429,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       if (lane == 0) mbar_arrive(&tempty_bar[ab]);
       ++j;
     }
+    if (lane == 0) bulk_wait_all();   // every output store has completed
   }
   tc_fence_before();
   __syncthreads();
@@ -387,6 +458,7 @@ __global__ void k_wait_probe(int* status, unsigned limit) {
 // ---------------------------------------------------------------- host side
 struct TcGemmPlan {
   CUtensorMap ta, tb, ta2, tb2;   // ta2 / tb2: low parts (split path; copies of ta / tb otherwise)
+  CUtensorMap to, to2;            // output (32-row x 16-column boxes); to2: low parts of a split output
   TcArgs a;
   dim3 grid;
   size_t smem;
@@ -513,6 +585,14 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
       p.ta2 = p.ta;
       p.tb2 = p.tb;
     }
+    // the output: [row_cap][ldo] (FP32 dE/dG for the last layer, BF16 otherwise)
+    const bool out_fp32 = (l.epi == kEpiStore);
+    if (!make_map_2d(&p.to, l.out, out_fp32, (uint64_t)l.ldo, R, (uint64_t)l.ldo, 16, 32) ||
+        !make_map_2d(&p.to2, (split && !out_fp32) ? l.out_lo : l.out, out_fp32, (uint64_t)l.ldo, R,
+                     (uint64_t)l.ldo, 16, 32)) {
+      delete st;
+      return NNP_ERR_CUDA;
+    }
     TcArgs& a = p.a;
     a.N = l.N; a.K = l.K; a.n_tile = nt; a.n_k = (l.K + kBK - 1) / kBK;
     a.tmem_cols = tmem_cols_for(nt);
@@ -534,17 +614,28 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     // (the split path holds both parts of A and B per stage; it takes one CTA per
     // SM where two would leave each CTA fewer than two stages)
     const size_t stage_bytes = (size_t)(split ? 2 : 1) * (kBM * kBK * 2 + nt * kBK * 2);
-    auto stages_for = [&](int c) {
+    // besides the ring: the epilogue warps' staging slots and, for the CELU
+    // layers, their bias and output-layer weight slots
+    const size_t epi_bytes = (l.epi == kEpiCelu || l.epi == kEpiCeluDot) ? kEpiWarps * 2 * 128 * 4 : 0;
+    auto extra = [&](int slots) { return (size_t)kEpiWarps * slots * kSlotBytes + epi_bytes; };
+    auto stages_for = [&](int c, int slots) {
       const size_t budget = std::min((size_t)kMaxDynSmem, (size_t)232448 / c - 2048);
-      const int n = (int)std::min<size_t>(kMaxStages, (budget - 1024) / stage_bytes);
+      if (budget < 1024 + extra(slots) + stage_bytes) return 0;
+      const int n = (int)std::min<size_t>(kMaxStages, (budget - 1024 - extra(slots)) / stage_bytes);
       return std::min(n, std::max(a.n_k, 1));
     };
+    // (the BF16 forward layers store from registers and need no slots)
+    const bool direct = !split && (l.epi == kEpiCelu || l.epi == kEpiCeluDot);
     int ctas = std::min(2, 512 / (2 * a.tmem_cols));
-    if (split && ctas == 2 && stages_for(2) < std::min(2, a.n_k)) ctas = 1;
-    const int stages = stages_for(ctas);
+    if (split && ctas == 2 && stages_for(2, 1) < std::min(2, a.n_k)) ctas = 1;
+    // two staging slots per warp (a chunk's store overlaps the next chunk) unless
+    // that would cost a ring stage
+    const int slots = direct ? 0 : stages_for(ctas, 2) >= stages_for(ctas, 1) ? 2 : 1;
+    const int stages = stages_for(ctas, slots);
     if (stages < 1) { delete st; return NNP_ERR_UNSUPPORTED; }
     a.stages = stages;
-    size_t sm = (size_t)stages * stage_bytes + 1024;
+    a.n_slot = slots;
+    size_t sm = (size_t)stages * stage_bytes + 1024 + extra(slots);
     const size_t floor_sm = 232448 / (size_t)(ctas + 1) + 1;
     p.smem = sm > floor_sm ? sm : floor_sm;
     if (p.smem > (size_t)kMaxDynSmem) { delete st; return NNP_ERR_UNSUPPORTED; }
@@ -622,7 +713,7 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
       while (grid.x > 1 && ntn > 1 && gcd((int)grid.x, ntn) != 1) --grid.x;
     }
 #define NNP_TC_LAUNCH(EPI_, SPLIT_) \
-  k_gemm_tc<EPI_, SPLIT_><<<grid, kThreads, p.smem, st>>>(p.ta, p.tb, p.ta2, p.tb2, a)
+  k_gemm_tc<EPI_, SPLIT_><<<grid, kThreads, p.smem, st>>>(p.ta, p.tb, p.ta2, p.tb2, p.to, p.to2, a)
     if (s->split) {
       switch (a.epi) {
         case kEpiCelu: NNP_TC_LAUNCH(kEpiCelu, true); break;

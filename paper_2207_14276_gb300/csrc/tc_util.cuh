@@ -71,6 +71,27 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// 2D tensor store from shared memory, completion tracked by the issuing thread's
+// bulk async-groups (commit with bulk_commit, wait with bulk_wait_*)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's store groups still read shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// wait until every store group of this thread has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy shared-memory writes of this thread -> visible to the async proxy (TMA)
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   uint64_t d = 0;
@@ -228,6 +249,24 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 3D bf16 map: dims (d0 innermost, d1, d2), strides in elements for d1 and d2,
 // box (box0, b1, b2) with box0 * 2 bytes equal to the swizzle span
+// 2D map of a row-major [d1][d0] array (row stride ld elements) with a box of
+// box0 columns x box1 rows, no swizzle (epilogue stores from shared memory)
+inline bool make_map_2d(CUtensorMap* m, const void* base, bool fp32, uint64_t d0, uint64_t d1,
+                        uint64_t ld, uint32_t box0, uint32_t box1) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const uint64_t esz = fp32 ? 4 : 2;
+  cuuint64_t dims[2] = {d0, d1};
+  cuuint64_t strides[1] = {ld * esz};
+  cuuint32_t box[2] = {box0, box1};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 inline bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t st1,
               uint64_t st2, uint32_t b1, uint32_t b2, uint32_t box0 = 64,
               CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {

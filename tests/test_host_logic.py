@@ -176,3 +176,26 @@ def test_cell_grid_never_exceeds_the_arena_capacity():
     L.nnp_debug_cell_grid(arr, ctypes.c_float(5.2), 100000, nc, ctypes.byref(cells))
     assert [nc[0], nc[1], nc[2]] == [19, 19, 19]
     assert L.nnp_debug_cell_grid(arr, ctypes.c_float(0.0), 10, nc, ctypes.byref(cells)) != 0
+
+
+def test_gemm_bytes_and_binding_ceiling():
+    """Compulsory bytes of the layer GEMMs, and the roofline entry picks the
+    ceiling that binds: B2 on the split path moves 2.25 GB per 100k atoms, more
+    time at 6.78 TB/s than its 78.6 GFLOP at a third of 1.89 PFLOP/s."""
+    import bench
+    s8 = bench.synth.model_spec("ani7x8")
+    n = 100000
+    b2 = bench.gemm_bytes("mlp_b2", s8, n, "fp32_split")
+    assert b2 == pytest.approx(n * (8 * 192 * 4 + 2 * 8 * 256 * 4))
+    assert bench.gemm_bytes("mlp_b2", s8, n, "bf16") == pytest.approx(b2 / 2)
+    assert bench.gemm_bytes("mlp_b1", s8, n, "fp32_split", (1.0, 0.5)) == pytest.approx(
+        n * (8 * 256 * 4 + 1008 * 0.5 * 4))
+    assert bench.gemm_bytes("aev_bwd", s8, n, "fp32_split") is None
+    peaks = {"hbm_gbs": 6780.0, "bf16_tflops": 1888.8}
+    r = bench.roofline({"mlp_b2": (0.5, 1)}, s8, (60.0, 17.0), n, "fp32_split", peaks, "measured",
+                       "solvated100k")
+    assert r["bound"] == "hbm" and r["kernel"] == "mlp_b2"
+    assert r["achieved"] == pytest.approx(b2 / 0.5e-3 / 1e9)
+    assert set(r["ceilings"]) == {"tensor", "hbm"}
+    assert r["ceilings"]["tensor"]["frac"] < r["frac"]
+
