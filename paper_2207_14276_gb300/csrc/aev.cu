@@ -400,7 +400,7 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
       const int same = (s == u);
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
       const int fb = ac.acol[q];
-      const float inv_cu = 1.f / (float)max(cu, 1);
+      const float inv_cu = rcp_approx((float)max(cu, 1));   // decode corrects one step either way
       float acc[32];
 #pragma unroll
       for (int f = 0; f < 32; ++f) acc[f] = 0.f;
@@ -501,13 +501,16 @@ __device__ __forceinline__ void radial_edge_bwd(const Ws& ws, const AevConst& ac
   const Geo g = pair_geo(xi, xj, d);
   float fc, dfc;
   fcut_both(g.r, ac.rc_r, inv_rc_r, &fc, &dfc);
-  float dEdR = 0.f;
+  // dE/dR = sum_r g_r e_r (-2 eta x_r f_c + f_c') = f_c (-2 eta) sum_r g_r e_r x_r + f_c' sum_r g_r e_r
+  float sge = 0.f, sgex = 0.f;
 #pragma unroll
   for (int r = 0; r < kNR; ++r) {
     const float x = g.r - ac.shf_r[r];
-    const float e = fast_exp2(cr_ * x * x);
-    dEdR = fmaf(gs[r], e * fmaf(-2.f * ac.eta_r * x, fc, dfc), dEdR);
+    const float ge = gs[r] * fast_exp2(cr_ * x * x);
+    sge += ge;
+    sgex = fmaf(ge, x, sgex);
   }
+  const float dEdR = fmaf(fc * (-2.f * ac.eta_r), sgex, dfc * sge);
   const float sc = dEdR * rcp_approx(g.r);
   const float gx = sc * g.dx, gy = sc * g.dy, gz = sc * g.dz;
   atomicAdd(&ws.f_pos[j], make_float4(-gx, -gy, -gz, 0.f));
@@ -778,8 +781,8 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
         cur = bl;
         const int4 g4 = bt_geo[bl];
         os = g4.x; cs = g4.y; ou = g4.z; cu = g4.w & 0xffff; same = (g4.w >> 16) & 1;
-        inv_cs = 1.f / (float)max(cs, 1);
-        inv_cu = 1.f / (float)max(cu, 1);
+        inv_cs = rcp_approx((float)max(cs, 1));
+        inv_cu = rcp_approx((float)max(cu, 1));   // decode corrects one step either way
         gblk = gall + (g4.w >> 17) * 8;
       }
       int j, k;
@@ -937,8 +940,8 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
         cur = bl;
         const int4 g4 = bt_geo[bl];
         os = g4.x; cs = g4.y; ou = g4.z; cu = g4.w & 0xffff; same = (g4.w >> 16) & 1;
-        inv_cs = 1.f / (float)max(cs, 1);
-        inv_cu = 1.f / (float)max(cu, 1);
+        inv_cs = rcp_approx((float)max(cs, 1));
+        inv_cu = rcp_approx((float)max(cu, 1));   // decode corrects one step either way
       }
       int j, k;
       decode_pair_diag(t - bt_start[bl], same, cs, cu, inv_cs, inv_cu, &j, &k);
