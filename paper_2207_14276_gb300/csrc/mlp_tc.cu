@@ -81,6 +81,7 @@ struct TcArgs {
   const uint32_t* kmask;
   const uint32_t* nmask;
   int n_slot;            // output staging slots per epilogue warp (1 or 2)
+  int aux_tma;           // kEpiMul, split path: the stored activation's boxes come by TMA
 };
 
 // which N tile of a row tile the last backward layer computes (all without nmask)
@@ -135,15 +136,19 @@ __device__ __forceinline__ void stage_store(uint8_t* slot, const float (&v)[16],
   }
 }
 
-template <int EPI, bool SPLIT>
+// AUXT (kEpiMul on the split path with TcArgs::aux_tma set): the stored
+// activation comes by TMA into shared memory instead of register prefetches
+template <int EPI, bool SPLIT, bool AUXT = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
           const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb2,
           const __grid_constant__ CUtensorMap to, const __grid_constant__ CUtensorMap to2,
+          const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tx2,
           TcArgs g) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], done_bar;
+  __shared__ __align__(8) uint64_t aux_bar[kEpiWarps];   // per epilogue warp: its TMA'd aux boxes
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -156,6 +161,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   // epilogue warp the bias and output-layer weights of its columns of a tile
   uint8_t* stg = smem + kStages * stage_bytes;
   float* epi_sh = reinterpret_cast<float*>(stg + kEpiWarps * g.n_slot * kSlotBytes);
+  // (kEpiMul with aux_tma) per epilogue warp: its chunks of the stored activation,
+  // 2 KB each (high part at 0, low part at 1 KB, 32 rows x 16 columns)
+  const int aux_chunks = (g.n_tile / 16 + 1) / 2;
+  uint8_t* aux_sm = stg + kEpiWarps * g.n_slot * kSlotBytes;
   volatile int* abort_flag = &abort_sh;
 
   if (threadIdx.x == 0) {
@@ -168,6 +177,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       mbar_init(&tempty_bar[i], kEpiWarps);
     }
     mbar_init(&done_bar, 1);
+    for (int i = 0; i < kEpiWarps; ++i) mbar_init(&aux_bar[i], 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -295,9 +305,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       const size_t oa = (size_t)m * g.ld_aux + (size_t)tl.e * g.aux_net + tl.n0;
       const __nv_bfloat16* arow = kPre ? static_cast<const __nv_bfloat16*>(g.aux) + oa : nullptr;
       const __nv_bfloat16* lrow = (kPre && SPLIT) ? static_cast<const __nv_bfloat16*>(g.aux2) + oa : nullptr;
+      constexpr bool aux_tma = SPLIT && kPre && AUXT;
+      uint8_t* my_aux = aux_sm + warp * aux_chunks * 2048;
       auto fetch_aux = [&](int ci) {
         const int c0 = half * 16 + 32 * ci;
-        if (kPre && row_ok && c0 < g.n_tile && tl.n0 + c0 < g.N) {
+        if (kPre && !aux_tma && row_ok && c0 < g.n_tile && tl.n0 + c0 < g.N) {
           const uint4* src = reinterpret_cast<const uint4*>(arow + c0);
           pre[ci % kPD][0] = src[0];
           pre[ci % kPD][1] = src[1];
@@ -312,6 +324,26 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
 #pragma unroll
         for (int ci = 0; ci < kPD; ++ci) fetch_aux(ci);
       }
+      if (aux_tma && lane == 0) {
+        // this tile's boxes of the stored activation (high and low parts) into
+        // the warp's buffer; the warp's reads of the previous tile's boxes are
+        // done (it passed the __syncwarp before releasing that accumulator)
+        fence_async_smem();
+        unsigned bytes = 0;
+        for (int ci = 0; ci < aux_chunks; ++ci) {
+          const int c0 = half * 16 + 32 * ci;
+          if (c0 < g.n_tile && tl.n0 + c0 < g.N) bytes += 2048;
+        }
+        mbar_expect_tx(&aux_bar[warp], bytes);
+        for (int ci = 0; ci < aux_chunks; ++ci) {
+          const int c0 = half * 16 + 32 * ci;
+          if (c0 < g.n_tile && tl.n0 + c0 < g.N) {
+            const int x = tl.e * g.aux_net + tl.n0 + c0, y = tl.m0 + q * 32;
+            tma_load_2d(my_aux + ci * 2048, &tx, &aux_bar[warp], x, y);
+            tma_load_2d(my_aux + ci * 2048 + 1024, &tx2, &aux_bar[warp], x, y);
+          }
+        }
+      }
       // the bias (and output-layer weights) of this warp's columns, also fetched
       // before the wait: lane l holds entries l + 32 i of the warp's 16-column chunks
       float bpre[4] = {0.f, 0.f, 0.f, 0.f}, wpre[4] = {0.f, 0.f, 0.f, 0.f};
@@ -325,7 +357,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           }
         }
       }
-      if (!mbar_wait(&tfull_bar[ab], (j >> 1) & 1, abort_flag)) break;
+      if (!mbar_wait(&tfull_bar[ab], (j >> 1) & 1, abort_flag)) {
+        if (aux_tma) mbar_drain(&aux_bar[warp], j & 1);   // the boxes in flight land first
+        break;
+      }
+      if (aux_tma && !mbar_wait(&aux_bar[warp], j & 1, abort_flag)) {
+        mbar_drain(&aux_bar[warp], j & 1);
+        break;
+      }
       if (EPI == kEpiCelu || EPI == kEpiCeluDot) {
         __syncwarp();   // the previous tile's reads of the warp's bias slots are done
 #pragma unroll
@@ -377,7 +416,19 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           // aux holds the layer's stored activation h = CELU(z): CELU'(z) = 1 for h > 0,
           // 1 + h / alpha otherwise (exp(z/alpha) = 1 + h/alpha on that branch)
           float a[16];
-          {
+          if (aux_tma) {   // the boxes in shared memory: this lane's row, 32 bytes per part
+            const uint4* sh = reinterpret_cast<const uint4*>(my_aux + ci * 2048 + lane * 32);
+            const uint4* sl = reinterpret_cast<const uint4*>(my_aux + ci * 2048 + 1024 + lane * 32);
+            const uint4 q4[4] = {sh[0], sh[1], sl[0], sl[1]};
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(q4);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+              const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[8 + i]));
+              a[2 * i] = f.x + fl.x;
+              a[2 * i + 1] = f.y + fl.y;
+            }
+          } else {
             const uint32_t* w = reinterpret_cast<const uint32_t*>(pre[kPre ? ci % kPD : 0]);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -386,7 +437,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
               a[2 * i + 1] = f.y;
             }
           }
-          if (SPLIT) {
+          if (SPLIT && !aux_tma) {
             // the stored activation h = hi + lo (about 16 significant bits)
             const uint32_t* wl = reinterpret_cast<const uint32_t*>(prel[kPre && SPLIT ? ci % kPD : 0]);
 #pragma unroll
@@ -459,6 +510,7 @@ __global__ void k_wait_probe(int* status, unsigned limit) {
 struct TcGemmPlan {
   CUtensorMap ta, tb, ta2, tb2;   // ta2 / tb2: low parts (split path; copies of ta / tb otherwise)
   CUtensorMap to, to2;            // output (32-row x 16-column boxes); to2: low parts of a split output
+  CUtensorMap tx, tx2;            // stored activation of a split kEpiMul layer (same boxes)
   TcArgs a;
   dim3 grid;
   size_t smem;
@@ -568,7 +620,14 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
   for (const L& l : layers) {
     TcGemmPlan p{};
     const bool single = (l.epi == kEpiCeluDot);
-    const int nt = pick_n_tile(l.N, row_tiles * l.nets, single, sms);
+    int nt = pick_n_tile(l.N, row_tiles * l.nets, single, sms);
+    // wide split backward layers that multiply by CELU' (N >= 256): half-width N
+    // tiles, so that the ring, the output slots and the TMA'd boxes of the stored
+    // activation fit in shared memory together (measured: B2 of the 8-network
+    // model 0.524 -> 0.401 ms; at N = 192 the narrower tiles cost more than the
+    // loads gain, 0.326 -> 0.335 ms, and B3 keeps its register prefetch)
+    const bool aux_tma = split && l.epi == kEpiMul && l.N % 32 == 0 && l.N >= 256 && l.N / 2 <= 256;
+    if (aux_tma) nt = l.N / 2;
     if (nt % 16 != 0 || nt > 256 || (single && nt < l.N)) { delete st; return NNP_ERR_UNSUPPORTED; }
     if (!make_map(&p.ta, l.A, l.a_d0, l.a_d1, R, l.a_st1, l.a_st2, 1, kBM) ||
         !make_map(&p.tb, l.B, l.b_d0, l.b_d1, l.b_d2, l.b_d0, l.b_d0 * l.b_d1, (uint32_t)nt, 1)) {
@@ -585,6 +644,13 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
       p.ta2 = p.ta;
       p.tb2 = p.tb;
     }
+    if (aux_tma) {
+      if (!make_map_2d(&p.tx, l.aux, false, (uint64_t)l.ld_aux, R, (uint64_t)l.ld_aux, 16, 32) ||
+          !make_map_2d(&p.tx2, l.aux_lo, false, (uint64_t)l.ld_aux, R, (uint64_t)l.ld_aux, 16, 32)) {
+        delete st;
+        return NNP_ERR_CUDA;
+      }
+    }
     // the output: [row_cap][ldo] (FP32 dE/dG for the last layer, BF16 otherwise)
     const bool out_fp32 = (l.epi == kEpiStore);
     if (!make_map_2d(&p.to, l.out, out_fp32, (uint64_t)l.ldo, R, (uint64_t)l.ldo, 16, 32) ||
@@ -592,6 +658,10 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
                      (uint64_t)l.ldo, 16, 32)) {
       delete st;
       return NNP_ERR_CUDA;
+    }
+    if (!aux_tma) {   // unused by the kernel, but passed: any valid map
+      p.tx = p.to;
+      p.tx2 = p.to2;
     }
     TcArgs& a = p.a;
     a.N = l.N; a.K = l.K; a.n_tile = nt; a.n_k = (l.K + kBK - 1) / kBK;
@@ -616,7 +686,8 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     const size_t stage_bytes = (size_t)(split ? 2 : 1) * (kBM * kBK * 2 + nt * kBK * 2);
     // besides the ring: the epilogue warps' staging slots and, for the CELU
     // layers, their bias and output-layer weight slots
-    const size_t epi_bytes = (l.epi == kEpiCelu || l.epi == kEpiCeluDot) ? kEpiWarps * 2 * 128 * 4 : 0;
+    const size_t epi_bytes = (l.epi == kEpiCelu || l.epi == kEpiCeluDot) ? kEpiWarps * 2 * 128 * 4
+                             : aux_tma ? (size_t)kEpiWarps * ((nt / 16 + 1) / 2) * 2048 : 0;
     auto extra = [&](int slots) { return (size_t)kEpiWarps * slots * kSlotBytes + epi_bytes; };
     auto stages_for = [&](int c, int slots) {
       const size_t budget = std::min((size_t)kMaxDynSmem, (size_t)232448 / c - 2048);
@@ -635,6 +706,7 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     if (stages < 1) { delete st; return NNP_ERR_UNSUPPORTED; }
     a.stages = stages;
     a.n_slot = slots;
+    a.aux_tma = aux_tma ? 1 : 0;
     size_t sm = (size_t)stages * stage_bytes + 1024 + extra(slots);
     const size_t floor_sm = 232448 / (size_t)(ctas + 1) + 1;
     p.smem = sm > floor_sm ? sm : floor_sm;
@@ -644,10 +716,11 @@ int mlp_tc_prepare(const MlpDims& md, const MlpWeights& mw, const MlpBufs& mb, i
     p.stage_id = l.stage;
     st->plans.push_back(p);
   }
-  const void* fns[8] = {(const void*)k_gemm_tc<kEpiCelu, false>, (const void*)k_gemm_tc<kEpiCeluDot, false>,
+  const void* fns[9] = {(const void*)k_gemm_tc<kEpiCelu, false>, (const void*)k_gemm_tc<kEpiCeluDot, false>,
                         (const void*)k_gemm_tc<kEpiMul, false>, (const void*)k_gemm_tc<kEpiStore, false>,
                         (const void*)k_gemm_tc<kEpiCelu, true>, (const void*)k_gemm_tc<kEpiCeluDot, true>,
-                        (const void*)k_gemm_tc<kEpiMul, true>, (const void*)k_gemm_tc<kEpiStore, true>};
+                        (const void*)k_gemm_tc<kEpiMul, true>, (const void*)k_gemm_tc<kEpiStore, true>,
+                        (const void*)k_gemm_tc<kEpiMul, true, true>};
   for (const void* fn : fns)
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess) {
       delete st;
@@ -713,12 +786,18 @@ int launch_mlp_tc(const Ws& ws, const MlpDims& md, const MlpWeights& mw, const M
       while (grid.x > 1 && ntn > 1 && gcd((int)grid.x, ntn) != 1) --grid.x;
     }
 #define NNP_TC_LAUNCH(EPI_, SPLIT_) \
-  k_gemm_tc<EPI_, SPLIT_><<<grid, kThreads, p.smem, st>>>(p.ta, p.tb, p.ta2, p.tb2, p.to, p.to2, a)
+  k_gemm_tc<EPI_, SPLIT_><<<grid, kThreads, p.smem, st>>>(p.ta, p.tb, p.ta2, p.tb2, p.to, p.to2, p.tx, p.tx2, a)
     if (s->split) {
       switch (a.epi) {
         case kEpiCelu: NNP_TC_LAUNCH(kEpiCelu, true); break;
         case kEpiCeluDot: NNP_TC_LAUNCH(kEpiCeluDot, true); break;
-        case kEpiMul: NNP_TC_LAUNCH(kEpiMul, true); break;
+        case kEpiMul:
+          if (a.aux_tma)
+            k_gemm_tc<kEpiMul, true, true><<<grid, kThreads, p.smem, st>>>(p.ta, p.tb, p.ta2, p.tb2, p.to,
+                                                                            p.to2, p.tx, p.tx2, a);
+          else
+            NNP_TC_LAUNCH(kEpiMul, true);
+          break;
         default: NNP_TC_LAUNCH(kEpiStore, true); break;
       }
     } else {
