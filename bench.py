@@ -138,6 +138,13 @@ def recorded_traffic(stage, workload):
     return None
 
 
+# N tile width of the last backward layer by network path (csrc/mlp_tc.cu: on
+# the split path 128 wherever the AEV width is a multiple of 128); the layer
+# computes the tiles with a live slice
+def b1_n_tile(path, Dp):
+    return 128 if path == "fp32_split" and Dp % 128 == 0 else 256
+
+
 def sparse_fractions(masks, Dp, n_tile=256):
     """(fraction of the AEV's 64-column K slices the first layer processes, fraction
     of the last backward layer's N columns it computes) from the tile masks:
@@ -737,7 +744,7 @@ def run_ours(args):
     clk = clocks.summary(t0, t1)
     path = pot.network_path()
     Dp = (spec.widths[0] + 63) // 64 * 64
-    sparse = sparse_fractions(pot.tile_masks() if path != "fp32_simt" else None, Dp)
+    sparse = sparse_fractions(pot.tile_masks() if path != "fp32_simt" else None, Dp, b1_n_tile(path, Dp))
     roof = roofline(stages, spec, counts, n_eval, path, peaks, peak_src, args.workload, sparse)
 
     # end to end through the host entry point (pinned host buffers, copies inside)
@@ -799,7 +806,7 @@ def run_ours(args):
                   "latency_ms": {"p50": float(np.percentile(b_ms, 50)),
                                  "p99": float(np.percentile(b_ms, 99))},
                   "roofline": roofline(b_stages, spec, counts, n_eval, "bf16", peaks, peak_src,
-                                       args.workload, sparse_fractions(pb.tile_masks(), Dp)),
+                                       args.workload, sparse_fractions(pb.tile_masks(), Dp, b1_n_tile("bf16", Dp))),
                   "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in b_stages.items()
                                          if v[1]}}
         if errors is not None:
