@@ -298,6 +298,21 @@ int nnp_sync_status(nnp_handle* h, void* stream);
 /* Length of the atomic environment vector. */
 int nnp_aev_dim(const nnp_handle* h);
 
+/* Deterministic mode (off by default): every energy and force call of the handle
+ * returns bitwise identical energies, forces and virials for identical inputs.
+ * The atoms of each cell are ordered by input index and the AEV rows of each
+ * species by packed position (both otherwise follow atomic counters); every
+ * force term is written to its own slot (per centre and neighbour-list entry)
+ * and a gather sums them in list order, energies and virials are summed over
+ * each system's atoms in a fixed order, and the lanes of a warp add into the
+ * shared-memory accumulators one after the other.  For catching races: a
+ * result that changes between repeated calls in this mode is a bug.  Costs
+ * extra memory ((cap_r + cap_a + 1) float4 and 10 doubles per atom) and time.
+ * Not covered: the force VJP, and on the FP32 FMA path the ensembles' six-GEMM
+ * chain (its output-layer dot products add partial sums atomically; the fused
+ * kernel of one-network models is covered).  Takes effect from the next call. */
+int nnp_set_deterministic(nnp_handle* h, int enable);
+
 /* ---------------------------------------------------------------- build variants
  * The library also builds as libnnp_debug.so with index checks in its kernels
  * (the neighbour lists' entries and the cells they come from, the packed

@@ -51,7 +51,7 @@ EXPORTS = (
     "nnp_n_weights", "nnp_debug_wait_probe", "nnp_set_skin", "nnp_list_stats",
     "nnp_integrate", "nnp_noalloc_max_atoms", "nnp_debug_cell_grid", "nnp_network_path",
     "nnp_set_fused_chain", "nnp_set_fused_aev_l1", "nnp_set_sparse_rows",
-    "nnp_debug_tile_masks", "nnp_build_flags", "nnp_debug_check_index",
+    "nnp_debug_tile_masks", "nnp_build_flags", "nnp_debug_check_index", "nnp_set_deterministic",
 )
 
 
@@ -129,6 +129,7 @@ def lib():
     L.nnp_set_fused_chain.argtypes = [P, i]
     L.nnp_set_fused_aev_l1.argtypes = [P, i]
     L.nnp_set_sparse_rows.argtypes = [P, i]
+    L.nnp_set_deterministic.argtypes = [P, i]
     L.nnp_debug_tile_masks.argtypes = [P, P, P, i, ctypes.POINTER(i)]
     L.nnp_last_launch_count.argtypes = [P]
     L.nnp_last_error.restype = ctypes.c_char_p

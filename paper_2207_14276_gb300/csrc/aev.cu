@@ -496,7 +496,7 @@ template <bool VIR>
 __device__ __forceinline__ void radial_edge_bwd(const Ws& ws, const AevConst& ac, const float4& xi,
                                                 const SysDev& d, int j, const float4& xj,
                                                 const float* gs, float inv_rc_r, float* fi,
-                                                float* vir) {
+                                                float* vir, float4* det_slot) {
   const float cr_ = -ac.eta_r * kLog2e;
   const Geo g = pair_geo(xi, xj, d);
   float fc, dfc;
@@ -513,7 +513,8 @@ __device__ __forceinline__ void radial_edge_bwd(const Ws& ws, const AevConst& ac
   const float dEdR = fmaf(fc * (-2.f * ac.eta_r), sgex, dfc * sge);
   const float sc = dEdR * rcp_approx(g.r);
   const float gx = sc * g.dx, gy = sc * g.dy, gz = sc * g.dz;
-  atomicAdd(&ws.f_pos[j], make_float4(-gx, -gy, -gz, 0.f));
+  if (det_slot) *det_slot = make_float4(-gx, -gy, -gz, 0.f);   // deterministic mode
+  else atomicAdd(&ws.f_pos[j], make_float4(-gx, -gy, -gz, 0.f));
   fi[0] += gx; fi[1] += gy; fi[2] += gz;
   if (VIR) {
     vir[0] -= g.dx * gx; vir[1] -= g.dx * gy; vir[2] -= g.dx * gz;
@@ -628,6 +629,7 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
   const unsigned lane = threadIdx.x & 31;
   const int p = blockIdx.x * kWarps + w;
   if (p >= ws.totals[0]) return;
+  const bool det = ws.fr_det != nullptr;   // deterministic mode
   const int n_copy = 1 << log_r;
   float4* angv = sm4 + (size_t)w * aev_bwd_warp_f4(cap_l, ac.n_pairs, n_copy);
   float4* angf = angv + cap_l;             // fc, dfc
@@ -708,11 +710,13 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
     const float4 xb = jb >= 0 ? ws.xyzq[jb] : xi;
     if (ja >= 0) {
       while (H.off_r[sr + 1] <= ta) ++sr;
-      radial_edge_bwd<VIR>(ws, ac, xi, d, ja, xa, grad + sr * kNR, inv_rc_r, fi, vir);
+      radial_edge_bwd<VIR>(ws, ac, xi, d, ja, xa, grad + sr * kNR, inv_rc_r, fi, vir,
+                           det ? ws.fr_det + (size_t)p * ws.cap_r + ta : nullptr);
     }
     if (jb >= 0) {
       while (H.off_r[sr + 1] <= tb) ++sr;
-      radial_edge_bwd<VIR>(ws, ac, xi, d, jb, xb, grad + sr * kNR, inv_rc_r, fi, vir);
+      radial_edge_bwd<VIR>(ws, ac, xi, d, jb, xb, grad + sr * kNR, inv_rc_r, fi, vir,
+                           det ? ws.fr_det + (size_t)p * ws.cap_r + tb : nullptr);
     }
   }
   // ---- angular triplets, one lane per (j, k) pair, numbered continuously over
@@ -775,7 +779,9 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
     const int t_end = bt_start[b_hi + 1];
     bl = b_lo;
     cur = -1;
-    for (int t = bt_start[b_lo] + (int)lane; t < t_end; t += 32) {
+    // triplet t of the group: its two force terms and their accumulator slots;
+    // false if a bounds check (checked build) rejected its neighbour slots
+    auto triplet = [&](int t, float3& uj, float3& uk, int& aj, int& ak) -> bool {
       while (bt_start[bl + 1] <= t) ++bl;
       if (bl != cur) {
         cur = bl;
@@ -790,17 +796,39 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
       const int tj = os + j, tk = ou + k;
       if (!NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tj, na_tot) ||
           !NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tk, na_tot))
-        continue;
-      float3 uj, uk;
+        return false;
       triplet_bwd<ZETA>(ac, angv[tj], angv[tk], angf[tj], angf[tk], gblk, uj, uk);
       const int cp = (int)lane & (n_copy - 1);
-      const int aj = (tj << log_r) | cp, ak = (tk << log_r) | cp;
-      atomicAdd(accx + aj, uj.x);
-      atomicAdd(accy + aj, uj.y);
-      atomicAdd(accz + aj, uj.z);
-      atomicAdd(accx + ak, uk.x);
-      atomicAdd(accy + ak, uk.y);
-      atomicAdd(accz + ak, uk.z);
+      aj = (tj << log_r) | cp;
+      ak = (tk << log_r) | cp;
+      return true;
+    };
+    if (!det) {
+      for (int t = bt_start[b_lo] + (int)lane; t < t_end; t += 32) {
+        float3 uj, uk;
+        int aj, ak;
+        if (!triplet(t, uj, uk, aj, ak)) continue;
+        atomicAdd(accx + aj, uj.x);
+        atomicAdd(accy + aj, uj.y);
+        atomicAdd(accz + aj, uj.z);
+        atomicAdd(accx + ak, uk.x);
+        atomicAdd(accy + ak, uk.y);
+        atomicAdd(accz + ak, uk.z);
+      }
+    } else {
+      // deterministic mode: the lanes of a pass add one after the other
+      for (int t0 = bt_start[b_lo]; t0 < t_end; t0 += 32) {
+        float3 uj, uk;
+        int aj = 0, ak = 0;
+        const bool act = t0 + (int)lane < t_end && triplet(t0 + (int)lane, uj, uk, aj, ak);
+        for (int l = 0; l < 32; ++l) {
+          if (act && (int)lane == l) {
+            accx[aj] += uj.x; accy[aj] += uj.y; accz[aj] += uj.z;
+            accx[ak] += uk.x; accy[ak] += uk.y; accz[ak] += uk.z;
+          }
+          __syncwarp();
+        }
+      }
     }
     __syncwarp();   // the group's slots are refilled by the next group
   }
@@ -815,7 +843,8 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
     }
     const float4 v = angv[t];
     const int jt = __float_as_int(angf[t].w);
-    if (NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, jt, ws.totals[0]))
+    if (det) ws.fa_det[(size_t)p * ws.cap_a + t] = make_float4(-a.x, -a.y, -a.z, 0.f);
+    else if (NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, jt, ws.totals[0]))
       atomicAdd(&ws.f_pos[jt], make_float4(-a.x, -a.y, -a.z, 0.f));
     fi[0] += a.x; fi[1] += a.y; fi[2] += a.z;
     if (VIR) {
@@ -831,13 +860,19 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
     fi[1] += __shfl_xor_sync(kFull, fi[1], o);
     fi[2] += __shfl_xor_sync(kFull, fi[2], o);
   }
-  if (lane == 0) atomicAdd(&ws.f_pos[p], make_float4(fi[0], fi[1], fi[2], 0.f));
+  if (lane == 0) {
+    if (det) ws.fs_det[p] = make_float4(fi[0], fi[1], fi[2], 0.f);
+    else atomicAdd(&ws.f_pos[p], make_float4(fi[0], fi[1], fi[2], 0.f));
+  }
   if (VIR && d.in.virial) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       float v = vir[k];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-      if (lane == 0) atomicAdd(d.in.virial + k, (double)v);
+      if (lane == 0) {
+        if (det) ws.v_det[(size_t)p * 9 + k] = (double)v;
+        else atomicAdd(d.in.virial + k, (double)v);
+      }
     }
   }
 }
@@ -882,6 +917,7 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
   int* bt_start = reinterpret_cast<int*>(bt_geo + ac.n_pairs);
   const int np = ac.n_pairs;
   const int n_heavy = ws.totals[2];
+  const bool det = ws.fr_det != nullptr;   // deterministic mode
   const float inv_rc_r = 1.f / ac.rc_r, inv_rc_a = 1.f / ac.rc_a;
   for (int h = blockIdx.x; h < n_heavy; h += gridDim.x) {
     const int p = ws.heavy[h];
@@ -927,14 +963,15 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
       while (H.off_r[sr + 1] <= t) ++sr;
       const int j = lr[t];
       if (!NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, j, ws.totals[0])) continue;
-      radial_edge_bwd<VIR>(ws, ac, xi, d, j, ws.xyzq[j], grad + sr * kNR, inv_rc_r, fi, vir);
+      radial_edge_bwd<VIR>(ws, ac, xi, d, j, ws.xyzq[j], grad + sr * kNR, inv_rc_r, fi, vir,
+                           det ? ws.fr_det + (size_t)p * ws.cap_r + t : nullptr);
     }
     const int n_tri = bt_start[np];
     const int cp = w * n_lane + ((int)lane & (n_lane - 1));
     int bl = 0, cur = -1;
     int os = 0, cs = 0, ou = 0, cu = 0, same = 0;
     float inv_cs = 0.f, inv_cu = 0.f;
-    for (int t = tid; t < n_tri; t += kHeavyThreads) {
+    auto triplet = [&](int t, float3& uj, float3& uk, int& aj, int& ak) -> bool {
       while (bt_start[bl + 1] <= t) ++bl;
       if (bl != cur) {
         cur = bl;
@@ -948,16 +985,39 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
       const int tj = os + j, tk = ou + k;
       if (!NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tj, na) ||
           !NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tk, na))
-        continue;
-      float3 uj, uk;
+        return false;
       triplet_bwd<ZETA>(ac, angv[tj], angv[tk], angf[tj], angf[tk], gall + bl * 8, uj, uk);
-      const int aj = tj * n_acc + cp, ak = tk * n_acc + cp;
-      atomicAdd(accx + aj, uj.x);
-      atomicAdd(accy + aj, uj.y);
-      atomicAdd(accz + aj, uj.z);
-      atomicAdd(accx + ak, uk.x);
-      atomicAdd(accy + ak, uk.y);
-      atomicAdd(accz + ak, uk.z);
+      aj = tj * n_acc + cp;
+      ak = tk * n_acc + cp;
+      return true;
+    };
+    if (!det) {
+      for (int t = tid; t < n_tri; t += kHeavyThreads) {
+        float3 uj, uk;
+        int aj, ak;
+        if (!triplet(t, uj, uk, aj, ak)) continue;
+        atomicAdd(accx + aj, uj.x);
+        atomicAdd(accy + aj, uj.y);
+        atomicAdd(accz + aj, uj.z);
+        atomicAdd(accx + ak, uk.x);
+        atomicAdd(accy + ak, uk.y);
+        atomicAdd(accz + ak, uk.z);
+      }
+    } else {
+      // deterministic mode: within a warp the lanes add one after the other (the
+      // warps add into their own copies)
+      for (int t0 = w * 32; t0 < n_tri; t0 += kHeavyThreads) {
+        float3 uj, uk;
+        int aj = 0, ak = 0;
+        const bool act = t0 + (int)lane < n_tri && triplet(t0 + (int)lane, uj, uk, aj, ak);
+        for (int l = 0; l < 32; ++l) {
+          if (act && (int)lane == l) {
+            accx[aj] += uj.x; accy[aj] += uj.y; accz[aj] += uj.z;
+            accx[ak] += uk.x; accy[ak] += uk.y; accz[ak] += uk.z;
+          }
+          __syncwarp();
+        }
+      }
     }
     __syncthreads();
     for (int t = tid; t < na; t += kHeavyThreads) {
@@ -970,7 +1030,8 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
       }
       const float4 v = angv[t];
       const int jt = __float_as_int(angf[t].w);
-      if (NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, jt, ws.totals[0]))
+      if (det) ws.fa_det[(size_t)p * ws.cap_a + t] = make_float4(-a.x, -a.y, -a.z, 0.f);
+      else if (NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, jt, ws.totals[0]))
         atomicAdd(&ws.f_pos[jt], make_float4(-a.x, -a.y, -a.z, 0.f));
       fi[0] += a.x; fi[1] += a.y; fi[2] += a.z;
       if (VIR) {
@@ -999,8 +1060,13 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
     if (tid < 12) {
       float v = 0.f;
       for (int k = 0; k < kHeavyThreads / 32; ++k) v += red[k][tid];
-      if (tid < 3) atomicAdd(reinterpret_cast<float*>(&ws.f_pos[p]) + tid, v);
-      else if (VIR && d.in.virial) atomicAdd(d.in.virial + (tid - 3), (double)v);
+      if (tid < 3) {
+        if (det) reinterpret_cast<float*>(&ws.fs_det[p])[tid] = v;
+        else atomicAdd(reinterpret_cast<float*>(&ws.f_pos[p]) + tid, v);
+      } else if (VIR && d.in.virial) {
+        if (det) ws.v_det[(size_t)p * 9 + (tid - 3)] = (double)v;
+        else atomicAdd(d.in.virial + (tid - 3), (double)v);
+      }
     }
   }
 }

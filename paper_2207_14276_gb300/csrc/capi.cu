@@ -125,6 +125,9 @@ struct nnp_handle {
   // first and last layer GEMMs restricted to them (exact: the rest is zero)
   bool sparse_rows = true;
   bool last_sparse = false;      // the last call ran with sparse rows
+  // deterministic mode: atoms and AEV rows in sorted order, force and energy
+  // contributions in their own slots summed in a fixed order (bitwise repeatable)
+  bool det = false;
   // persistent neighbour lists with a Verlet skin (0: rebuilt on every call)
   float skin = 0.f;
   bool lists_valid = false;   // the lists in the arena belong to list_sig's batch layout
@@ -396,6 +399,16 @@ size_t carve(nnp_handle* h, char* base) {
   ws.atom_e = c.take<float>(rows);
   ws.f_pos = c.take<float4>(n);
   ws.heavy = c.take<int>(n);
+  if (h->det) {
+    ws.fr_det = c.take<float4>(n * h->cap_r);
+    ws.fa_det = c.take<float4>(n * h->cap_a);
+    ws.fs_det = c.take<float4>(n);
+    ws.e_det = c.take<double>(n);
+    ws.v_det = c.take<double>(n * 9);
+  } else {
+    ws.fr_det = ws.fa_det = ws.fs_det = nullptr;
+    ws.e_det = ws.v_det = nullptr;
+  }
   if (h->skin > 0.f) {
     ws.skin_state = c.take<int>(4);
     ws.ref = c.take<float4>(n);
@@ -621,6 +634,11 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
       launches += 4;
     }
     if ((rc = chk("cell lists"))) return rc;
+    if (ws.fr_det) {   // deterministic mode: sorted atoms and rows
+      StageTimer t(h, st, 0);
+      launch_det_order(ws, m.ac.S, st);
+      launches += 2;
+    }
     { StageTimer t(h, st, 1); launch_neighbors(ws, n_in, ac, st); }
     if ((rc = chk("neighbors"))) return rc;
     if (ws.skin_state) ++launches;   // the list refresh
@@ -656,11 +674,13 @@ int enqueue_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, const std::v
     if (!energy_only) {
       StageTimer t(h, st, 9);
       launch_aev_bwd(ws, n_in, ac, any_virial ? 1 : 0, st);
+      if (ws.fr_det) { launch_det_force_gather(ws, n_in, st); ++launches; }
     }
     if ((rc = chk("aev_bwd"))) return rc;
     {
       StageTimer t(h, st, 10);
       launch_finalize_e(ws, n_in, h->mb.e_row, m.md.E, ws.row_cap, m.ebias, st);
+      if (ws.e_det) { launch_det_reduce(ws, any_virial ? 1 : 0, st); ++launches; }
     }
     launches += 2;
   }
@@ -747,6 +767,7 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
     put(&h->fused_chain, sizeof(h->fused_chain));
     put(&h->fused_aev_l1, sizeof(h->fused_aev_l1));
     put(&h->sparse_rows, sizeof(h->sparse_rows));
+    put(&h->det, sizeof(h->det));
     // the kernels read only the first n_sys descriptors of a chunk
     for (const auto& bp : chunks)
       put(&bp, offsetof(BatchParams, sys) + (size_t)bp.n_sys * sizeof(SysIn));
@@ -862,6 +883,7 @@ int nnp_clone(const nnp_handle* src, nnp_handle** out) {
   h->cap_a = src->cap_a;
   h->fused_chain = src->fused_chain;
   h->fused_aev_l1 = src->fused_aev_l1;
+  h->det = src->det;
   if (!alloc_host_words(h)) {
     nnp_destroy(h);
     return fail(NNP_ERR_CUDA, "cudaMallocHost failed");
@@ -1210,6 +1232,10 @@ extern "C" int nnp_force_vjp_batch(nnp_handle* h, int n_sys, const nnp_vjp_syste
   ws.aev_l = nullptr;
   ws.row_mask = nullptr;      // the FP32 chain reads whole rows
   ws.tile_mask = nullptr;
+  // the deterministic mode covers energy and force calls, not the VJP (whose
+  // dual backward adds atomically): the forces here add atomically as well
+  ws.fr_det = ws.fa_det = ws.fs_det = nullptr;
+  ws.e_det = ws.v_det = nullptr;
   h->last_aev_fp32 = true;
   h->last_sparse = false;
   // the force VJP builds its own lists at the cutoffs in the shared buffers:
@@ -1320,6 +1346,17 @@ int nnp_debug_tile_masks(nnp_handle* h, void* stream, uint32_t* out_host, int ma
   const int n = std::min(seg / kRowTile, max_tiles);
   if (n > 0) CU_TRY(cudaMemcpy(out_host, h->ws.tile_mask, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
   *n_tiles = n;
+  return NNP_OK;
+}
+
+int nnp_set_deterministic(nnp_handle* h, int enable) {
+  g_err.clear();
+  if (!h) return fail(NNP_ERR_ARG, "null handle");
+  if (h->det != (enable != 0)) {
+    h->det = enable != 0;
+    h->dirty = true;   // the arena gains or drops the per-contribution buffers
+    h->lists_valid = false;
+  }
   return NNP_OK;
 }
 
@@ -1544,6 +1581,8 @@ size_t noalloc_carve(const Model& m, int n_atoms, char* base, Ws* ws, MlpBufs* m
   ws->atom_e = c.take<float>(rows);
   ws->f_pos = c.take<float4>(n);
   ws->heavy = c.take<int>(n);
+  ws->fr_det = ws->fa_det = ws->fs_det = nullptr;
+  ws->e_det = ws->v_det = nullptr;
   *mb = MlpBufs{};
   if (!mlp_fused_supported(m.md)) {   // the fused kernel needs no activation buffers
     mb->H1 = c.take<float>(rows * E * m.md.h1);

@@ -39,7 +39,9 @@ __global__ void k_finalize(Ws ws, const float* e_row, int E, int e_row_net,
       F[2] = f.z;
     }
     if (d.in.atom_e) d.in.atom_e[local] = (float)Ei;
+    if (ws.e_det) ws.e_det[p] = Ei;   // deterministic mode: summed in order later
   }
+  if (ws.e_det) return;
   // segmented FP64 reduction over the systems present in this warp
   unsigned todo = __ballot_sync(0xffffffffu, live);
   while (todo) {
@@ -95,7 +97,89 @@ __global__ void k_gather_nbrs(Ws ws, int angular, int cap_out, int* out) {
     out[(size_t)gi * cap_out + t] = t < n ? ws.pos_src[lst[t]] : -1;
 }
 
+// deterministic mode: f_pos[j] = j's own term + the terms of j that its
+// neighbours i wrote into their list slots (found by scanning i's list for j:
+// the lists are symmetric), each lane summing its neighbours in list order and
+// the warp combining the lanes in a fixed tree
+__global__ void k_det_force_gather(Ws ws) {
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const unsigned lane = threadIdx.x & 31;
+  if (j >= ws.totals[0]) return;
+  const uint16_t* hj = ws.nb_cnt + (size_t)j * 16;
+  int nr = 0, na = 0;
+  for (int s = 0; s < 8; ++s) { nr += hj[s]; na += hj[8 + s]; }
+  float r[3] = {0.f, 0.f, 0.f}, a[3] = {0.f, 0.f, 0.f};
+  for (int t = lane; t < nr; t += 32) {
+    const int i = ws.nb_r[(size_t)j * ws.cap_r + t];
+    if (!NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, i, ws.totals[0])) continue;
+    const uint16_t* hi = ws.nb_cnt + (size_t)i * 16;
+    int ni = 0;
+    for (int s = 0; s < 8; ++s) ni += hi[s];
+    const int* li = ws.nb_r + (size_t)i * ws.cap_r;
+    for (int u = 0; u < ni; ++u)
+      if (li[u] == j) {
+        const float4 f = ws.fr_det[(size_t)i * ws.cap_r + u];
+        r[0] += f.x; r[1] += f.y; r[2] += f.z;
+        break;
+      }
+  }
+  for (int t = lane; t < na; t += 32) {
+    const int i = ws.nb_a[(size_t)j * ws.cap_a + t];
+    if (!NNP_IN_BOUNDS(ws.status, kSiteBwdNeighbour, i, ws.totals[0])) continue;
+    const uint16_t* hi = ws.nb_cnt + (size_t)i * 16;
+    int ni = 0;
+    for (int s = 0; s < 8; ++s) ni += hi[8 + s];
+    const int* li = ws.nb_a + (size_t)i * ws.cap_a;
+    for (int u = 0; u < ni; ++u)
+      if (li[u] == j) {
+        const float4 f = ws.fa_det[(size_t)i * ws.cap_a + u];
+        a[0] += f.x; a[1] += f.y; a[2] += f.z;
+        break;
+      }
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int k = 0; k < 3; ++k) {
+      r[k] += __shfl_xor_sync(0xffffffffu, r[k], o);
+      a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
+    }
+  if (lane == 0) {
+    const float4 f = ws.fs_det[j];
+    ws.f_pos[j] = make_float4(f.x + (r[0] + a[0]), f.y + (r[1] + a[1]), f.z + (r[2] + a[2]), 0.f);
+  }
+}
+
+// deterministic mode: warp per system, its energy (and virial) summed over its
+// packed positions in a fixed order
+__global__ void k_det_reduce(Ws ws, int want_virial) {
+  const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const unsigned lane = threadIdx.x & 31;
+  if (b >= ws.n_sys) return;
+  const SysDev& d = ws.sys[b];
+  const int beg = d.atom_base, end = d.atom_base + d.n_ml;
+  double e = 0.0;
+  for (int p = beg + (int)lane; p < end; p += 32) e += ws.e_det[p];
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if (lane == 0 && d.in.energy) d.in.energy[0] = e;
+  if (want_virial && d.in.virial)
+    for (int k = 0; k < 9; ++k) {
+      double v = 0.0;
+      for (int p = beg + (int)lane; p < end; p += 32) v += ws.v_det[(size_t)p * 9 + k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) d.in.virial[k] = v;
+    }
+}
+
 }  // namespace
+
+void launch_det_force_gather(const Ws& ws, int n_in, cudaStream_t st) {
+  if (!ws.fr_det || n_in <= 0) return;
+  k_det_force_gather<<<(n_in + 7) / 8, 256, 0, st>>>(ws);
+}
+
+void launch_det_reduce(const Ws& ws, int want_virial, cudaStream_t st) {
+  if (!ws.e_det || ws.n_sys <= 0) return;
+  k_det_reduce<<<(ws.n_sys + 7) / 8, 256, 0, st>>>(ws, want_virial);
+}
 
 void launch_finalize_e(const Ws& ws, int n_in, const float* e_row, int E, int e_row_net,
                        const double* ebias, cudaStream_t st) {

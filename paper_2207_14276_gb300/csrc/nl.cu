@@ -932,4 +932,83 @@ void launch_neighbors(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t s
   }
 }
 
+// ---------------------------------------------------------------- deterministic mode
+namespace {
+
+// one thread per cell: its packed atoms in input order (insertion sort by input
+// index; a cell holds a few atoms), which the binning's atomic counter had
+// placed in arrival order
+__global__ void k_det_cell_sort(Ws ws) {
+  if (!lists_rebuild(ws)) return;
+  const int T = ws.totals[1];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < T; c += gridDim.x * blockDim.x) {
+    const int b = ws.cell_start[c], e = ws.cell_start[c + 1];
+    for (int i = b + 1; i < e; ++i) {
+      const float4 x = ws.xyzq[i];
+      const int src = ws.pos_src[i], sys = ws.pos_sys[i], cell = ws.pos_cell[i];
+      int k = i - 1;
+      while (k >= b && ws.pos_src[k] > src) {
+        ws.xyzq[k + 1] = ws.xyzq[k];
+        ws.pos_src[k + 1] = ws.pos_src[k];
+        ws.pos_sys[k + 1] = ws.pos_sys[k];
+        ws.pos_cell[k + 1] = ws.pos_cell[k];
+        --k;
+      }
+      ws.xyzq[k + 1] = x;
+      ws.pos_src[k + 1] = src;
+      ws.pos_sys[k + 1] = sys;
+      ws.pos_cell[k + 1] = cell;
+    }
+    if (ws.in_pos)
+      for (int i = b; i < e; ++i) ws.in_pos[ws.pos_src[i]] = i;
+  }
+}
+
+// one CTA: the AEV row of every packed atom, species segment by segment in
+// packed order (the binning's atomic counter had assigned them in arrival order)
+__global__ void __launch_bounds__(1024) k_det_slots(Ws ws, int S) {
+  if (!lists_rebuild(ws)) return;
+  __shared__ int next[kMaxSpecies];
+  __shared__ int wcount[32][kMaxSpecies];
+  const int n = ws.totals[0];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid < kMaxSpecies) next[tid] = tid < S ? ws.seg_start[tid] : 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += 1024) {
+    const int p = c0 + tid;
+    const int s = p < n ? __float_as_int(ws.xyzq[p].w) : -1;
+    int rank = 0;
+    for (int q = 0; q < S; ++q) {
+      const unsigned m = __ballot_sync(0xffffffffu, s == q);
+      if (s == q) rank = __popc(m & lanemask_lt());
+      if (lane == 0) wcount[w][q] = __popc(m);
+    }
+    __syncthreads();
+    if (s >= 0 && s < S) {
+      for (int k = 0; k < w; ++k) rank += wcount[k][s];
+      const int slot = next[s] + rank;
+      if (NNP_IN_BOUNDS(ws.status, kSiteAevRow, slot, ws.row_cap)) {
+        ws.pos_slot[p] = slot;
+        ws.in_slot[ws.pos_src[p]] = slot;
+        if (ws.slot_pos) ws.slot_pos[slot] = p;
+      }
+    }
+    __syncthreads();
+    if (tid < S) {
+      int tot = 0;
+      for (int k = 0; k < 32; ++k) tot += wcount[k][tid];
+      next[tid] += tot;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+void launch_det_order(const Ws& ws, int S, cudaStream_t st) {
+  if (!ws.fr_det) return;
+  k_det_cell_sort<<<std::max(1, std::min((ws.cell_cap + 255) / 256, 1024)), 256, 0, st>>>(ws);
+  k_det_slots<<<1, 1024, 0, st>>>(ws, S);
+}
+
 }  // namespace nnp

@@ -173,6 +173,14 @@ struct Ws {
   float4* f_pos;        // [n_in] forces on packed atoms
   int* heavy;           // [n_in] packed positions of the centres the warp-per-centre
                         // AEV backward hands on (count in totals[2])
+  // deterministic mode (null otherwise): the force kernels write every
+  // contribution to its own slot instead of adding it atomically, and fixed-order
+  // gathers and reductions sum them (results bitwise repeatable)
+  float4* fr_det;       // [n_in][cap_r] radial edge term on the neighbour of list slot t
+  float4* fa_det;       // [n_in][cap_a] angular terms on the neighbour of list slot t
+  float4* fs_det;       // [n_in] the centre's own force
+  double* e_det;        // [n_in] atomic energy (FP64), by packed position
+  double* v_det;        // [n_in][9] the centre's virial contribution
   // persistent neighbour lists with a skin (null skin_state: rebuilt every call)
   int* skin_state;      // [4]: max displacement (float bits), forced rebuild, builds, lists valid
   float half_skin;      // rebuild when an atom moved farther than this since the build
@@ -203,6 +211,16 @@ void launch_skin_check(const Ws& ws, const BatchParams& bp, int n_in_chunk, cuda
 // init + prep + setup + bin + scan + scatter of a one-chunk batch in one CTA
 void launch_front(const Ws& ws, const BatchParams& bp, const AevConst& ac, int n_in,
                   cudaStream_t st);
+// deterministic mode (ws.fr_det set): after a list build, the atoms of every cell
+// in input order and the AEV rows of every species in packed order (both are
+// otherwise taken by atomic counters)
+void launch_det_order(const Ws& ws, int S, cudaStream_t st);
+// deterministic mode: f_pos[j] = own term + the terms of j in its neighbours'
+// lists, summed in list order
+void launch_det_force_gather(const Ws& ws, int n_in, cudaStream_t st);
+// deterministic mode: system energies (and virials) summed over their packed
+// positions in order
+void launch_det_reduce(const Ws& ws, int want_virial, cudaStream_t st);
 // ---- aev.cu
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st);
 // sparse rows (ws.row_mask set): zero the slices of each row that its tile reads

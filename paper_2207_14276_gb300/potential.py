@@ -105,6 +105,11 @@ class Potential:
         or as four layer GEMMs."""
         check(lib().nnp_set_fused_chain(self._h, 1 if enable else 0))
 
+    def set_deterministic(self, enable):
+        """Bitwise repeatable energies, forces and virials (sorted atom order,
+        fixed-order sums of per-contribution slots); slower, more memory."""
+        check(lib().nnp_set_deterministic(self._h, 1 if enable else 0))
+
     def set_sparse_rows(self, enable):
         """Tensor-core paths: write and multiply only the live 64-column slices of
         the AEV rows (default on; the result is the same)."""
