@@ -444,23 +444,30 @@ k_aev_fwd(Ws ws, AevConst ac) {
   __shared__ uint8_t pair_su[kMaxSpecies * (kMaxSpecies + 1) / 2];
   const int w = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31;
-  const int p = blockIdx.x * kWarps + w;
   const bool sparse = ws.row_mask != nullptr;
   fill_pair_table(pair_su, ac);
   __syncthreads();
-  if (p >= ws.totals[0]) return;
-  if (!NNP_IN_BOUNDS(ws.status, kSiteAevRow, ws.pos_slot[p], ws.row_cap)) return;
-  const size_t row = (size_t)ws.pos_slot[p] * ac.Dp;
-  float* G = ws.aev + row;
-  uint16_t* Gh = ws.aev_h ? ws.aev_h + row : nullptr;
-  uint16_t* Gl = ws.aev_l ? ws.aev_l + row : nullptr;
-  uint32_t m = 0;
-  aev_centre<ZETA>(ws, ac, p, sm4 + (size_t)w * aev_fwd_warp_f4(ws.cap_a, ws.cap_r), hdrs[w], lane,
-                   pair_su, [&](int f, float v) { put_g(G, Gh, Gl, f, v); }, sparse, &m);
-  if (sparse && lane == 0) {
-    const int slot = ws.pos_slot[p];
-    ws.row_mask[slot] = m;
-    atomicOr(ws.tile_mask + (slot >> 7), m);
+  // persistent: every warp takes the next centre from a counter until none is left
+  // (dense centres do not hold a CTA's other warps' slots, nor pile up in one warp)
+  const int n = ws.totals[0];
+  for (;;) {
+    int p = 0;
+    if (lane == 0) p = atomicAdd(ws.totals + 4, 1);
+    p = __shfl_sync(kFull, p, 0);
+    if (p >= n) break;
+    if (!NNP_IN_BOUNDS(ws.status, kSiteAevRow, ws.pos_slot[p], ws.row_cap)) continue;
+    const size_t row = (size_t)ws.pos_slot[p] * ac.Dp;
+    float* G = ws.aev + row;
+    uint16_t* Gh = ws.aev_h ? ws.aev_h + row : nullptr;
+    uint16_t* Gl = ws.aev_l ? ws.aev_l + row : nullptr;
+    uint32_t m = 0;
+    aev_centre<ZETA>(ws, ac, p, sm4 + (size_t)w * aev_fwd_warp_f4(ws.cap_a, ws.cap_r), hdrs[w], lane,
+                     pair_su, [&](int f, float v) { put_g(G, Gh, Gl, f, v); }, sparse, &m);
+    if (sparse && lane == 0) {
+      const int slot = ws.pos_slot[p];
+      ws.row_mask[slot] = m;
+      atomicOr(ws.tile_mask + (slot >> 7), m);
+    }
   }
 }
 
@@ -621,14 +628,9 @@ __device__ __forceinline__ void triplet_bwd(const AevConst& ac, const float4& vj
 // per-warp shared-memory region is sized for cap_l); a centre with more is
 // appended to ws.heavy (count in totals[2]) for k_aev_bwd_heavy and skipped.
 template <int ZETA, bool VIR>
-__global__ void __launch_bounds__(kWarps * 32, 4)
-k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
-  extern __shared__ float4 sm4[];
-  __shared__ ListHdr hdrs[kWarps];
-  const int w = threadIdx.x >> 5;
-  const unsigned lane = threadIdx.x & 31;
-  const int p = blockIdx.x * kWarps + w;
-  if (p >= ws.totals[0]) return;
+__device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int log_r, int cap_l,
+                                           int p, float4* sm4, ListHdr& H, int w, unsigned lane) {
+  __syncwarp();   // the warp's previous centre is done with its shared memory
   const bool det = ws.fr_det != nullptr;   // deterministic mode
   const int n_copy = 1 << log_r;
   float4* angv = sm4 + (size_t)w * aev_bwd_warp_f4(cap_l, ac.n_pairs, n_copy);
@@ -646,7 +648,6 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
   float4* gall = past_acc + 32;
   int4* bt_geo = reinterpret_cast<int4*>(gall + 8 * n_gall);         // [n_pairs]
   int* bt_start = reinterpret_cast<int*>(bt_geo + ac.n_pairs);       // [n_pairs + 1]
-  ListHdr& H = hdrs[w];
 
   const float4 xi = ws.xyzq[p];
   const SysDev& d = ws.sys[ws.pos_sys[p]];
@@ -874,6 +875,24 @@ k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
         else atomicAdd(d.in.virial + k, (double)v);
       }
     }
+  }
+}
+
+template <int ZETA, bool VIR>
+__global__ void __launch_bounds__(kWarps * 32, 4)
+k_aev_bwd(Ws ws, AevConst ac, int log_r, int cap_l) {
+  extern __shared__ float4 sm4[];
+  __shared__ ListHdr hdrs[kWarps];
+  const int w = threadIdx.x >> 5;
+  const unsigned lane = threadIdx.x & 31;
+  // persistent: every warp takes the next centre from a counter until none is left
+  const int n = ws.totals[0];
+  for (;;) {
+    int p = 0;
+    if (lane == 0) p = atomicAdd(ws.totals + 5, 1);
+    p = __shfl_sync(kFull, p, 0);
+    if (p >= n) break;
+    bwd_centre<ZETA, VIR>(ws, ac, log_r, cap_l, p, sm4, hdrs[w], w, lane);
   }
 }
 
@@ -1252,10 +1271,23 @@ static size_t heavy_smem(const Ws& ws, int n_pairs) {
   return aev_bwd_heavy_smem(ws.cap_a, n_pairs, 1 << heavy_log_n(ws, n_pairs));
 }
 
+// grid of the persistent warp-per-centre kernels: four CTAs per SM at most,
+// fewer for small batches
+static int centre_grid(int n_in) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+  }
+  return std::max(1, std::min((n_in + kWarps - 1) / kWarps, 4 * sms));
+}
+
 void launch_aev_fwd(const Ws& ws, int n_in, const AevConst& ac, cudaStream_t st) {
   if (n_in <= 0) return;
   const size_t sm = aev_fwd_smem(ws);
-  const int grid = (n_in + kWarps - 1) / kWarps;
+  const int grid = centre_grid(n_in);
   if (ac.zeta == 32) k_aev_fwd<32><<<grid, kWarps * 32, sm, st>>>(ws, ac);
   else k_aev_fwd<0><<<grid, kWarps * 32, sm, st>>>(ws, ac);
 }
@@ -1272,7 +1304,7 @@ void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
   const size_t sm = aev_bwd_smem(ws, ac.n_pairs);
   const int copies = aev_bwd_copies(cap_l, ac.n_pairs);
   const int log_r = copies == 4 ? 2 : copies == 2 ? 1 : 0;
-  const int grid = (n_in + kWarps - 1) / kWarps;
+  const int grid = centre_grid(n_in);
   if (ac.zeta == 32) {
     if (want_virial) k_aev_bwd<32, true><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r, cap_l);
     else k_aev_bwd<32, false><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r, cap_l);

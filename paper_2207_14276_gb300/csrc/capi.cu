@@ -378,7 +378,7 @@ size_t carve(nnp_handle* h, char* base) {
   ws.species_count = c.take<int>(kMaxSpecies);
   ws.species_fill = c.take<int>(kMaxSpecies);
   ws.seg_start = c.take<int>(kMaxSpecies + 1);
-  ws.totals = c.take<int>(4);
+  ws.totals = c.take<int>(8);
   ws.cell_count = c.take<int>(cells);
   ws.cell_start = c.take<int>(cells + 1);
   ws.in_cell = c.take<int>(n);
@@ -1558,7 +1558,7 @@ size_t noalloc_carve(const Model& m, int n_atoms, char* base, Ws* ws, MlpBufs* m
   ws->species_count = c.take<int>(kMaxSpecies);
   ws->species_fill = c.take<int>(kMaxSpecies);
   ws->seg_start = c.take<int>(kMaxSpecies + 1);
-  ws->totals = c.take<int>(4);
+  ws->totals = c.take<int>(8);
   ws->cell_count = c.take<int>(cells);
   ws->cell_start = c.take<int>(cells + 1);
   ws->in_cell = c.take<int>(n);

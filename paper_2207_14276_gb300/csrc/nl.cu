@@ -51,7 +51,11 @@ __device__ __forceinline__ void init_body(const Ws& ws, const BatchParams& bp, i
   // the AEV kernel ORs this call's live slices into the tile masks
   if (zero_all && ws.tile_mask)
     for (int i = tid; i <= ws.row_cap / 128; i += stride) ws.tile_mask[i] = 0u;
-  if (zero_all && tid == 0) ws.totals[2] = 0;   // centres handed to the CTA-per-centre backward
+  if (zero_all && tid == 0) {
+    ws.totals[2] = 0;   // centres handed to the CTA-per-centre backward
+    ws.totals[4] = 0;   // next centre of the AEV forward
+    ws.totals[5] = 0;   // next centre of the warp-per-centre backward
+  }
   if (!rebuild) {
     // persistent lists: the grids and counts of the last build stay; only this
     // call's pointers are new, and the forces start again from zero

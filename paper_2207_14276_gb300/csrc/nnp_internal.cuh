@@ -139,7 +139,8 @@ struct Ws {
   int* species_count;   // [kMaxSpecies]
   int* species_fill;    // [kMaxSpecies]
   int* seg_start;       // [kMaxSpecies+1] 128-aligned row segments; [S] = total rows
-  int* totals;          // [4]: total ML atoms, total cells
+  int* totals;          // [8]: total ML atoms, total cells, dense centres, -, next centre
+                        // of the AEV forward and of the warp-per-centre backward
   int* cell_count;      // [cell_cap]
   int* cell_start;      // [cell_cap + 1]
   // per input atom
