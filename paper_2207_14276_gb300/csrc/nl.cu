@@ -612,39 +612,58 @@ __device__ __forceinline__ void centre_lists_staged(const Ws& ws, const AevConst
   int* out_r = ws.nb_r + (size_t)p * ws.cap_r;
   int* out_a = ws.nb_a + (size_t)p * ws.cap_a;
   int wr_r = 0, wr_a = 0;
+  // candidate t of the staged list: within the radial / angular list cutoff?
+  auto test = [&](int t, int end, int& j, bool& keep, bool& ang) {
+    keep = ang = false;
+    j = 0;
+    if (t < end) {
+      const float4 xj = cand[t];
+      j = cand_j[t];
+      float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+      if (any_mi) {
+        float n;
+        if (min_img[0]) { n = rintf(dx / d.in.box_hi[0]); dx = fmaf(-n, d.in.box_hi[0], dx); dx = fmaf(-n, d.in.box_lo[0], dx); }
+        if (min_img[1]) { n = rintf(dy / d.in.box_hi[1]); dy = fmaf(-n, d.in.box_hi[1], dy); dy = fmaf(-n, d.in.box_lo[1], dy); }
+        if (min_img[2]) { n = rintf(dz / d.in.box_hi[2]); dz = fmaf(-n, d.in.box_hi[2], dz); dz = fmaf(-n, d.in.box_lo[2], dz); }
+      }
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      keep = (r2 <= rr2) && (r2 > 1e-12f) && (j != p);
+      ang = keep && (r2 <= ra2);
+    }
+  };
   for (int s = 0; s < ac.S; ++s) {
     int cr = 0, ca = 0;
     const int end = sp_start[s + 1];
-    for (int t0 = sp_start[s]; t0 < end; t0 += 32) {
-      const int t = t0 + lane;
-      bool keep = false, ang = false;
-      int j = 0;
-      if (t < end) {
-        const float4 xj = cand[t];
-        j = cand_j[t];
-        float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        if (any_mi) {
-          float n;
-          if (min_img[0]) { n = rintf(dx / d.in.box_hi[0]); dx = fmaf(-n, d.in.box_hi[0], dx); dx = fmaf(-n, d.in.box_lo[0], dx); }
-          if (min_img[1]) { n = rintf(dy / d.in.box_hi[1]); dy = fmaf(-n, d.in.box_hi[1], dy); dy = fmaf(-n, d.in.box_lo[1], dy); }
-          if (min_img[2]) { n = rintf(dz / d.in.box_hi[2]); dz = fmaf(-n, d.in.box_hi[2], dz); dz = fmaf(-n, d.in.box_lo[2], dz); }
-        }
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        keep = (r2 <= rr2) && (r2 > 1e-12f) && (j != p);
-        ang = keep && (r2 <= ra2);
+    // two 32-candidate chunks per pass (independent loads and tests), appended
+    // in candidate order
+    for (int t0 = sp_start[s]; t0 < end; t0 += 64) {
+      int j0, j1;
+      bool k0, a0, k1, a1;
+      test(t0 + (int)lane, end, j0, k0, a0);
+      test(t0 + 32 + (int)lane, end, j1, k1, a1);
+      const unsigned br0 = __ballot_sync(0xffffffffu, k0), ba0 = __ballot_sync(0xffffffffu, a0);
+      const unsigned br1 = __ballot_sync(0xffffffffu, k1), ba1 = __ballot_sync(0xffffffffu, a1);
+      const unsigned lt = lanemask_lt();
+      if (k0) {
+        const int at = wr_r + cr + __popc(br0 & lt);
+        if (at < ws.cap_r && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j0, ws.totals[0])) out_r[at] = j0;
       }
-      const unsigned br = __ballot_sync(0xffffffffu, keep);
-      const unsigned ba = __ballot_sync(0xffffffffu, ang);
-      if (keep) {
-        const int at = wr_r + cr + __popc(br & lanemask_lt());
-        if (at < ws.cap_r && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j, ws.totals[0])) out_r[at] = j;
+      if (a0) {
+        const int at = wr_a + ca + __popc(ba0 & lt);
+        if (at < ws.cap_a && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j0, ws.totals[0])) out_a[at] = j0;
       }
-      if (ang) {
-        const int at = wr_a + ca + __popc(ba & lanemask_lt());
-        if (at < ws.cap_a && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j, ws.totals[0])) out_a[at] = j;
+      cr += __popc(br0);
+      ca += __popc(ba0);
+      if (k1) {
+        const int at = wr_r + cr + __popc(br1 & lt);
+        if (at < ws.cap_r && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j1, ws.totals[0])) out_r[at] = j1;
       }
-      cr += __popc(br);
-      ca += __popc(ba);
+      if (a1) {
+        const int at = wr_a + ca + __popc(ba1 & lt);
+        if (at < ws.cap_a && NNP_IN_BOUNDS(ws.status, kSiteNbCandidate, j1, ws.totals[0])) out_a[at] = j1;
+      }
+      cr += __popc(br1);
+      ca += __popc(ba1);
     }
     const int keep_r = max(0, min(cr, ws.cap_r - wr_r));
     const int keep_a = max(0, min(ca, ws.cap_a - wr_a));
