@@ -490,3 +490,25 @@ def test_sparse_rows_equal_dense_rows(torch_cuda, precision, kind):
     Gr = orc.energy_forces(s.coords, s.species, s.box, want_aev=True)["aev"]
     tol = 2e-5 if precision == "fp32" else 5e-3
     np.testing.assert_allclose(G, Gr, rtol=tol, atol=1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp32_split", "bf16"])
+def test_batch_of_more_systems_than_one_parameter_chunk(torch_cuda, precision):
+    """150 molecules in one call: the descriptors travel as kernel parameters in
+    chunks of 64 systems, so the front end runs three init and prep launches and
+    the later kernels index systems across chunks.  Every molecule's energy and
+    forces against the oracle, plus a periodic box in the last chunk."""
+    pot, orc = make("ani7", precision=precision)
+    rng = np.random.Generator(np.random.PCG64(77))
+    mols = [synth.gas_molecule(rng, int(n), synth.systems._species_exact(
+        synth.systems.SOLUTE_FRACTIONS, int(n), rng)) for n in rng.integers(8, 33, 149)]
+    mols.append(synth.water_box(100, 14.5, 5, seed=3))
+    outs = pot.energy_forces_batch([to_cuda(m) for m in mols], atom_energies=True)
+    bf16 = precision == "bf16"
+    for m, o in zip(mols, outs):
+        ref = orc.energy_forces(m.coords, m.species, m.box)
+        scale = float(np.abs(ref["atom_energies"]).sum())
+        assert abs(float(o["energy"].cpu()[0]) - ref["energy"]) <= (2e-3 * scale + 1e-4 if bf16 else E_TOL)
+        rms, _ = force_errors(o["forces"].cpu().numpy(), ref["forces"])
+        f_rms = float(np.sqrt(np.mean(ref["forces"] ** 2)))
+        assert rms <= (2e-2 if bf16 else 1e-4) * f_rms + 1e-7
