@@ -85,8 +85,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--serving-rates", default="",
                     help="Poisson request rates (req/s) of the serving stream, e.g. "
-                         "'1000,10000,50000'; off by default: one run of the BF16 server "
-                         "raised an illegal-address fault whose cause is not known")
+                         "'1000,10000,50000,1e9' (1e8 or more: the whole stream at once, "
+                         "the sustained capacity); off by default")
+    ap.add_argument("--serving-precision", default="fp32", choices=["fp32", "bf16"],
+                    help="network path of the batched server (fp32 by default: one run of "
+                         "the BF16 server raised an illegal-address fault whose cause is "
+                         "not known, so it runs only when asked for)")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--md-steps", type=int, default=100,
                     help="MD-like trajectory steps for the persistent-list (skin) measurement; 0 to skip")
@@ -508,6 +512,7 @@ def drive_stream(srv, reqs, rids):
     th = threading.Thread(target=poller)
     th.start()
     t0 = time.perf_counter() + 0.02
+    t_sub = time.perf_counter()
     for k, r in enumerate(reqs):
         target = t0 + r.arrival_s
         while True:
@@ -522,18 +527,23 @@ def drive_stream(srv, reqs, rids):
             tk = srv.submit(r.solute_xyz, resident_id=rids[r.box_id])
         lag[k] = time.perf_counter() - target
         tickets[k] = tk
+    t_sub = time.perf_counter() - max(t_sub, t0)
     th.join()
     lat = np.array([lag[k] + done[k][3] for k in range(n)])
     bad = sum(1 for d in done if d[0] != 0)
     makespan = max(reqs[k].arrival_s + lat[k] for k in range(n))
     atoms = sum(r.n_ml for r in reqs)
-    return {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
-            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "atom_evals_per_s": atoms / makespan, "requests": n, "failed": bad}
+    out = {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+           "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+           "atom_evals_per_s": atoms / makespan,
+           "offered_atom_evals_per_s": atoms / max(reqs[-1].arrival_s, 1e-9),
+           "submit_req_per_s": n / max(t_sub, 1e-9),
+           "requests": n, "failed": bad}
+    return out, done
 
 
-def run_serving(rates, n_requests, precision="bf16", lanes=2, max_systems=256,
-                max_atoms=262144, seed=3):
+def run_serving(rates, n_requests, precision="fp32", lanes=2, max_systems=256,
+                max_atoms=262144, seed=3, oracle_sample=0):
     from paper_2207_14276_gb300 import Potential
     from paper_2207_14276_gb300.serving import Server
     spec = synth.model_spec("ani7")
@@ -544,13 +554,42 @@ def run_serving(rates, n_requests, precision="bf16", lanes=2, max_systems=256,
     # warm-up: every lane sees a full-size batch once
     drive_stream(srv, synth.request_stream(1e6, 64, seed=999, boxes=boxes), rids)
     out = {}
+    errs = []
     for i, rate in enumerate(rates):
-        reqs = synth.request_stream(rate, n_requests, seed=seed + i, boxes=boxes)
+        # at least 0.4 s of arrivals per rate; a rate of 1e8 req/s or more submits
+        # the whole stream at once and so measures the sustained capacity
+        saturated = rate >= 1e8
+        n_req = 5 * n_requests if saturated else max(n_requests, int(0.4 * rate))
+        reqs = synth.request_stream(rate, n_req, seed=seed + i, boxes=boxes)
         b0, r0 = srv.stats()
-        res = drive_stream(srv, reqs, rids)
+        res, done = drive_stream(srv, reqs, rids)
         b1, r1 = srv.stats()
         res["mean_batch"] = (r1 - r0) / max(b1 - b0, 1)
-        out[str(int(rate))] = res
+        if saturated:
+            del res["offered_atom_evals_per_s"]
+        out["saturated" if saturated else str(int(rate))] = res
+        if oracle_sample and i == len(rates) - 1:
+            # the served results of the first gas-phase requests of the last
+            # stream (the largest batches) against the FP64 oracle
+            import oracle
+            orc = oracle.Model(spec, synth.make_weights(spec, 1))
+            for r, d in zip(reqs, done):
+                if r.system is None or d[0] != 0:
+                    continue
+                ref = orc.energy_forces(r.system.coords, r.system.species)
+                dF = np.asarray(d[2], np.float64).reshape(-1, 3) - ref["forces"]
+                errs.append((abs(float(d[1]) - ref["energy"]), float(np.sqrt(np.mean(dF * dF))),
+                             float(np.abs(dF).max())))
+                if len(errs) >= oracle_sample:
+                    break
+    if errs:
+        e = np.array(errs)
+        out["errors_vs_oracle"] = {
+            "sample": f"the first {len(errs)} gas-phase requests of the last stream "
+                      f"({'saturated' if rates[-1] >= 1e8 else f'{int(rates[-1])} req/s'})",
+            "energy_abs_err_max_kcal_mol": float(e[:, 0].max()),
+            "force_err_rms_kcal_mol_A": float(np.sqrt(np.mean(e[:, 1] ** 2))),
+            "force_err_max_kcal_mol_A": float(e[:, 2].max())}
     srv.close()
     return out
 
@@ -907,10 +946,12 @@ def run_ours(args):
                         "1008-256-192-160-1; Poisson arrivals; latency from scheduled arrival"}
         # the serving runs come last among the GPU sections: a failure there is
         # recorded in its entry and leaves the measurements above intact
-        for key, fn in (("batched_bf16",
-                         lambda: run_serving(rates, args.serving_requests, "bf16", lanes=2)),
+        for key, fn in ((f"batched_{args.serving_precision}",
+                         lambda: run_serving(rates, args.serving_requests, args.serving_precision,
+                                             lanes=2, oracle_sample=100)),
                         ("one_system_per_launch_fp32",
-                         lambda: run_serving(rates[:2], args.serving_requests // 4, "fp32",
+                         lambda: run_serving([r for r in rates if r <= 5000] + [1e9],
+                                             args.serving_requests, "fp32",
                                              lanes=1, max_systems=1))):
             try:
                 serving[key] = fn()
