@@ -162,27 +162,78 @@ struct ListHdr {
 constexpr int kGallBlocks = 16;
 
 // float4s of shared memory per warp of the backward kernel: neighbour geometry
-// and cutoffs (2 cap_a), `copies` copies of the x/y/z accumulators (3 cap_a
-// copies floats), radial dE/dG (32), up to kGallBlocks angular blocks' dE/dG
-// (8 per block) and the block table (5 ints per block + 1)
+// and cutoffs (2 cap_a), `copies` copies of the float4 accumulators (one per
+// neighbour each), a region that holds first the radial dE/dG (S * 16 <= 128
+// floats) and then up to kGallBlocks angular blocks' dE/dG (9 float4s per block:
+// 8 rows [z][a] and one of padding, so that lanes reading row z of different
+// blocks hit different banks), and the bytes of the neighbours' species and of
+// the species-pair -> block-slot table (64)
+constexpr int kGallStride = 9;
+__host__ __device__ constexpr int aev_bwd_gall_f4(int n_pairs) {
+  return kGallStride * (n_pairs < kGallBlocks ? n_pairs : kGallBlocks) > 32
+             ? kGallStride * (n_pairs < kGallBlocks ? n_pairs : kGallBlocks)
+             : 32;
+}
 __host__ __device__ constexpr int aev_bwd_warp_f4(int cap_a, int n_pairs, int copies) {
-  return 2 * cap_a + (3 * cap_a * copies + 3) / 4 + 32 +
-         8 * (n_pairs < kGallBlocks ? n_pairs : kGallBlocks) + (5 * n_pairs + 1 + 3) / 4;
+  return 2 * cap_a + copies * cap_a + aev_bwd_gall_f4(n_pairs) + (cap_a + 64 + 15) / 16;
 }
 
-// Copies of the per-neighbour angular accumulators.  The lanes of one 32-triplet
-// window often add into the same neighbour (a block with few neighbours of a
-// species repeats them across the window), and shared-memory float atomics on
-// one address serialise; with R copies lane l adds into copy l mod R, so only
-// lanes equal mod R can collide.  R = 4, 2 or 1: the largest that keeps four
-// CTAs on an SM (228 KiB of shared memory per SM, 1 KiB reserved per CTA, plus
-// the static list headers).
+// Copies of the per-neighbour angular accumulators.  The triplets are taken in
+// round-robin order (rr_pair below): one round pairs every neighbour at most
+// once, and the lanes of one 32-triplet pass span at most `copies` consecutive
+// rounds, round r adding into copy r mod copies, so no two lanes of a pass add
+// into the same accumulator and plain read-add-write is race-free.  4, 2 or 1:
+// the most that keep four CTAs on an SM (228 KiB of shared memory per SM, 1 KiB
+// reserved per CTA, plus the static list headers).
 constexpr int kBwdCtaSmem = 228 * 1024 / 4 - 1024 - kWarps * (int)sizeof(ListHdr);
 int aev_bwd_copies(int cap_a, int n_pairs) {
   for (int r = 4; r > 1; r >>= 1)
     if ((size_t)kWarps * aev_bwd_warp_f4(cap_a, n_pairs, r) * sizeof(float4) <= (size_t)kBwdCtaSmem)
       return r;
   return 1;
+}
+
+// The unordered pairs of n neighbours as rounds of disjoint pairs (the circle
+// method of round-robin tournament scheduling).  n even: n - 1 rounds of
+// h = n / 2 pairs, round r = (r, n - 1) and (r + i, r - i) mod (n - 1) for
+// i = 1 .. h - 1; n odd: n rounds of h = (n - 1) / 2 pairs, (r + i, r - i) mod n
+// for i = 1 .. h (neighbour r sits the round out).  Pair t is pair t mod h of
+// round t / h; every unordered pair occurs once.
+struct RoundRobin {
+  int n, m, h, off, n_tri;   // m: the circle's size; off: 1 for odd n
+  float inv_h;
+};
+__device__ __forceinline__ RoundRobin make_round_robin(int n) {
+  RoundRobin rr;
+  rr.n = n;
+  const bool odd = n & 1;
+  rr.m = odd ? n : n - 1;
+  rr.h = max(odd ? (n - 1) / 2 : n / 2, 1);
+  rr.off = odd ? 1 : 0;
+  rr.n_tri = n * (n - 1) / 2;
+  rr.inv_h = 1.f / (float)rr.h;
+  return rr;
+}
+// round of pair t (exact: the float estimate is corrected by one step)
+__device__ __forceinline__ int rr_round(const RoundRobin& rr, int t) {
+  int r = (int)((t + 0.5f) * rr.inv_h);
+  if (r * rr.h > t) --r;
+  else if ((r + 1) * rr.h <= t) ++r;
+  return r;
+}
+__device__ __forceinline__ void rr_pair(const RoundRobin& rr, int t, int* round, int* a, int* b) {
+  const int r = rr_round(rr, t);
+  const int i = t - r * rr.h + rr.off;
+  int x = r + i, y = r - i;
+  if (x >= rr.m) x -= rr.m;
+  if (y < 0) y += rr.m;
+  if (i == 0) {   // even n: the fixed neighbour n - 1
+    x = r;
+    y = rr.n - 1;
+  }
+  *round = r;
+  *a = x;
+  *b = y;
 }
 
 __device__ __forceinline__ void load_hdr(const uint16_t* hdr, int S, unsigned lane, ListHdr* h) {
@@ -624,9 +675,10 @@ __device__ __forceinline__ void triplet_bwd(const AevConst& ac, const float4& vj
                    sk * (vj.z - chat * vk.z) + rk * vk.z);
 }
 
-// Warp per centre, for centres with at most cap_l angular neighbours (the
-// per-warp shared-memory region is sized for cap_l); a centre with more is
-// appended to ws.heavy (count in totals[2]) for k_aev_bwd_heavy and skipped.
+// Warp per centre, for centres with at most cap_l angular neighbours whose
+// angular terms fall in at most kGallBlocks species-pair blocks (the blocks'
+// dE/dG are all staged at once); a centre with more is appended to ws.heavy
+// (count in totals[2]) for k_aev_bwd_heavy and skipped.
 template <int ZETA, bool VIR>
 __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int log_r, int cap_l,
                                            int p, float4* sm4, ListHdr& H, int w, unsigned lane) {
@@ -634,26 +686,28 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
   const bool det = ws.fr_det != nullptr;   // deterministic mode
   const int n_copy = 1 << log_r;
   float4* angv = sm4 + (size_t)w * aev_bwd_warp_f4(cap_l, ac.n_pairs, n_copy);
-  float4* angf = angv + cap_l;             // fc, dfc
-  // dE/du per angular neighbour as three arrays (x, y, z), each [neighbour][copy]:
-  // lane l adds into copy l mod n_copy, and lanes adding into consecutive
-  // neighbours hit consecutive banks
-  float* accx = reinterpret_cast<float*>(angf + cap_l);
-  float* accy = accx + cap_l * n_copy;
-  float* accz = accy + cap_l * n_copy;
-  float4* past_acc = angf + cap_l + (3 * cap_l * n_copy + 3) / 4;
-  float* grad = reinterpret_cast<float*>(past_acc);  // S*16 radial dE/dG
-  // dE/dG of up to kGallBlocks angular blocks with triplets, [slot][z][a]
-  const int n_gall = min(ac.n_pairs, kGallBlocks);
-  float4* gall = past_acc + 32;
-  int4* bt_geo = reinterpret_cast<int4*>(gall + 8 * n_gall);         // [n_pairs]
-  int* bt_start = reinterpret_cast<int*>(bt_geo + ac.n_pairs);       // [n_pairs + 1]
+  float4* angf = angv + cap_l;             // fc, dfc, 1/R, packed index
+  float4* acc = angf + cap_l;              // dE/du per neighbour, [copy][neighbour]
+  float4* uni = acc + (size_t)n_copy * cap_l;
+  float* grad = reinterpret_cast<float*>(uni);   // S*16 radial dE/dG, then:
+  float4* gall = uni;                            // angular dE/dG, [slot][z][a] (+ pad)
+  uint8_t* spec = reinterpret_cast<uint8_t*>(uni + aev_bwd_gall_f4(ac.n_pairs));  // [cap_l]
+  uint8_t* pslot = spec + cap_l;           // [8 s + u]: block slot of species pair (s, u)
 
   const float4 xi = ws.xyzq[p];
   const SysDev& d = ws.sys[ws.pos_sys[p]];
   const float* g_row = ws.dEdG + (size_t)ws.pos_slot[p] * ac.Dp;
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
-  if (H.off_a[ac.S] > cap_l) {
+  // species-pair blocks with triplets: pairs of present species and species
+  // present at least twice
+  int n_live;
+  {
+    const int c = (int)lane < ac.S ? H.off_a[lane + 1] - H.off_a[lane] : 0;
+    const int n_one = __popc(__ballot_sync(kFull, c >= 1));
+    const int n_two = __popc(__ballot_sync(kFull, c >= 2));
+    n_live = n_one * (n_one - 1) / 2 + n_two;
+  }
+  if (H.off_a[ac.S] > cap_l || n_live > kGallBlocks) {
     if (lane == 0) {
       const int hi = atomicAdd(ws.totals + 2, 1);
       if (NNP_IN_BOUNDS(ws.status, kSiteBwdHeavy, hi, ws.n_in)) ws.heavy[hi] = p;
@@ -671,7 +725,7 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
     const int f = (int)lane + 32 * i;
     gr[i] = f < ac.S * kNR ? g_row[ac.rcol[f >> 4] + (f & 15)] : 0.f;
   }
-  // angular neighbours: unit vector and R, (f_c, f_c', 1/R, packed index)
+  // angular neighbours: unit vector and R, (f_c, f_c', 1/R, packed index), species
   stage_list(H.off_a[ac.S], la, xi, d, ws, lane,
              [&](int slot, int j, const Geo& g) {
                const float inv = rcp_approx(g.r);
@@ -681,11 +735,13 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
                angf[slot] = make_float4(fc, dfc, inv, __int_as_float(j));
              });
   const int na_tot = H.off_a[ac.S];
-  for (int i = lane; i < (na_tot << log_r); i += 32) {
-    accx[i] = 0.f;
-    accy[i] = 0.f;
-    accz[i] = 0.f;
+  for (int t = lane; t < na_tot; t += 32) {
+    int s = 0;
+    while (s + 1 < ac.S && H.off_a[s + 1] <= t) ++s;
+    spec[t] = (uint8_t)s;
   }
+  for (int c = 0; c < n_copy; ++c)
+    for (int t = lane; t < na_tot; t += 32) acc[c * cap_l + t] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int i = 0; i < kMaxSpecies * kNR / 32; ++i) {
     const int f = (int)lane + 32 * i;
@@ -720,127 +776,89 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
                            det ? ws.fr_det + (size_t)p * ws.cap_r + tb : nullptr);
     }
   }
-  // ---- angular triplets, one lane per (j, k) pair, numbered continuously over
-  // all species-pair blocks of the centre so that a warp's 32 lanes stay busy
-  // across block boundaries
-  const int np = ac.n_pairs;
-  build_block_table(H, ac, lane, bt_geo, bt_start);
-  __syncwarp();   // the block table is complete
-  // the dE/dG blocks with triplets, in block order; a group of up to n_gall of
-  // them at a time is staged (its 32 values, index 8a + z, transposed to [z][a]
-  // so that an angle section is one 16-byte load) and its triplets processed
-  float* gf = reinterpret_cast<float*>(gall);
+  __syncwarp();   // the radial dE/dG's region now takes the angular blocks
+  // ---- the live species-pair blocks: slot k of the k-th live pair (s <= u) in
+  // the order 8 s + u, its dE/dG (32 values, index 8a + z) staged as [z][a]
   {
-    const unsigned l0 = __ballot_sync(kFull, (int)lane < np && bt_start[lane + 1] > bt_start[lane]);
-    const int q1 = 32 + (int)lane;
-    const unsigned l1 = __ballot_sync(kFull, q1 < np && bt_start[q1 + 1] > bt_start[q1]);
-    if (lane == 0) { H.live[0] = l0; H.live[1] = l1; }
-  }
-  __syncwarp();
-  const int n_live = __popc(H.live[0]) + __popc(H.live[1]);
-  const int tpos = (lane & 7) * 4 + (lane >> 3);
-  int bl = 0, cur = -1;
-  int os = 0, cs = 0, ou = 0, cu = 0, same = 0;
-  float inv_cs = 0.f, inv_cu = 0.f;
-  const float4* gblk = gall;
-  for (int first = 0; first < n_live; first += n_gall) {
-    // live blocks first .. first + n_gall - 1 into slots 0 .. (the slot also goes
-    // to bits 17.. of the block's table entry); block ids b_lo .. b_hi
-    int b_lo = -1, b_hi = -1;
-    {
-      unsigned m0 = H.live[0], m1 = H.live[1];
-      for (int idx = 0; idx < first; ++idx) {   // the blocks of earlier groups
-        if (m0) m0 &= m0 - 1;
-        else m1 &= m1 - 1;
+    float* gf = reinterpret_cast<float*>(gall);
+    unsigned m[2];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int l = 32 * half + (int)lane, s = l >> 3, u = l & 7;
+      bool live = false;
+      if (s <= u && u < ac.S) {
+        const int cs = H.off_a[s + 1] - H.off_a[s], cu = H.off_a[u + 1] - H.off_a[u];
+        live = s == u ? cs >= 2 : (cs >= 1 && cu >= 1);
       }
-      const int cnt = min(n_gall, n_live - first);
-      // the group's dE/dG loads are all issued before the shared-memory stores,
-      // eight blocks at a time, so that their latencies overlap
-      for (int k0 = 0; k0 < cnt; k0 += 8) {
-        float gv[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          gv[k] = 0.f;
-          if (k0 + k < cnt) {
-            int q;
-            if (m0) { q = __ffs(m0) - 1; m0 &= m0 - 1; }
-            else { q = 32 + __ffs(m1) - 1; m1 &= m1 - 1; }
-            gv[k] = g_row[ac.acol[q] + lane];
-            if (lane == 0) bt_geo[q].w = (bt_geo[q].w & 0x1ffff) | ((k0 + k) << 17);
-            if (b_lo < 0) b_lo = q;
-            b_hi = q;
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k0 + k < cnt) gf[(k0 + k) * 32 + tpos] = gv[k];
+      m[half] = __ballot_sync(kFull, live);
+      if (live) {
+        const int slot = (half ? __popc(m[0]) : 0) + __popc(m[half] & ((1u << lane) - 1u));
+        pslot[8 * s + u] = (uint8_t)slot;
+        pslot[8 * u + s] = (uint8_t)slot;
       }
     }
-    __syncwarp();
-    const int t_end = bt_start[b_hi + 1];
-    bl = b_lo;
-    cur = -1;
-    // triplet t of the group: its two force terms and their accumulator slots;
-    // false if a bounds check (checked build) rejected its neighbour slots
-    auto triplet = [&](int t, float3& uj, float3& uk, int& aj, int& ak) -> bool {
-      while (bt_start[bl + 1] <= t) ++bl;
-      if (bl != cur) {
-        cur = bl;
-        const int4 g4 = bt_geo[bl];
-        os = g4.x; cs = g4.y; ou = g4.z; cu = g4.w & 0xffff; same = (g4.w >> 16) & 1;
-        inv_cs = rcp_approx((float)max(cs, 1));
-        inv_cu = rcp_approx((float)max(cu, 1));   // decode corrects one step either way
-        gblk = gall + (g4.w >> 17) * 8;
+    // the blocks' loads are issued eight at a time before their stores
+    const int tpos = (lane & 7) * 4 + (lane >> 3);
+    for (int k0 = 0; k0 < n_live; k0 += 8) {
+      float gv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        gv[k] = 0.f;
+        if (k0 + k < n_live) {
+          int l;
+          if (m[0]) { l = __ffs(m[0]) - 1; m[0] &= m[0] - 1; }
+          else { l = 32 + __ffs(m[1]) - 1; m[1] &= m[1] - 1; }
+          const int s = l >> 3, u = l & 7;
+          const int q = s * ac.S - s * (s - 1) / 2 + (u - s);
+          gv[k] = g_row[ac.acol[q] + lane];
+        }
       }
-      int j, k;
-      decode_pair_diag(t - bt_start[bl], same, cs, cu, inv_cs, inv_cu, &j, &k);
-      const int tj = os + j, tk = ou + k;
-      if (!NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tj, na_tot) ||
-          !NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, tk, na_tot))
-        return false;
-      triplet_bwd<ZETA>(ac, angv[tj], angv[tk], angf[tj], angf[tk], gblk, uj, uk);
-      const int cp = (int)lane & (n_copy - 1);
-      aj = (tj << log_r) | cp;
-      ak = (tk << log_r) | cp;
-      return true;
-    };
-    if (!det) {
-      for (int t = bt_start[b_lo] + (int)lane; t < t_end; t += 32) {
-        float3 uj, uk;
-        int aj, ak;
-        if (!triplet(t, uj, uk, aj, ak)) continue;
-        atomicAdd(accx + aj, uj.x);
-        atomicAdd(accy + aj, uj.y);
-        atomicAdd(accz + aj, uj.z);
-        atomicAdd(accx + ak, uk.x);
-        atomicAdd(accy + ak, uk.y);
-        atomicAdd(accz + ak, uk.z);
-      }
-    } else {
-      // deterministic mode: the lanes of a pass add one after the other
-      for (int t0 = bt_start[b_lo]; t0 < t_end; t0 += 32) {
-        float3 uj, uk;
-        int aj = 0, ak = 0;
-        const bool act = t0 + (int)lane < t_end && triplet(t0 + (int)lane, uj, uk, aj, ak);
-        for (int l = 0; l < 32; ++l) {
-          if (act && (int)lane == l) {
-            accx[aj] += uj.x; accy[aj] += uj.y; accz[aj] += uj.z;
-            accx[ak] += uk.x; accy[ak] += uk.y; accz[ak] += uk.z;
-          }
-          __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k0 + k < n_live) gf[(k0 + k) * (4 * kGallStride) + tpos] = gv[k];
+    }
+  }
+  __syncwarp();
+  // ---- angular triplets in round-robin order, one lane per pair: a pass takes
+  // the next 32 pairs but at most n_copy rounds, round r adding into copy
+  // r mod n_copy with plain read-add-write (within a round the pairs are
+  // disjoint, so no two lanes of a pass touch the same accumulator); the order
+  // of every addition is fixed, in the deterministic mode too
+  const RoundRobin rr = make_round_robin(na_tot);
+  for (int t0 = 0; t0 < rr.n_tri;) {
+    const int r0 = rr_round(rr, t0);
+    const int t1 = min(min(t0 + 32, (r0 + n_copy) * rr.h), rr.n_tri);
+    const int t = t0 + (int)lane;
+    if (t < t1) {
+      int r, a, b;
+      rr_pair(rr, t, &r, &a, &b);
+      if (NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, a, na_tot) &&
+          NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, b, na_tot)) {
+        const int slot = pslot[8 * spec[a] + spec[b]];
+        if (NNP_IN_BOUNDS(ws.status, kSiteBwdTriplet, slot, n_live)) {
+          float3 ua, ub;
+          triplet_bwd<ZETA>(ac, angv[a], angv[b], angf[a], angf[b], gall + slot * kGallStride,
+                            ua, ub);
+          float4* A = acc + (r & (n_copy - 1)) * cap_l;
+          float4 x = A[a];
+          x.x += ua.x; x.y += ua.y; x.z += ua.z;
+          A[a] = x;
+          float4 y = A[b];
+          y.x += ub.x; y.y += ub.y; y.z += ub.z;
+          A[b] = y;
         }
       }
     }
-    __syncwarp();   // the group's slots are refilled by the next group
+    __syncwarp();   // the next pass may add into the same accumulators
+    t0 = t1;
   }
-  __syncwarp();
   for (int t = lane; t < na_tot; t += 32) {
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int c = 0; c < n_copy; ++c) {
-      const int i = (t << log_r) + c;
-      a.x += accx[i];
-      a.y += accy[i];
-      a.z += accz[i];
+    float4 a = acc[t];
+    for (int c = 1; c < n_copy; ++c) {
+      const float4 v = acc[c * cap_l + t];
+      a.x += v.x;
+      a.y += v.y;
+      a.z += v.z;
     }
     const float4 v = angv[t];
     const int jt = __float_as_int(angf[t].w);
@@ -1312,7 +1330,8 @@ void launch_aev_bwd(const Ws& ws, int n_in, const AevConst& ac, int want_virial,
     if (want_virial) k_aev_bwd<0, true><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r, cap_l);
     else k_aev_bwd<0, false><<<grid, kWarps * 32, sm, st>>>(ws, ac, log_r, cap_l);
   }
-  if (ws.cap_a <= cap_l) return;   // no centre can have more neighbours than the warps took
+  // no centre can have more neighbours or live species-pair blocks than the warps take
+  if (ws.cap_a <= cap_l && ac.n_pairs <= kGallBlocks) return;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
