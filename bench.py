@@ -83,10 +83,10 @@ def parse():
                          "with the FP64 oracle (0 to skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--serving-rates", default="",
-                    help="Poisson request rates (req/s) of the serving stream, e.g. "
-                         "'1000,10000,50000,1e9' (1e8 or more: the whole stream at once, "
-                         "the sustained capacity); off by default")
+    ap.add_argument("--serving-rates", default="1000,2000,5000,10000,20000,50000,1e9",
+                    help="Poisson request rates (req/s) of the serving stream (1e8 or more: "
+                         "the whole stream at once, the sustained capacity); an empty "
+                         "string skips the serving section")
     ap.add_argument("--serving-precision", default="fp32", choices=["fp32", "bf16"],
                     help="network path of the batched server (fp32 by default: one run of "
                          "the BF16 server raised an illegal-address fault whose cause is "

@@ -23,7 +23,7 @@
 //   radial edges: lane-per-neighbour, 16 shells each.
 //   angular: lane-per-triplet, the triplets numbered continuously over the
 //   species-pair blocks that have any.  The dE/dG of those blocks is staged in
-//   shared memory ([z][a], up to 16 blocks at a time).  Each lane contracts its
+//   shared memory (feature order, up to 16 blocks).  Each lane contracts its
 //   block's 32 values to dE/dcos, dE/dRbar and dE/d(f_j f_k), forms dE/du_j
 //   and dE/du_k and adds them to per-neighbour accumulators in shared memory.
 //   The accumulators come in up to four lane-indexed copies, so that lanes of
@@ -150,23 +150,49 @@ __device__ __forceinline__ float sin_theta(const float4& a, const float4& b, flo
   return sqrt_approx(fmaf(1.f - k * k, chat * chat, s2));
 }
 
+// The angular factors of two sections at once (the pair (z, z + 1) of one
+// float2): base = 1 + c cos(theta_z) + s sin(theta_z), B = base^zeta, and
+// B1 = base^(zeta - 1) where asked for.  Packed FP32x2 multiplies and FMAs (one
+// instruction for both sections; each lane is an IEEE FP32 operation).
+template <int ZETA>
+__device__ __forceinline__ float2 section_pair(const AevConst& ac, int m, float2 c2, float2 s2,
+                                               float2* B1 = nullptr) {
+  const float2 cz = reinterpret_cast<const float2*>(ac.cos_z)[m];
+  const float2 sz = reinterpret_cast<const float2*>(ac.sin_z)[m];
+  const float2 base = __ffma2_rn(s2, sz, __ffma2_rn(c2, cz, make_float2(1.f, 1.f)));
+  if constexpr (ZETA == 32) {
+    float2 p = __fmul2_rn(base, base);   // ^2
+    p = __fmul2_rn(p, p);                // ^4
+    p = __fmul2_rn(p, p);                // ^8
+    p = __fmul2_rn(p, p);                // ^16
+    const float2 B = __fmul2_rn(p, p);
+    // base >= 1 + cos(15 pi / 16) > 0: base^31 = base^32 / base
+    if (B1) *B1 = __fmul2_rn(B, make_float2(rcp_approx(base.x), rcp_approx(base.y)));
+    return B;
+  } else {
+    const float2 b1 = make_float2(ipow<0>(base.x, ac.zeta - 1), ipow<0>(base.y, ac.zeta - 1));
+    if (B1) *B1 = b1;
+    return __fmul2_rn(b1, base);
+  }
+}
+
 // per-warp header: species offsets/counts of the radial and angular lists
 struct ListHdr {
   int off_r[kMaxSpecies + 1], off_a[kMaxSpecies + 1];
   unsigned live[2];   // backward kernel: angular blocks with triplets (bit q = block q)
 };
 
-// dE/dG blocks of a centre held in shared memory at a time by the backward
-// kernel (the blocks with triplets, in block order; a centre with more passes
-// over them in groups of this many)
+// dE/dG blocks of a centre held in shared memory by the warp-per-centre backward
+// kernel (the blocks with triplets, in block order; a centre with more goes to
+// the CTA-per-centre kernel)
 constexpr int kGallBlocks = 16;
 
 // float4s of shared memory per warp of the backward kernel: neighbour geometry
 // and cutoffs (2 cap_a), `copies` copies of the float4 accumulators (one per
 // neighbour each), a region that holds first the radial dE/dG (S * 16 <= 128
 // floats) and then up to kGallBlocks angular blocks' dE/dG (9 float4s per block:
-// 8 rows [z][a] and one of padding, so that lanes reading row z of different
-// blocks hit different banks), and the bytes of the neighbours' species and of
+// 8 in feature order and one of padding, so that lanes reading float4 i of
+// different blocks hit different banks), and the bytes of the neighbours' species and of
 // the species-pair -> block-slot table (64)
 constexpr int kGallStride = 9;
 __host__ __device__ constexpr int aev_bwd_gall_f4(int n_pairs) {
@@ -452,9 +478,10 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
       const int n_tri = same ? cs * (cs - 1) / 2 : cs * cu;
       const int fb = ac.acol[q];
       const float inv_cu = rcp_approx((float)max(cu, 1));   // decode corrects one step either way
-      float acc[32];
+      // acc2[4a + m] holds features 8a + 2m and 8a + 2m + 1 (packed FP32x2 FMAs)
+      float2 acc2[16];
 #pragma unroll
-      for (int f = 0; f < 32; ++f) acc[f] = 0.f;
+      for (int f = 0; f < 16; ++f) acc2[f] = make_float2(0.f, 0.f);
       for (int t0 = 0; t0 < n_tri; t0 += 32) {
         const int t = t0 + lane;
         if (t < n_tri) {
@@ -467,19 +494,27 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
           const float c = ac.cos_scale * chat;
           const float sn = sin_theta(vj, vk, chat, ac.cos_scale);
           const float rb = 0.5f * (vj.w + vk.w);
-          float A[kNA];
+          float2 A[kNA];
 #pragma unroll
           for (int a = 0; a < kNA; ++a) {
             const float x = rb - ac.shf_a[a];
-            A[a] = fast_exp2(ca_ * x * x) * fjk;
+            const float v = fast_exp2(ca_ * x * x) * fjk;
+            A[a] = make_float2(v, v);
           }
+          const float2 c2 = make_float2(c, c), s2 = make_float2(sn, sn);
 #pragma unroll
-          for (int z = 0; z < kNZ; ++z) {
-            const float B = ipow<ZETA>(fmaf(sn, ac.sin_z[z], fmaf(c, ac.cos_z[z], 1.f)), ac.zeta);
+          for (int m = 0; m < kNZ / 2; ++m) {
+            const float2 B = section_pair<ZETA>(ac, m, c2, s2);
 #pragma unroll
-            for (int a = 0; a < kNA; ++a) acc[a * kNZ + z] = fmaf(A[a], B, acc[a * kNZ + z]);
+            for (int a = 0; a < kNA; ++a) acc2[4 * a + m] = __ffma2_rn(A[a], B, acc2[4 * a + m]);
           }
         }
+      }
+      float acc[32];
+#pragma unroll
+      for (int f = 0; f < 16; ++f) {
+        acc[2 * f] = acc2[f].x;
+        acc[2 * f + 1] = acc2[f].y;
       }
       out(fb + lane, transpose_reduce32(acc, lane));
     }
@@ -560,14 +595,20 @@ __device__ __forceinline__ void radial_edge_bwd(const Ws& ws, const AevConst& ac
   float fc, dfc;
   fcut_both(g.r, ac.rc_r, inv_rc_r, &fc, &dfc);
   // dE/dR = sum_r g_r e_r (-2 eta x_r f_c + f_c') = f_c (-2 eta) sum_r g_r e_r x_r + f_c' sum_r g_r e_r
-  float sge = 0.f, sgex = 0.f;
+  // (shells in pairs: packed FP32x2 arithmetic, sums over the even and odd shells)
+  const float2 r2 = make_float2(g.r, g.r), cr2 = make_float2(cr_, cr_);
+  const float2* shf2 = reinterpret_cast<const float2*>(ac.shf_r);
+  const float2* gs2 = reinterpret_cast<const float2*>(gs);   // gs: 8-byte aligned
+  float2 sge2 = make_float2(0.f, 0.f), sgex2 = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int r = 0; r < kNR; ++r) {
-    const float x = g.r - ac.shf_r[r];
-    const float ge = gs[r] * fast_exp2(cr_ * x * x);
-    sge += ge;
-    sgex = fmaf(ge, x, sgex);
+  for (int m = 0; m < kNR / 2; ++m) {
+    const float2 x = __ffma2_rn(shf2[m], make_float2(-1.f, -1.f), r2);
+    const float2 q = __fmul2_rn(__fmul2_rn(x, x), cr2);
+    const float2 ge = __fmul2_rn(gs2[m], make_float2(fast_exp2(q.x), fast_exp2(q.y)));
+    sge2 = __fadd2_rn(sge2, ge);
+    sgex2 = __ffma2_rn(ge, x, sgex2);
   }
+  const float sge = sge2.x + sge2.y, sgex = sgex2.x + sgex2.y;
   const float dEdR = fmaf(fc * (-2.f * ac.eta_r), sgex, dfc * sge);
   const float sc = dEdR * rcp_approx(g.r);
   const float gx = sc * g.dx, gy = sc * g.dy, gz = sc * g.dz;
@@ -614,9 +655,10 @@ __device__ __forceinline__ void build_block_table(const ListHdr& H, const AevCon
 }
 
 // One angular triplet (Eq. 5) of a centre: neighbours j and k (unit vector and
-// R; f_c, f_c', 1/R), the 32 dE/dG values of their species-pair block as
-// [z] float4s of the four radial shells.  Returns dE/d(r_j) and dE/d(r_k)
-// (the force terms on j and k; their negatives act on the centre).
+// R; f_c, f_c', 1/R), the 32 dE/dG values of their species-pair block in
+// feature order (index 8a + z: float4 2a + h holds sections 4h .. 4h + 3 of
+// radial shell a).  Returns dE/d(r_j) and dE/d(r_k) (the force terms on j and
+// k; their negatives act on the centre).
 template <int ZETA>
 __device__ __forceinline__ void triplet_bwd(const AevConst& ac, const float4& vj, const float4& vk,
                                             const float4& fj4, const float4& fk4,
@@ -626,30 +668,38 @@ __device__ __forceinline__ void triplet_bwd(const AevConst& ac, const float4& vj
   const float chat = vj.x * vk.x + vj.y * vk.y + vj.z * vk.z;
   const float c = ac.cos_scale * chat;
   const float sn = fmaxf(sin_theta(vj, vk, chat, ac.cos_scale), 1e-6f);
-  const float c_over_s = c * rcp_approx(sn);
+  const float m_c_over_s = -c * rcp_approx(sn);
   const float rb = 0.5f * (vj.w + vk.w);
   // contract the block's dE/dG over the 8 angle sections first:
-  //   F_a = sum_z g[a][z] B_z,  dF_a = sum_z g[a][z] dB_z/dc
-  float F[kNA] = {0.f, 0.f, 0.f, 0.f}, dF[kNA] = {0.f, 0.f, 0.f, 0.f};
+  //   F_a = sum_z g[a][z] B_z,  dF_a = sum_z g[a][z] dB_z/dc,
+  // dB_z/dc = zeta base^(zeta-1) (cos(theta_z) - sin(theta_z) c / s) (the factor
+  // zeta is applied at the end); sections in pairs, Fp[a] holding the sums over
+  // the even and the odd sections
+  const float2 c2 = make_float2(c, c), s2 = make_float2(sn, sn);
+  const float2 mcs2 = make_float2(m_c_over_s, m_c_over_s);
+  float2 Fp[kNA], dFp[kNA];
 #pragma unroll
-  for (int z = 0; z < kNZ; ++z) {
-    const float base = fmaf(sn, ac.sin_z[z], fmaf(c, ac.cos_z[z], 1.f));
-    float B, B1;
-    if constexpr (ZETA == 32) {
-      // base >= 1 + cos(15 pi / 16) > 0: base^31 = base^32 / base
-      const float p2 = base * base, p4 = p2 * p2, p8 = p4 * p4, p16 = p8 * p8;
-      B = p16 * p16;
-      B1 = B * rcp_approx(base);
-    } else {
-      B1 = ipow<0>(base, ac.zeta - 1);
-      B = B1 * base;
+  for (int a = 0; a < kNA; ++a) Fp[a] = dFp[a] = make_float2(0.f, 0.f);
+  const float2* g2 = reinterpret_cast<const float2*>(gblk);
+#pragma unroll
+  for (int m = 0; m < kNZ / 2; ++m) {
+    float2 B1;
+    const float2 B = section_pair<ZETA>(ac, m, c2, s2, &B1);
+    const float2 cz = reinterpret_cast<const float2*>(ac.cos_z)[m];
+    const float2 sz = reinterpret_cast<const float2*>(ac.sin_z)[m];
+    const float2 dB = __fmul2_rn(B1, __ffma2_rn(sz, mcs2, cz));
+#pragma unroll
+    for (int a = 0; a < kNA; ++a) {
+      const float2 g = g2[4 * a + m];
+      Fp[a] = __ffma2_rn(g, B, Fp[a]);
+      dFp[a] = __ffma2_rn(g, dB, dFp[a]);
     }
-    const float dB = B1 * fmaf(-ac.sin_z[z], c_over_s, ac.cos_z[z]);
-    const float4 gz = gblk[z];
-    F[0] = fmaf(gz.x, B, F[0]); F[1] = fmaf(gz.y, B, F[1]);
-    F[2] = fmaf(gz.z, B, F[2]); F[3] = fmaf(gz.w, B, F[3]);
-    dF[0] = fmaf(gz.x, dB, dF[0]); dF[1] = fmaf(gz.y, dB, dF[1]);
-    dF[2] = fmaf(gz.z, dB, dF[2]); dF[3] = fmaf(gz.w, dB, dF[3]);
+  }
+  float F[kNA], dF[kNA];
+#pragma unroll
+  for (int a = 0; a < kNA; ++a) {
+    F[a] = Fp[a].x + Fp[a].y;
+    dF[a] = dFp[a].x + dFp[a].y;
   }
   float tc = 0.f, tR = 0.f, tf = 0.f;
 #pragma unroll
@@ -690,7 +740,7 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
   float4* acc = angf + cap_l;              // dE/du per neighbour, [copy][neighbour]
   float4* uni = acc + (size_t)n_copy * cap_l;
   float* grad = reinterpret_cast<float*>(uni);   // S*16 radial dE/dG, then:
-  float4* gall = uni;                            // angular dE/dG, [slot][z][a] (+ pad)
+  float4* gall = uni;                            // angular dE/dG, [slot][8a + z] (+ pad)
   uint8_t* spec = reinterpret_cast<uint8_t*>(uni + aev_bwd_gall_f4(ac.n_pairs));  // [cap_l]
   uint8_t* pslot = spec + cap_l;           // [8 s + u]: block slot of species pair (s, u)
 
@@ -778,7 +828,7 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
   }
   __syncwarp();   // the radial dE/dG's region now takes the angular blocks
   // ---- the live species-pair blocks: slot k of the k-th live pair (s <= u) in
-  // the order 8 s + u, its dE/dG (32 values, index 8a + z) staged as [z][a]
+  // the order 8 s + u, its dE/dG (32 values, index 8a + z) staged in that order
   {
     float* gf = reinterpret_cast<float*>(gall);
     unsigned m[2];
@@ -798,7 +848,6 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
       }
     }
     // the blocks' loads are issued eight at a time before their stores
-    const int tpos = (lane & 7) * 4 + (lane >> 3);
     for (int k0 = 0; k0 < n_live; k0 += 8) {
       float gv[8];
 #pragma unroll
@@ -815,7 +864,7 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
       }
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        if (k0 + k < n_live) gf[(k0 + k) * (4 * kGallStride) + tpos] = gv[k];
+        if (k0 + k < n_live) gf[(k0 + k) * (4 * kGallStride) + lane] = gv[k];
     }
   }
   __syncwarp();
@@ -927,7 +976,7 @@ __host__ __device__ constexpr size_t aev_bwd_heavy_smem(int cap_a, int n_pairs, 
   return (size_t)2 * cap_a * 16 +                        // angv, angf
          (size_t)3 * cap_a * (kHeavyThreads / 32) * n_lane * 4 +  // accumulators
          (size_t)kMaxSpecies * kNR * 4 +                  // radial dE/dG
-         (size_t)n_pairs * 32 * 4 +                       // angular dE/dG, [q][z][a]
+         (size_t)n_pairs * 32 * 4 +                       // angular dE/dG, [q][8a + z]
          (size_t)n_pairs * 16 + (size_t)(n_pairs + 1) * 4 + 16;   // block table
 }
 
@@ -985,10 +1034,10 @@ k_aev_bwd_heavy(Ws ws, AevConst ac, int log_n) {
     for (int f = tid; f < ac.S * kNR; f += kHeavyThreads) grad[f] = g_row[ac.rcol[f >> 4] + (f & 15)];
     if (w == 0) build_block_table(H, ac, lane, bt_geo, bt_start);
     __syncthreads();
-    // every block with triplets: its 32 dE/dG values (index 8a + z) as [z][a]
+    // every block with triplets: its 32 dE/dG values (index 8a + z)
     for (int i = tid; i < np * 32; i += kHeavyThreads) {
       const int q = i >> 5, l = i & 31;
-      if (bt_start[q + 1] > bt_start[q]) gf[q * 32 + (l & 7) * 4 + (l >> 3)] = g_row[ac.acol[q] + l];
+      if (bt_start[q + 1] > bt_start[q]) gf[q * 32 + l] = g_row[ac.acol[q] + l];
     }
     __syncthreads();
     float fi[3] = {0.f, 0.f, 0.f};
