@@ -94,9 +94,9 @@ __device__ __forceinline__ Geo pair_geo(const float4& xi, const float4& xj, cons
   float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
   if (d.in.periodic) {
     float n;
-    n = rintf(dx * (1.f / d.in.box_hi[0])); dx = fmaf(-n, d.in.box_hi[0], dx); dx = fmaf(-n, d.in.box_lo[0], dx);
-    n = rintf(dy * (1.f / d.in.box_hi[1])); dy = fmaf(-n, d.in.box_hi[1], dy); dy = fmaf(-n, d.in.box_lo[1], dy);
-    n = rintf(dz * (1.f / d.in.box_hi[2])); dz = fmaf(-n, d.in.box_hi[2], dz); dz = fmaf(-n, d.in.box_lo[2], dz);
+    n = rintf(dx * d.in.inv_box[0]); dx = fmaf(-n, d.in.box_hi[0], dx); dx = fmaf(-n, d.in.box_lo[0], dx);
+    n = rintf(dy * d.in.inv_box[1]); dy = fmaf(-n, d.in.box_hi[1], dy); dy = fmaf(-n, d.in.box_lo[1], dy);
+    n = rintf(dz * d.in.inv_box[2]); dz = fmaf(-n, d.in.box_hi[2], dz); dz = fmaf(-n, d.in.box_lo[2], dz);
   }
   Geo g;
   g.dx = dx; g.dy = dy; g.dz = dz;

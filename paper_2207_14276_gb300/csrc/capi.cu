@@ -564,9 +564,10 @@ void StageHook::end() {
 
 namespace {
 
-void split_box(double L, float* hi, float* lo) {
+void split_box(double L, float* hi, float* lo, float* inv) {
   *hi = (float)L;
   *lo = (float)(L - (double)*hi);
+  *inv = 1.f / *hi;
 }
 
 // batches up to this many atoms (in one descriptor chunk) run the front end of
@@ -722,7 +723,7 @@ int run_batch(nnp_handle* h, int n_sys, const nnp_system_t* sy, cudaStream_t st)
       si.n_in = (int)s.n_atoms;
       si.in_base = in_base;
       si.periodic = s.periodic ? 1 : 0;
-      for (int c = 0; c < 3; ++c) split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c]);
+      for (int c = 0; c < 3; ++c) split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c], &si.inv_box[c]);
       in_base += (int)s.n_atoms;
     }
     chunks.push_back(bp);
@@ -1259,7 +1260,7 @@ extern "C" int nnp_force_vjp_batch(nnp_handle* h, int n_sys, const nnp_vjp_syste
       si.coords = s.coords; si.species = s.species; si.mask = s.mask;
       si.energy = s.energy; si.forces = s.forces; si.virial = nullptr; si.atom_e = s.atom_energies;
       si.n_in = (int)s.n_atoms; si.in_base = in_base; si.periodic = s.periodic ? 1 : 0;
-      for (int c = 0; c < 3; ++c) split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c]);
+      for (int c = 0; c < 3; ++c) split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c], &si.inv_box[c]);
       si.dLdF = vs[b0 + k].dL_dF;
       si.dLdR = vs[b0 + k].dL_dcoords;
       si.gE = vs[b0 + k].dL_dE;
@@ -1659,7 +1660,7 @@ extern "C" int nnp_energy_forces_noalloc(nnp_handle* h, int64_t n_atoms, const f
     si.in_base = 0;
     si.periodic = s.periodic;
     for (int c = 0; c < 3; ++c)
-      split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c]);
+      split_box(s.periodic ? s.box[c] : 1.0, &si.box_hi[c], &si.box_lo[c], &si.inv_box[c]);
     const int n = (int)n_atoms;
     // each stage's launch status is checked so that a failure names its stage
     auto stage_ok = [&](const char* name) -> int {

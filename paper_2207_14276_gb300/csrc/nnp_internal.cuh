@@ -102,6 +102,7 @@ struct SysIn {
   int in_base;       // offset of this system's atoms in the batch input index space
   int periodic;
   float box_hi[3], box_lo[3];   // box edge as float hi + float residual
+  float inv_box[3];             // 1 / box_hi (FP32), for the minimum-image shift
   // force vector-Jacobian product only (null otherwise)
   const float* dLdF;
   float* dLdR;
