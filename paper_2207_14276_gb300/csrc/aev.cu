@@ -237,7 +237,7 @@ __device__ __forceinline__ RoundRobin make_round_robin(int n) {
   rr.h = max(odd ? (n - 1) / 2 : n / 2, 1);
   rr.off = odd ? 1 : 0;
   rr.n_tri = n * (n - 1) / 2;
-  rr.inv_h = 1.f / (float)rr.h;
+  rr.inv_h = rcp_approx((float)rr.h);   // rr_round corrects the estimate by one step
   return rr;
 }
 // round of pair t (exact: the float estimate is corrected by one step)
@@ -847,11 +847,11 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
         pslot[8 * u + s] = (uint8_t)slot;
       }
     }
-    // the blocks' loads are issued eight at a time before their stores
-    for (int k0 = 0; k0 < n_live; k0 += 8) {
-      float gv[8];
+    // the blocks' loads are issued four at a time before their stores
+    for (int k0 = 0; k0 < n_live; k0 += 4) {
+      float gv[4];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < 4; ++k) {
         gv[k] = 0.f;
         if (k0 + k < n_live) {
           int l;
@@ -863,7 +863,7 @@ __device__ __forceinline__ void bwd_centre(const Ws& ws, const AevConst& ac, int
         }
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
+      for (int k = 0; k < 4; ++k)
         if (k0 + k < n_live) gf[(k0 + k) * (4 * kGallStride) + lane] = gv[k];
     }
   }

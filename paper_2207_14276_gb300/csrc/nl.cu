@@ -598,11 +598,14 @@ __device__ void centre_lists_global(const Ws& ws, const AevConst& ac, int p, int
 // Species-sorted radial (R <= rc_r) and angular (R <= rc_a) lists of centre p
 // from the candidates cand[t] / cand_j[t], t in [sp_start[s], sp_start[s+1])
 // for species s (coordinates already shifted to the centre's periodic image;
-// dimensions flagged in min_img take the minimum image per pair instead).
+// dimensions flagged in min_img take the minimum image per pair instead).  With
+// idx, position t of the scan is candidate idx[t] (a subset of the candidates in
+// their order, sp_start counting positions of idx).
 __device__ __forceinline__ void centre_lists_staged(const Ws& ws, const AevConst& ac, int p,
                                                     const float4* cand, const int* cand_j,
                                                     const int* sp_start, const int* min_img,
-                                                    const SysDev& d) {
+                                                    const SysDev& d,
+                                                    const uint16_t* idx = nullptr) {
   const unsigned lane = threadIdx.x & 31;
   const float4 xi = ws.xyzq[p];
   const float rl = ac.rc_r + ac.skin, al = ac.rc_a + ac.skin;   // list cutoffs
@@ -617,8 +620,9 @@ __device__ __forceinline__ void centre_lists_staged(const Ws& ws, const AevConst
     keep = ang = false;
     j = 0;
     if (t < end) {
-      const float4 xj = cand[t];
-      j = cand_j[t];
+      const int c = idx ? (int)idx[t] : t;
+      const float4 xj = cand[c];
+      j = cand_j[c];
       float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
       if (any_mi) {
         float n;
@@ -686,6 +690,12 @@ __device__ __forceinline__ void centre_lists_staged(const Ws& ws, const AevConst
 
 constexpr int kNbThreads = 256;   // 8 warps
 constexpr int kCandCap = 2048;    // staged candidates of one home cell
+constexpr int kOctCap = 512;      // candidates of one octant list
+
+// octant of a point of the home cell about the cell's centre mid
+__device__ __forceinline__ int octant_of(const float4& x, const float* mid) {
+  return (x.x >= mid[0] ? 1 : 0) | (x.y >= mid[1] ? 2 : 0) | (x.z >= mid[2] ? 4 : 0);
+}
 
 // One CTA per home cell (grid-stride over the cells of the batch).  The atoms of
 // the 27 neighbour cells are staged once in shared memory, shifted to the home
@@ -700,6 +710,13 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbors(Ws ws, AevConst ac) {
   __shared__ float r_shift[27][3];
   __shared__ int sp_start[kMaxSpecies + 1];
   __shared__ int min_img[3];
+  // octant lists: the candidates (positions in cand, in order) within the list
+  // cutoff of the bounding box of the home cell's atoms in each octant
+  __shared__ uint16_t oct_idx[8][kOctCap];
+  __shared__ int oct_sp[8][kMaxSpecies + 1];
+  __shared__ int oct_n[8];
+  __shared__ unsigned oct_key[8][6];   // box as order-preserving keys: min x y z, max x y z
+  __shared__ float oct_mid[3];
   const int tid = threadIdx.x, w = tid >> 5;
   const unsigned lane = tid & 31;
   if (!lists_rebuild(ws)) return;
@@ -815,9 +832,76 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbors(Ws ws, AevConst ac) {
         __syncthreads();
       }
     }
+    // ---- octant lists (when no dimension takes the minimum image per pair):
+    // warp o keeps, species by species and in candidate order, the candidates
+    // within the list cutoff of the bounding box of the home cell's atoms in
+    // octant o; a centre then scans only its octant's list (the same neighbours
+    // in the same order, a superset of them being tested).  A list longer than
+    // kOctCap is not used.
+    const bool use_oct = !(min_img[0] | min_img[1] | min_img[2]);
+    if (use_oct) {
+      if (tid < 48) oct_key[tid / 6][tid % 6] = (tid % 6) < 3 ? 0xffffffffu : 0u;
+      if (tid < 3) oct_mid[tid] = d.origin[tid] + ((float)cc[tid] + 0.5f) / d.inv_cell[tid];
+      __syncthreads();
+      for (int p = cbeg + tid; p < cend; p += kNbThreads) {
+        const float4 x = ws.xyzq[p];
+        const int o = octant_of(x, oct_mid);
+        atomicMin(&oct_key[o][0], float_key(x.x));
+        atomicMin(&oct_key[o][1], float_key(x.y));
+        atomicMin(&oct_key[o][2], float_key(x.z));
+        atomicMax(&oct_key[o][3], float_key(x.x));
+        atomicMax(&oct_key[o][4], float_key(x.y));
+        atomicMax(&oct_key[o][5], float_key(x.z));
+      }
+      __syncthreads();
+      {
+        const int o = w;
+        int cnt = 0;
+        if (oct_key[o][0] <= oct_key[o][3]) {   // the octant holds atoms
+          const float lo[3] = {key_float(oct_key[o][0]), key_float(oct_key[o][1]), key_float(oct_key[o][2])};
+          const float hi[3] = {key_float(oct_key[o][3]), key_float(oct_key[o][4]), key_float(oct_key[o][5])};
+          // the centres' own test decides; this one only has to keep every
+          // candidate it could accept, so its cutoff has a margin for rounding
+          const float rl = ac.rc_r + ac.skin;
+          const float rl2 = rl * rl * (1.f + 1e-5f) + 1e-6f;
+          for (int s = 0; s < ac.S; ++s) {
+            if (lane == 0) oct_sp[o][s] = cnt;
+            const int end = sp_start[s + 1];
+            for (int t0 = sp_start[s]; t0 < end; t0 += 32) {
+              const int t = t0 + (int)lane;
+              bool in = false;
+              if (t < end) {
+                const float4 c = cand[t];
+                const float ex = fmaxf(fmaxf(lo[0] - c.x, c.x - hi[0]), 0.f);
+                const float ey = fmaxf(fmaxf(lo[1] - c.y, c.y - hi[1]), 0.f);
+                const float ez = fmaxf(fmaxf(lo[2] - c.z, c.z - hi[2]), 0.f);
+                in = ex * ex + ey * ey + ez * ez <= rl2;
+              }
+              const unsigned bal = __ballot_sync(0xffffffffu, in);
+              if (in) {
+                const int at = cnt + __popc(bal & lanemask_lt());
+                if (at < kOctCap) oct_idx[o][at] = (uint16_t)t;
+              }
+              cnt += __popc(bal);
+            }
+          }
+          if (lane == 0) oct_sp[o][ac.S] = cnt;
+        }
+        if (lane == 0) oct_n[o] = cnt;
+      }
+      __syncthreads();
+    }
     // ---- one warp per centre of the home cell
-    for (int p = cbeg + w; p < cend; p += kNbThreads / 32)
+    for (int p = cbeg + w; p < cend; p += kNbThreads / 32) {
+      if (use_oct) {
+        const int o = octant_of(ws.xyzq[p], oct_mid);
+        if (oct_n[o] <= kOctCap) {
+          centre_lists_staged(ws, ac, p, cand, cand_j, oct_sp[o], min_img, d, oct_idx[o]);
+          continue;
+        }
+      }
       centre_lists_staged(ws, ac, p, cand, cand_j, sp_start, min_img, d);
+    }
     __syncthreads();   // the stage is rebuilt for the next home cell
   }
 }
