@@ -121,6 +121,19 @@ def test_dense_box_neighbourhood_beyond_the_stage(torch_cuda):
     compare_neighbours(pot, s, pot.spec)
 
 
+@pytest.mark.parametrize("n_mol,edge,n_side", [(1000, 21.5, 10), (600, 16.0, 9)])
+def test_octant_candidate_lists_at_high_density(torch_cuda, n_mol, edge, n_side):
+    # about 1,270 candidates per home cell at three times liquid density (4 cells
+    # per edge): every centre scans its octant's list of ~350 candidates; 1,800
+    # atoms in a 16 A box (3 cells per edge, the whole box is every home cell's
+    # neighbourhood): most octant lists exceed their 512 entries and those
+    # centres scan all candidates.  Either way the lists equal the oracle's.
+    pot, orc = make("ani4")
+    s = synth.water_box(n_mol, edge, n_side, seed=23)
+    check_system(pot, orc, s, rel_f=3e-4, aev=False)
+    compare_neighbours(pot, s, pot.spec)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
 def test_water9000_fp32(torch_cuda, precision):
     # "fp32": tensor-core layers on split BF16 operands (three products per
