@@ -413,6 +413,12 @@ __device__ __forceinline__ void aev_centre(const Ws& ws, const AevConst& ac, int
   float2* rad = reinterpret_cast<float2*>(angf + ws.cap_a + 4);
   const float4 xi = ws.xyzq[p];
   const SysDev& d = ws.sys[ws.pos_sys[p]];
+  {   // the first lines of the neighbour lists travel while the header loads
+    const int* a = nullptr;
+    if (lane < 2 && (int)lane * 32 < ws.cap_r) a = ws.nb_r + (size_t)p * ws.cap_r + lane * 32;
+    else if (lane == 2) a = ws.nb_a + (size_t)p * ws.cap_a;
+    if (a) asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+  }
   load_hdr(ws.nb_cnt + (size_t)p * 16, ac.S, lane, &H);
   const uint32_t m = sparse ? row_slices(H, ac, lane, pair_su) : ~0u;
   if (mask) *mask = m;
