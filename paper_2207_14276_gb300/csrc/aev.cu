@@ -11,7 +11,8 @@
 //   angular (Eq. 5): lane-per-triplet.  The (j, k) pairs of one unordered
 //           species pair are numbered and decoded in closed form; every lane
 //           forms the 4 Gaussians of the averaged distance and the 8 angular
-//           factors of its pair and accumulates all 32 products in registers.
+//           factors of its pair (two sections per packed FP32x2 instruction)
+//           and accumulates all 32 products in registers.
 //           A transpose-reduce across the warp (31 shuffles) leaves lane l with
 //           feature l = 8a + z of the block: one coalesced 128-byte store.
 //   The angular factor uses cos(theta - theta_z) = cos theta cos theta_z +
@@ -20,15 +21,18 @@
 //   specialised at compile time for zeta = 32).
 //
 // Backward (F = -dE/dr)
-//   radial edges: lane-per-neighbour, 16 shells each.
-//   angular: lane-per-triplet, the triplets numbered continuously over the
-//   species-pair blocks that have any.  The dE/dG of those blocks is staged in
-//   shared memory (feature order, up to 16 blocks).  Each lane contracts its
-//   block's 32 values to dE/dcos, dE/dRbar and dE/d(f_j f_k), forms dE/du_j
-//   and dE/du_k and adds them to per-neighbour accumulators in shared memory.
-//   The accumulators come in up to four lane-indexed copies, so that lanes of
-//   one window rarely add into the same address.  Afterwards each neighbour
-//   receives one vector atomic and the centre one warp-reduced atomic.
+//   radial edges: lane-per-neighbour, 16 shells each (two per packed FP32x2
+//   instruction).
+//   angular: lane-per-pair (j, k) of the centre's angular neighbours, the pairs
+//   taken in round-robin order (one round pairs every neighbour at most once).
+//   The dE/dG of the species-pair blocks that have pairs is staged in shared
+//   memory (feature order, up to 16 blocks).  Each lane contracts its block's
+//   32 values to dE/dcos, dE/dRbar and dE/d(f_j f_k), forms dE/du_j and dE/du_k
+//   and adds them to per-neighbour accumulators in shared memory: round r into
+//   copy r mod (number of copies), so no two lanes of a pass add into the same
+//   address.  Afterwards each neighbour receives one vector atomic and the
+//   centre one warp-reduced atomic.  Centres with too many angular neighbours
+//   or blocks go to a CTA-per-centre kernel.
 #include <cuda_bf16.h>
 
 #include <algorithm>

@@ -11,10 +11,12 @@
 //   k_scan     exclusive scan of the cell counts
 //   k_scatter  packed (cell-ordered) float4 coordinates and index maps
 //   k_neighbors one CTA per home cell: the atoms of the 27 neighbour cells are
-//              staged in shared memory, sorted by species; one warp per centre
-//              keeps pairs with R <= rc_r, marks R <= rc_a and writes
-//              species-sorted lists (per-centre search from global memory when
-//              a neighbourhood does not fit the stage)
+//              staged in shared memory, sorted by species, and listed per
+//              octant of the home cell (the candidates near that octant's
+//              atoms); one warp per centre scans its octant's list, keeps pairs
+//              with R <= rc_r, marks R <= rc_a and writes species-sorted lists
+//              (per-centre search from global memory when a neighbourhood does
+//              not fit the stage)
 // A one-chunk batch of at most 2048 atoms runs init .. scatter as one CTA
 // (k_front).  With a Verlet skin, k_skin_check measures the displacement since
 // the last build, the front-end kernels and k_neighbors return at once when no
