@@ -693,6 +693,7 @@ __device__ __forceinline__ void centre_lists_staged(const Ws& ws, const AevConst
 constexpr int kNbThreads = 256;   // 8 warps
 constexpr int kCandCap = 2048;    // staged candidates of one home cell
 constexpr int kOctCap = 512;      // candidates of one octant list
+constexpr int kOctMin = 256;      // octant lists only for more candidates than this
 
 // octant of a point of the home cell about the cell's centre mid
 __device__ __forceinline__ int octant_of(const float4& x, const float* mid) {
@@ -839,8 +840,9 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbors(Ws ws, AevConst ac) {
     // within the list cutoff of the bounding box of the home cell's atoms in
     // octant o; a centre then scans only its octant's list (the same neighbours
     // in the same order, a superset of them being tested).  A list longer than
-    // kOctCap is not used.
-    const bool use_oct = !(min_img[0] | min_img[1] | min_img[2]);
+    // kOctCap is not used; neighbourhoods of at most kOctMin candidates (small
+    // molecules) are scanned whole, which costs less than building the lists.
+    const bool use_oct = !(min_img[0] | min_img[1] | min_img[2]) && total > kOctMin;
     if (use_oct) {
       if (tid < 48) oct_key[tid / 6][tid % 6] = (tid % 6) < 3 ? 0xffffffffu : 0u;
       if (tid < 3) oct_mid[tid] = d.origin[tid] + ((float)cc[tid] + 0.5f) / d.inv_cell[tid];
