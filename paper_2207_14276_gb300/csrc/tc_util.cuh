@@ -256,8 +256,6 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3D bf16 map: dims (d0 innermost, d1, d2), strides in elements for d1 and d2,
-// box (box0, b1, b2) with box0 * 2 bytes equal to the swizzle span
 // 2D map of a row-major [d1][d0] array (row stride ld elements) with a box of
 // box0 columns x box1 rows, no swizzle (epilogue stores from shared memory)
 inline bool make_map_2d(CUtensorMap* m, const void* base, bool fp32, uint64_t d0, uint64_t d1,
@@ -276,6 +274,8 @@ inline bool make_map_2d(CUtensorMap* m, const void* base, bool fp32, uint64_t d0
   return r == CUDA_SUCCESS;
 }
 
+// 3D bf16 map: dims (d0 innermost, d1, d2), strides in elements for d1 and d2,
+// box (box0, b1, b2) with box0 * 2 bytes equal to the swizzle span
 inline bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t st1,
               uint64_t st2, uint32_t b1, uint32_t b2, uint32_t box0 = 64,
               CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
